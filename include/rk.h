@@ -1,0 +1,193 @@
+/*
+ * rk.h -- C ABI of the B300 library for mixed-precision, perturbed diagonally
+ * implicit Runge-Kutta (DIRK) time stepping of linear 3D PDEs du/dt = L u.
+ *
+ * Method (arXiv 2412.16638):
+ *   one step is u_{n+1} = u_n + tau sum_j b_j k_j                 (Eq. RKstep)
+ *   with a tableau split A = A_hi + A_lo into coefficients of high-precision
+ *   stage derivatives k_j = f(y_j) and low-precision ones k^eps_j = f^eps(y_j)
+ *   (Sec. 2.2, Tables ButchertabA/B/C; Eqs. mpAstep1-5).  Each implicit stage
+ *   solves the core system of Sec. 3 (Eq. corelinear) in the stage-derivative
+ *   form (I - tau a_ii L) k^eps_i = L r_i with a low-precision preconditioned
+ *   Krylov method (CG for heat, restarted GMRES for advection-diffusion,
+ *   Sec. 3), followed by the high-precision explicit evaluation
+ *   k_i = L (r_i + tau a_ii k^eps_i) (Sec. 2.1 step 2, Sec. 4.2).
+ *
+ * Grid: n^3 interior nodes of the unit cube, h = 1/(n+1), homogeneous
+ * Dirichlet boundary, lexicographic numbering u[i + j n + k n^2] (Sec. 4.2).
+ *
+ * Conventions for every entry point:
+ *   - returns rk_status; on error rk_last_error() gives a thread-local message;
+ *   - never traps or aborts on bad input: arguments are checked first;
+ *   - host arrays passed in are copied, never retained; the caller keeps
+ *     ownership of everything it passes;
+ *   - the library owns all device memory it allocates (rk_destroy_* frees it);
+ *   - a problem object is not thread-safe; a server object is.
+ *   - RK_ERR_NOT_CONVERGED still leaves a valid state and filled statistics.
+ */
+#ifndef RK_H
+#define RK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RK_OK = 0,
+  RK_ERR_ARG = 1,            /* invalid argument (null pointer, size, enum)      */
+  RK_ERR_OOM = 2,            /* device or host allocation failed / over budget   */
+  RK_ERR_CUDA = 3,           /* a CUDA runtime call failed                       */
+  RK_ERR_NOT_CONVERGED = 4,  /* a stage solve hit max_iter; state still valid    */
+  RK_ERR_NONFINITE = 5,      /* NaN/Inf or Krylov breakdown detected             */
+  RK_ERR_TIMEOUT = 6,        /* a bounded device wait gave up                    */
+  RK_ERR_BUSY = 7,           /* server queue full / job not finished             */
+  RK_ERR_NOT_FOUND = 8       /* unknown job id                                   */
+} rk_status;
+
+typedef enum { RK_F64 = 0, RK_F32 = 1, RK_F16 = 2, RK_BF16 = 3 } rk_dtype;
+
+typedef enum {
+  RK_OP_HEAT7 = 0,      /* L u = kappa/h^2 * (7-point Laplacian), constant kappa,
+                           applied matrix-free (Sec. 5.2.1)                     */
+  RK_OP_ADVDIFF_CSR = 1 /* L u = div(kappa(x) grad u) - v.grad u, face kappa =
+                           mean of the two nodes, first-order upwind, assembled
+                           in CSR (variable-coefficient stand-in for Sec. 5.2.2) */
+} rk_op;
+
+typedef enum { RK_KRYLOV_CG = 0, RK_KRYLOV_GMRES = 1 } rk_krylov;
+
+typedef struct {
+  int op;                    /* rk_op                                             */
+  int n;                     /* interior nodes per direction, 1 <= n <= 1024      */
+  double kappa;              /* constant diffusivity (RK_OP_HEAT7), > 0           */
+  const double* kappa_field; /* RK_OP_ADVDIFF_CSR: n^3 host values at the nodes,
+                                lexicographic; copied at creation                 */
+  double vel[3];             /* RK_OP_ADVDIFF_CSR: constant velocity (vx,vy,vz)   */
+} rk_problem_desc;
+
+typedef struct {
+  int krylov;      /* rk_krylov: CG (symmetric heat) or GMRES (advection-diffusion) */
+  int restart;     /* GMRES restart length m, 1..64 (30 by default)                 */
+  int bj_block;    /* block-Jacobi block size along x: 1, 2, 4, 8, 16 or 32         */
+  double tol_rel;  /* stop when ||res||_2 <= tol_rel ||rhs||_2 ...                  */
+  double tol_abs;  /* ... or ||res||_2 <= tol_abs (either-or rule of Sec. 5.3)     */
+  int max_iter;    /* iteration cap per solve (Sec. 5.3 uses 40)                    */
+  int storage;     /* rk_dtype of the Krylov vectors (and CSR values)               */
+  int arith;       /* rk_dtype of the Krylov arithmetic: RK_F64 (only with F64
+                      storage) or RK_F32                                            */
+  int correct;     /* 1: perturbed form, k_i = L y_i re-evaluated in FP64 after the
+                      low-precision solve (Sec. 2.1/2.2); 0: plain DIRK, k_i taken
+                      from the solve (the FP64 baseline)                            */
+  int max_refine;  /* extra refinement solves when the FP64 true residual
+                      ||L r_i - (I - tau a_ii L) k^eps_i|| / ||L r_i|| exceeds
+                      tol_true (0 disables)                                         */
+  double tol_true; /* true-residual acceptance bound (<= 0: report only)            */
+} rk_solver_desc;
+
+typedef struct {
+  long long iters_total; /* Krylov iterations over all solves of the call         */
+  int iters_max;         /* largest single-solve iteration count                  */
+  int solves;            /* number of stage solves                                */
+  int refinements;       /* refinement solves triggered by the true residual      */
+  int not_converged;     /* solves that hit max_iter                              */
+  double true_res;       /* largest relative FP64 true residual seen (-1 if none) */
+  double seconds;        /* wall time of the call                                 */
+} rk_stats;
+
+typedef struct rk_problem rk_problem;
+typedef struct rk_server rk_server;
+
+/* ---- problem lifecycle (Sec. 3 problem class; Sec. 5.2 test cases) -------- */
+
+/* Create a problem: allocates and owns the device state (u, stage vectors,
+ * Krylov workspace, operator data).  `cuda_stream` is a cudaStream_t (NULL =
+ * legacy default stream) on which every later call of this problem runs.
+ * Errors: RK_ERR_ARG (bad descriptor), RK_ERR_OOM, RK_ERR_CUDA. */
+rk_status rk_create_problem(const rk_problem_desc* desc, const rk_solver_desc* solver,
+                            void* cuda_stream, rk_problem** out);
+
+/* Set the split Butcher tableau (Sec. 2.2): q stages (1..8), A_hi and A_lo
+ * q*q row-major host arrays, b length q.  A_hi must be strictly lower
+ * triangular and A_lo lower triangular (DIRK structure); stage i is implicit
+ * iff A_lo[i*q+i] != 0.  Copied.  Errors: RK_ERR_ARG. */
+rk_status rk_set_tableau(rk_problem* p, int q, const double* A_hi, const double* A_lo,
+                         const double* b);
+
+/* Copy n^3 float64 values into u_n.  is_device_ptr = 1: `u` is a device
+ * pointer (e.g. a torch CUDA tensor), else host memory.  Synchronous. */
+rk_status rk_set_state(rk_problem* p, const double* u, int is_device_ptr);
+
+/* Copy u_n out (n^3 float64).  Synchronous. */
+rk_status rk_get_state(const rk_problem* p, double* u, int is_device_ptr);
+
+/* One time step of size dt (Eq. RKstep).  stats may be NULL. */
+rk_status rk_step(rk_problem* p, double dt, rk_stats* stats);
+
+/* nsteps steps of size dt. */
+rk_status rk_integrate(rk_problem* p, double dt, int nsteps, rk_stats* stats);
+
+rk_status rk_destroy_problem(rk_problem* p);
+
+/* ---- single operations of the step (for testing the kernels) ------------- */
+
+/* y = L x in FP64 (the explicit evaluation k = f(y) of Sec. 4.2).  x, y: n^3
+ * float64, host or device per is_device_ptr. */
+rk_status rk_apply_op(rk_problem* p, const double* x, double* y, int is_device_ptr);
+
+/* Solve (I - shift L) k = g (Eq. corelinear in stage-derivative form) with the
+ * problem's Krylov method, preconditioner and precision, from k = 0.  g, k:
+ * n^3 float64 (k widened from the storage precision).  stats may be NULL. */
+rk_status rk_solve(rk_problem* p, double shift, const double* g, double* k,
+                   int is_device_ptr, rk_stats* stats);
+
+/* z = D^{-1} r with D the x-line block-Jacobi diagonal of (I - shift L), in
+ * the problem's storage/arithmetic precision.  r, z: n^3 float64. */
+rk_status rk_apply_precond(rk_problem* p, double shift, const double* r, double* z,
+                           int is_device_ptr);
+
+/* ---- batched stepping (many independent problems per launch) ------------- */
+
+/* Advance `count` problems by nsteps steps of size dt each, all problems in
+ * one persistent launch per step (one CTA per problem).  Every problem must
+ * be RK_OP_HEAT7 with CG, have a tableau and a state, and share the stream
+ * of ps[0].  stats (may be NULL) receives the totals. */
+rk_status rk_integrate_batch(rk_problem** ps, int count, double dt, int nsteps,
+                             rk_stats* stats);
+
+/* ---- serving: continuous batching of time-integration jobs --------------- */
+
+/* Create a server that admits jobs while their device footprint fits
+ * hbm_budget_bytes and a slot (of max_slots) is free; it steps all resident
+ * jobs together on its own worker thread and stream. */
+rk_status rk_server_create(size_t hbm_budget_bytes, int max_slots, rk_server** out);
+
+/* Queue a job: problem + solver descriptors, tableau, host initial state u0
+ * (copied), step size and count.  Returns its id.  Non-blocking. */
+rk_status rk_submit_job(rk_server* s, const rk_problem_desc* desc, const rk_solver_desc* solver,
+                        int q, const double* A_hi, const double* A_lo, const double* b,
+                        const double* u0, double dt, int nsteps, uint64_t* job_id);
+
+/* done = 1 when the job has finished (result ready).  Non-blocking. */
+rk_status rk_poll_job(rk_server* s, uint64_t job_id, int* done);
+
+/* Block until the job finishes; copy its final state (n^3 float64, host) into
+ * u_out (may be NULL) and its statistics into stats (may be NULL); latency_s
+ * (may be NULL) receives submit-to-finish seconds.  Frees the job. */
+rk_status rk_wait_job(rk_server* s, uint64_t job_id, double* u_out, rk_stats* stats,
+                      double* latency_s);
+
+rk_status rk_server_destroy(rk_server* s);
+
+/* Thread-local description of the last error on this thread ("" if none). */
+const char* rk_last_error(void);
+
+/* Library version string. */
+const char* rk_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RK_H */

@@ -1,0 +1,817 @@
+// C ABI implementation: problem lifecycle, the DIRK stage loop, the heat CG
+// driver and the kernel-level test entry points.
+#include <cmath>
+#include <cstdarg>
+#include <mutex>
+#include <unordered_map>
+
+#include "rk_internal.h"
+
+namespace rk {
+
+static thread_local std::string g_last_error;
+
+void set_error(const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+}
+
+int device_sms() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 148;
+  }
+  return sms;
+}
+
+// Grid size for a grid-stride kernel: enough CTAs for the work, at most the
+// number that can be resident at once (SMs x occupancy).
+int grid_for(const void* kernel, long long work_items, int threads) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, int> occ;
+  int o;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = occ.find(kernel);
+    if (it == occ.end()) {
+      int v = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kernel, threads, 0) != cudaSuccess || v <= 0) v = 1;
+      occ[kernel] = v;
+      o = v;
+    } else {
+      o = it->second;
+    }
+  }
+  long long need = (work_items + threads - 1) / threads;
+  long long cap = (long long)device_sms() * o;
+  long long g = need < cap ? need : cap;
+  return (int)(g < 1 ? 1 : g);
+}
+
+rk_status alloc_dev(rk_problem* p, void** ptr, size_t bytes) {
+  *ptr = nullptr;
+  if (bytes == 0) return RK_OK;
+  cudaError_t e = cudaMalloc(ptr, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *ptr = nullptr;
+    set_error("cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    return RK_ERR_OOM;
+  }
+  p->bytes += bytes;
+  return RK_OK;
+}
+
+// Dense inverse of a tridiagonal m x m block (diag dd, off-diagonals off) by
+// Gauss-Jordan elimination with partial pivoting in FP64, written into the
+// top-left corner of a zeroed BS x BS array.
+static void tridiag_block_inverse(int m, double dd, double off, int BS, double* inv) {
+  std::vector<double> a((size_t)m * 2 * m, 0.0);
+  for (int i = 0; i < m; ++i) {
+    a[(size_t)i * 2 * m + i] = dd;
+    if (i > 0) a[(size_t)i * 2 * m + i - 1] = off;
+    if (i + 1 < m) a[(size_t)i * 2 * m + i + 1] = off;
+    a[(size_t)i * 2 * m + m + i] = 1.0;
+  }
+  for (int c = 0; c < m; ++c) {
+    int piv = c;
+    for (int i = c + 1; i < m; ++i)
+      if (std::fabs(a[(size_t)i * 2 * m + c]) > std::fabs(a[(size_t)piv * 2 * m + c])) piv = i;
+    if (piv != c)
+      for (int jj = 0; jj < 2 * m; ++jj) std::swap(a[(size_t)c * 2 * m + jj], a[(size_t)piv * 2 * m + jj]);
+    const double d = a[(size_t)c * 2 * m + c];
+    for (int jj = 0; jj < 2 * m; ++jj) a[(size_t)c * 2 * m + jj] /= d;
+    for (int i = 0; i < m; ++i) {
+      if (i == c) continue;
+      const double f = a[(size_t)i * 2 * m + c];
+      if (f == 0.0) continue;
+      for (int jj = 0; jj < 2 * m; ++jj) a[(size_t)i * 2 * m + jj] -= f * a[(size_t)c * 2 * m + jj];
+    }
+  }
+  for (int i = 0; i < BS * BS; ++i) inv[i] = 0.0;
+  for (int i = 0; i < m; ++i)
+    for (int jj = 0; jj < m; ++jj) inv[i * BS + jj] = a[(size_t)i * 2 * m + m + jj];
+}
+
+// Block-Jacobi inverses of (I - shift L) for the heat operator: blocks are
+// x-line segments of bs nodes, so every full block is the same tridiagonal
+// matrix (diag 1 + 6 shift c, off -shift c) and the line's tail block is the
+// same matrix of size n mod bs.  Cached per shift value.
+static rk_status heat_minv(rk_problem* p, double shift, const void** out) {
+  const int bs = p->sol.bj_block;
+  for (auto& e : p->minv)
+    if (e.valid && e.shift == shift) {
+      *out = e.dev;
+      return RK_OK;
+    }
+  MinvEntry& e = p->minv[p->minv_next];
+  p->minv_next = (p->minv_next + 1) % 8;
+  const size_t tsize = (p->sol.arith == RK_F64) ? 8 : 4;
+  if (!e.dev) RK_TRY(alloc_dev(p, &e.dev, 2 * (size_t)bs * bs * tsize));
+  std::vector<double> inv(2 * (size_t)bs * bs, 0.0);
+  const double dd = 1.0 + 6.0 * shift * p->c, off = -shift * p->c;
+  tridiag_block_inverse(std::min(bs, p->n), dd, off, bs, inv.data());
+  const int tail = p->n % bs;
+  if (tail) tridiag_block_inverse(tail, dd, off, bs, inv.data() + (size_t)bs * bs);
+  if (tsize == 8) {
+    RK_CUDA(cudaMemcpyAsync(e.dev, inv.data(), inv.size() * 8, cudaMemcpyHostToDevice, p->st));
+    RK_CUDA(cudaStreamSynchronize(p->st));  // the host vector goes out of scope
+  } else {
+    std::vector<float> f(inv.begin(), inv.end());
+    RK_CUDA(cudaMemcpyAsync(e.dev, f.data(), f.size() * 4, cudaMemcpyHostToDevice, p->st));
+    RK_CUDA(cudaStreamSynchronize(p->st));
+  }
+  e.shift = shift;
+  e.valid = true;
+  *out = e.dev;
+  return RK_OK;
+}
+
+rk_status get_minv(rk_problem* p, double shift, const void** out) {
+  if (p->desc.op == RK_OP_HEAT7) return heat_minv(p, shift, out);
+  set_error("get_minv: the CSR preconditioner is set up by the GMRES path");
+  return RK_ERR_ARG;
+}
+
+static HeatGeo heat_geo(const rk_problem* p, int seg) {
+  HeatGeo g;
+  g.n = p->n;
+  g.nseg = (p->n + seg - 1) / seg;
+  g.n2 = (long long)p->n * p->n;
+  g.N = p->N;
+  return g;
+}
+
+rk_status op_apply_f64(rk_problem* p, const double* x, double* y, RhsScalars* rs) {
+  if (p->desc.op != RK_OP_HEAT7) return csr_apply_f64(p, x, y, rs);
+  constexpr int SEG = 4;
+  HeatGeo g = heat_geo(p, SEG);
+  auto kern = heat_apply_f64<SEG>;
+  int grid = grid_for((const void*)kern, g.n2 * g.nseg);
+  kern<<<grid, kThreads, 0, p->st>>>(g, x, y, -6.0 * p->c, p->c, rs, p->partials);
+  RK_CUDA(cudaGetLastError());
+  return RK_OK;
+}
+
+rk_status op_correct_f64(rk_problem* p, double shift, const double* gv, const void* ke, double* kout,
+                         RhsScalars* rs) {
+  if (p->desc.op != RK_OP_HEAT7) return csr_correct_f64(p, shift, gv, ke, kout, rs);
+  constexpr int SEG = 4;
+  HeatGeo g = heat_geo(p, SEG);
+  rk_status st = RK_OK;
+  dispatch_st(p->sol.storage, [&](auto ts, auto) {
+    using S = typename decltype(ts)::type;
+    auto kern = heat_correct_f64<S, SEG>;
+    int grid = grid_for((const void*)kern, g.n2 * g.nseg);
+    kern<<<grid, kThreads, 0, p->st>>>(g, gv, static_cast<const S*>(ke), shift * p->c, kout, rs, p->partials);
+    if (cudaGetLastError() != cudaSuccess) st = RK_ERR_CUDA;
+  });
+  if (st != RK_OK) set_error("heat_correct_f64 launch failed");
+  return st;
+}
+
+// Chunked device-resident CG: after cg_init, sweeps A and B are launched in
+// chunks; each sweep returns at once when the device flag `done` is set, and
+// the host reads the flag back once per chunk.  The first chunk is sized by
+// the iteration count of the previous solve of the same stage slot.
+static rk_status heat_cg_solve(rk_problem* p, double shift, const double* g64, RhsScalars* rs, void* x,
+                               int slot, int* iters, int* status) {
+  const void* minv = nullptr;
+  RK_TRY(get_minv(p, shift, &minv));
+  CgScalars init{};
+  init.tol_rel = p->sol.tol_rel;
+  init.tol_abs = p->sol.tol_abs;
+  init.max_iter = p->sol.max_iter;
+  *p->h_sc = init;
+  RK_CUDA(cudaMemcpyAsync(p->sc, p->h_sc, sizeof(CgScalars), cudaMemcpyHostToDevice, p->st));
+  rk_status st = RK_OK;
+  dispatch_st(p->sol.storage, [&](auto ts, auto tt) {
+    using S = typename decltype(ts)::type;
+    using T = typename decltype(tt)::type;
+    dispatch_bs(p->sol.bj_block, [&](auto bsc) {
+      constexpr int BS = decltype(bsc)::value;
+      constexpr int SEG = seg_of<S, BS>();
+      HeatGeo g = heat_geo(p, SEG);
+      const long long work = g.n2 * g.nseg;
+      const T d = (T)(1.0 + 6.0 * shift * p->c), o = (T)(-shift * p->c);
+      S* r = static_cast<S*>(p->wr);
+      S* z = static_cast<S*>(p->wz);
+      S* xs = static_cast<S*>(x);
+      const T* M = static_cast<const T*>(minv);
+      auto ki = cg_init<S, T, BS, SEG>;
+      auto ka = cg_sweep_a<S, T, SEG>;
+      auto kb = cg_sweep_b<S, T, BS, SEG>;
+      const int gi = grid_for((const void*)ki, work), ga = grid_for((const void*)ka, work),
+                gb = grid_for((const void*)kb, work);
+      ki<<<gi, kThreads, 0, p->st>>>(g, g64, rs, M, r, z, xs, p->sc, p->partials);
+      int launched = 0, cur = 0;
+      const int predicted = p->last_iters[slot] > 0 ? p->last_iters[slot] : 8;
+      int chunk = std::max(2, predicted - 1);
+      while (true) {
+        for (int c = 0; c < chunk; ++c) {
+          S* pn = static_cast<S*>(p->wp[cur]);
+          const S* po = static_cast<const S*>(p->wp[cur ^ 1]);
+          ka<<<ga, kThreads, 0, p->st>>>(g, d, o, z, po, pn, p->sc, p->partials);
+          kb<<<gb, kThreads, 0, p->st>>>(g, d, o, pn, xs, r, z, M, p->sc, p->partials);
+          cur ^= 1;
+        }
+        launched += chunk;
+        if (cudaGetLastError() != cudaSuccess) {
+          st = RK_ERR_CUDA;
+          set_error("CG sweep launch failed");
+          return;
+        }
+        if (cudaMemcpyAsync(p->h_sc, p->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, p->st) != cudaSuccess ||
+            cudaStreamSynchronize(p->st) != cudaSuccess) {
+          st = RK_ERR_CUDA;
+          set_error("CG status readback failed: %s", cudaGetErrorString(cudaGetLastError()));
+          return;
+        }
+        if (p->h_sc->done) break;
+        if (launched > p->sol.max_iter + 4) {  // the device caps iterations itself
+          st = RK_ERR_TIMEOUT;
+          set_error("CG did not stop after %d sweeps", launched);
+          return;
+        }
+        chunk = std::max(4, std::min(64, launched / 4));
+        // while the solve runs every launched pair advances the device count
+        // by one, so the ping-pong parity equals the device iteration parity
+        cur = p->h_sc->iter & 1;
+      }
+    });
+  });
+  if (st != RK_OK) return st;
+  *iters = p->h_sc->iter;
+  *status = p->h_sc->status;
+  p->last_iters[slot] = p->h_sc->iter;
+  return RK_OK;
+}
+
+rk_status krylov_solve(rk_problem* p, double shift, const double* g64, RhsScalars* rs, void* x, int slot,
+                       int* iters, int* status) {
+  if (p->sol.krylov == RK_KRYLOV_GMRES) return gmres_solve(p, shift, g64, rs, x, slot, iters, status);
+  if (p->desc.op != RK_OP_HEAT7) {
+    set_error("CG is implemented for the heat operator; use GMRES for advection-diffusion");
+    return RK_ERR_ARG;
+  }
+  return heat_cg_solve(p, shift, g64, rs, x, slot, iters, status);
+}
+
+static rk_status launch_combine(rk_problem* p, const CombineArgs& a) {
+  rk_status st = RK_OK;
+  dispatch_st(p->sol.storage, [&](auto ts, auto) {
+    using S = typename decltype(ts)::type;
+    auto kern = combine_f64<S>;
+    int grid = grid_for((const void*)kern, a.N);
+    kern<<<grid, kThreads, 0, p->st>>>(a);
+    if (cudaGetLastError() != cudaSuccess) st = RK_ERR_CUDA;
+  });
+  if (st != RK_OK) set_error("combine launch failed");
+  return st;
+}
+
+template <typename F>
+static rk_status launch_typed(rk_problem* p, F&& f) {
+  rk_status st = RK_OK;
+  dispatch_st(p->sol.storage, [&](auto ts, auto) {
+    using S = typename decltype(ts)::type;
+    f(Tag<S>{});
+    if (cudaGetLastError() != cudaSuccess) st = RK_ERR_CUDA;
+  });
+  if (st != RK_OK) set_error("kernel launch failed");
+  return st;
+}
+
+// One DIRK step (Sec. 2.2; Eqs. mpAstep1-5 and RKstep): the same loop as the
+// float64 oracle, with the implicit solves in the storage/arithmetic
+// precision and every explicit evaluation and linear combination in FP64.
+rk_status step_impl(rk_problem* p, double dt, rk_stats* acc) {
+  const int q = p->q;
+  const bool mixed = p->sol.correct != 0;
+  bool implicit[kMaxStages];
+  for (int i = 0; i < q; ++i) implicit[i] = p->Al[i * q + i] != 0.0;
+  rk_status worst = RK_OK;
+  for (int i = 0; i < q; ++i) {
+    // stage right-hand side r_i
+    CombineArgs ca{};
+    ca.u = p->u;
+    ca.out = p->r;
+    ca.N = p->N;
+    for (int j = 0; j < i; ++j) {
+      double chj = dt * p->Ah[i * q + j];
+      double cej = dt * p->Al[i * q + j];
+      if (cej != 0.0 && (!implicit[j] || !mixed)) {
+        chj += cej;  // k^eps_j of an explicit stage (or of the plain form) is k_j
+        cej = 0.0;
+      }
+      if (chj != 0.0) {
+        ca.kh[ca.nh] = p->k[j];
+        ca.ch[ca.nh++] = chj;
+      }
+      if (cej != 0.0) {
+        ca.ke[ca.ne] = p->ke[j];
+        ca.ce[ca.ne] = cej;
+        ca.rs[ca.ne++] = p->rs + j;
+      }
+    }
+    const double* rp = p->u;
+    if (ca.nh + ca.ne > 0) {
+      RK_TRY(launch_combine(p, ca));
+      rp = p->r;
+    }
+    if (!implicit[i]) {
+      RK_TRY(op_apply_f64(p, rp, p->k[i], nullptr));
+      continue;
+    }
+    const double shift = dt * p->Al[i * q + i];
+    RhsScalars* rs = p->rs + i;
+    RK_TRY(op_apply_f64(p, rp, p->g64, rs));  // g = L r_i (FP64) + norms + scale
+    int iters = 0, status = 0;
+    RK_TRY(krylov_solve(p, shift, p->g64, rs, p->ke[i], i, &iters, &status));
+    if (acc) {
+      acc->iters_total += iters;
+      acc->iters_max = std::max(acc->iters_max, iters);
+      acc->solves += 1;
+      if (status == 4) acc->not_converged += 1;
+    }
+    if (status == 5) {
+      set_error("stage %d solve: non-finite value or Krylov breakdown", i);
+      return RK_ERR_NONFINITE;
+    }
+    if (status == 4) worst = RK_ERR_NOT_CONVERGED;
+    if (mixed) {
+      // k_i = L y_i, y_i = r_i + shift k^eps_i, in FP64; true residual
+      RK_TRY(op_correct_f64(p, shift, p->g64, p->ke[i], p->k[i], rs));
+      for (int it = 0; it < p->sol.max_refine && p->sol.tol_true > 0.0; ++it) {
+        RK_CUDA(cudaMemcpyAsync(p->h_rs + i, rs, sizeof(RhsScalars), cudaMemcpyDeviceToHost, p->st));
+        RK_CUDA(cudaStreamSynchronize(p->st));
+        const double rel = std::sqrt(p->h_rs[i].res2 / std::max(p->h_rs[i].gg, 1e-300));
+        if (!(rel > p->sol.tol_true)) break;
+        // refinement: solve (I - shift L) delta = res, k^eps += delta
+        if (!p->res64) RK_TRY(alloc_dev(p, (void**)&p->res64, (size_t)p->N * 8));
+        if (!p->wdelta) RK_TRY(alloc_dev(p, &p->wdelta, (size_t)p->N * dtype_size(p->sol.storage)));
+        RhsScalars* rsd = p->rs + 9;
+        RK_TRY(launch_typed(p, [&](auto ts) {
+          using S = typename decltype(ts)::type;
+          auto kern = true_residual_f64<S>;
+          kern<<<grid_for((const void*)kern, p->N), kThreads, 0, p->st>>>(
+              p->k[i], static_cast<const S*>(p->ke[i]), rs, p->res64, p->N);
+        }));
+        {
+          auto kern = vec_norms_f64;
+          kern<<<grid_for((const void*)kern, p->N), kThreads, 0, p->st>>>(p->res64, p->N, rsd, p->partials);
+          RK_CUDA(cudaGetLastError());
+        }
+        int it2 = 0, st2 = 0;
+        RK_TRY(krylov_solve(p, shift, p->res64, rsd, p->wdelta, 8, &it2, &st2));
+        if (acc) {
+          acc->iters_total += it2;
+          acc->refinements += 1;
+        }
+        RK_TRY(launch_typed(p, [&](auto ts) {
+          using S = typename decltype(ts)::type;
+          auto kern = add_scaled_inplace<S>;
+          kern<<<grid_for((const void*)kern, p->N), kThreads, 0, p->st>>>(
+              static_cast<S*>(p->ke[i]), static_cast<const S*>(p->wdelta), rs, rsd, p->N);
+        }));
+        RK_TRY(op_correct_f64(p, shift, p->g64, p->ke[i], p->k[i], rs));
+      }
+    } else if (!p->ke_alias[i]) {
+      RK_TRY(launch_typed(p, [&](auto ts) {
+        using S = typename decltype(ts)::type;
+        auto kern = widen_f64<S>;
+        kern<<<grid_for((const void*)kern, p->N), kThreads, 0, p->st>>>(static_cast<const S*>(p->ke[i]), rs,
+                                                                         p->k[i], p->N);
+      }));
+    }
+  }
+  // u_{n+1} = u_n + dt sum_j b_j k_j
+  CombineArgs ca{};
+  ca.u = p->u;
+  ca.out = p->u;
+  ca.N = p->N;
+  for (int j = 0; j < q; ++j)
+    if (p->b[j] != 0.0) {
+      ca.kh[ca.nh] = p->k[j];
+      ca.ch[ca.nh++] = dt * p->b[j];
+    }
+  RK_TRY(launch_combine(p, ca));
+  if (mixed && acc) {
+    RK_CUDA(cudaMemcpyAsync(p->h_rs, p->rs, sizeof(RhsScalars) * q, cudaMemcpyDeviceToHost, p->st));
+    RK_CUDA(cudaStreamSynchronize(p->st));
+    for (int i = 0; i < q; ++i)
+      if (implicit[i]) {
+        const double rel = std::sqrt(p->h_rs[i].res2 / std::max(p->h_rs[i].gg, 1e-300));
+        acc->true_res = std::max(acc->true_res, rel);
+      }
+  }
+  return worst;
+}
+
+}  // namespace rk
+
+using namespace rk;
+
+// ------------------------------------------------------------------ helpers
+static rk_status check_solver(const rk_solver_desc* s, const rk_problem_desc* d) {
+  if (!s) {
+    set_error("solver descriptor is NULL");
+    return RK_ERR_ARG;
+  }
+  if (s->krylov != RK_KRYLOV_CG && s->krylov != RK_KRYLOV_GMRES) {
+    set_error("unknown krylov %d", s->krylov);
+    return RK_ERR_ARG;
+  }
+  const int bs = s->bj_block;
+  if (!(bs == 1 || bs == 2 || bs == 4 || bs == 8 || bs == 16 || bs == 32)) {
+    set_error("bj_block must be 1, 2, 4, 8, 16 or 32 (got %d)", bs);
+    return RK_ERR_ARG;
+  }
+  if (s->storage < RK_F64 || s->storage > RK_BF16) {
+    set_error("unknown storage dtype %d", s->storage);
+    return RK_ERR_ARG;
+  }
+  if (!((s->arith == RK_F64 && s->storage == RK_F64) || (s->arith == RK_F32 && s->storage != RK_F64))) {
+    set_error("supported precision pairs: storage F64 / arith F64, storage F32|F16|BF16 / arith F32");
+    return RK_ERR_ARG;
+  }
+  if (!(s->tol_rel >= 0.0) || !(s->tol_abs >= 0.0) || s->max_iter < 1 || s->max_iter > 1000000) {
+    set_error("tolerances must be >= 0 and 1 <= max_iter <= 1e6");
+    return RK_ERR_ARG;
+  }
+  if (s->krylov == RK_KRYLOV_GMRES && (s->restart < 1 || s->restart > 64)) {
+    set_error("GMRES restart must be in 1..64");
+    return RK_ERR_ARG;
+  }
+  if (s->krylov == RK_KRYLOV_CG && d && d->op != RK_OP_HEAT7) {
+    set_error("CG needs the symmetric heat operator");
+    return RK_ERR_ARG;
+  }
+  if (s->max_refine < 0 || s->max_refine > 10) {
+    set_error("max_refine must be in 0..10");
+    return RK_ERR_ARG;
+  }
+  return RK_OK;
+}
+
+static void free_problem(rk_problem* p) {
+  if (!p) return;
+  auto f = [](void* ptr) {
+    if (ptr) cudaFree(ptr);
+  };
+  f(p->u);
+  f(p->r);
+  f(p->g64);
+  f(p->res64);
+  for (int i = 0; i < 8; ++i) {
+    f(p->k[i]);
+    if (!p->ke_alias[i]) f(p->ke[i]);
+  }
+  f(p->wr);
+  f(p->wz);
+  f(p->wp[0]);
+  f(p->wp[1]);
+  f(p->wdelta);
+  f(p->partials);
+  f(p->sc);
+  f(p->rs);
+  for (auto& e : p->minv) f(e.dev);
+  if (p->h_sc) cudaFreeHost(p->h_sc);
+  if (p->h_rs) cudaFreeHost(p->h_rs);
+  csr_free(p);
+  delete p;
+}
+
+extern "C" {
+
+const char* rk_last_error(void) { return g_last_error.c_str(); }
+
+const char* rk_version(void) { return "rk-b300 0.1 (sm_103a)"; }
+
+rk_status rk_create_problem(const rk_problem_desc* desc, const rk_solver_desc* solver, void* cuda_stream,
+                            rk_problem** out) {
+  if (!out) {
+    set_error("out is NULL");
+    return RK_ERR_ARG;
+  }
+  *out = nullptr;
+  if (!desc) {
+    set_error("problem descriptor is NULL");
+    return RK_ERR_ARG;
+  }
+  if (desc->op != RK_OP_HEAT7 && desc->op != RK_OP_ADVDIFF_CSR) {
+    set_error("unknown operator %d", desc->op);
+    return RK_ERR_ARG;
+  }
+  if (desc->n < 1 || desc->n > 1024) {
+    set_error("n must be in 1..1024 (got %d)", desc->n);
+    return RK_ERR_ARG;
+  }
+  if (desc->op == RK_OP_HEAT7 && !(desc->kappa > 0.0 && std::isfinite(desc->kappa))) {
+    set_error("kappa must be positive and finite");
+    return RK_ERR_ARG;
+  }
+  if (desc->op == RK_OP_ADVDIFF_CSR) {
+    if (!desc->kappa_field) {
+      set_error("RK_OP_ADVDIFF_CSR needs kappa_field");
+      return RK_ERR_ARG;
+    }
+    if ((long long)desc->n * desc->n * desc->n * 7 > 2000000000LL) {
+      set_error("CSR with int32 indices supports n^3*7 < 2e9");
+      return RK_ERR_ARG;
+    }
+  }
+  RK_TRY(check_solver(solver, desc));
+  rk_problem* p = new rk_problem();
+  p->desc = *desc;
+  p->desc.kappa_field = nullptr;
+  p->sol = *solver;
+  p->st = static_cast<cudaStream_t>(cuda_stream);
+  p->n = desc->n;
+  p->N = (long long)desc->n * desc->n * desc->n;
+  p->h = 1.0 / (desc->n + 1);
+  p->c = desc->kappa / (p->h * p->h);
+  const size_t N = (size_t)p->N, s = dtype_size(solver->storage);
+  rk_status st = RK_OK;
+  auto A = [&](void** ptr, size_t bytes) {
+    if (st == RK_OK) st = alloc_dev(p, ptr, bytes);
+  };
+  A((void**)&p->u, N * 8);
+  A((void**)&p->r, N * 8);
+  A((void**)&p->g64, N * 8);
+  A(&p->wr, N * s);
+  A(&p->wz, N * s);
+  A(&p->wp[0], N * s);
+  A(&p->wp[1], N * s);
+  A((void**)&p->partials, (size_t)device_sms() * 32 * 4 * 8);
+  A((void**)&p->sc, sizeof(CgScalars));
+  A((void**)&p->rs, 10 * sizeof(RhsScalars));
+  if (st == RK_OK && cudaMallocHost((void**)&p->h_sc, sizeof(CgScalars)) != cudaSuccess) st = RK_ERR_OOM;
+  if (st == RK_OK && cudaMallocHost((void**)&p->h_rs, 10 * sizeof(RhsScalars)) != cudaSuccess) st = RK_ERR_OOM;
+  if (st == RK_OK) {
+    std::vector<RhsScalars> z(10);
+    for (auto& r : z) {
+      r = RhsScalars{};
+      r.sigma = 1.0;
+      r.want_scale = (solver->storage == RK_F16);
+    }
+    if (cudaMemcpy(p->rs, z.data(), sizeof(RhsScalars) * 10, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(p->sc, 0, sizeof(CgScalars)) != cudaSuccess || cudaMemset(p->u, 0, N * 8) != cudaSuccess) {
+      set_error("initial device copies failed");
+      st = RK_ERR_CUDA;
+    }
+  }
+  if (st == RK_OK && desc->op == RK_OP_ADVDIFF_CSR) {
+    // csr_setup reads the kappa field from the caller's descriptor
+    p->desc.kappa_field = desc->kappa_field;
+    st = csr_setup(p);
+    p->desc.kappa_field = nullptr;
+  }
+  if (st != RK_OK) {
+    free_problem(p);
+    return st;
+  }
+  *out = p;
+  return RK_OK;
+}
+
+rk_status rk_destroy_problem(rk_problem* p) {
+  if (!p) {
+    set_error("problem is NULL");
+    return RK_ERR_ARG;
+  }
+  if (p->st)
+    cudaStreamSynchronize(p->st);
+  else
+    cudaDeviceSynchronize();
+  free_problem(p);
+  return RK_OK;
+}
+
+rk_status rk_set_tableau(rk_problem* p, int q, const double* A_hi, const double* A_lo, const double* b) {
+  if (!p || !A_hi || !A_lo || !b) {
+    set_error("rk_set_tableau: NULL argument");
+    return RK_ERR_ARG;
+  }
+  if (q < 1 || q > kMaxStages) {
+    set_error("q must be in 1..%d", kMaxStages);
+    return RK_ERR_ARG;
+  }
+  for (int i = 0; i < q; ++i) {
+    if (!std::isfinite(b[i])) {
+      set_error("b must be finite");
+      return RK_ERR_ARG;
+    }
+    for (int j = 0; j < q; ++j) {
+      if (!std::isfinite(A_hi[i * q + j]) || !std::isfinite(A_lo[i * q + j])) {
+        set_error("tableau entries must be finite");
+        return RK_ERR_ARG;
+      }
+      if (j >= i && A_hi[i * q + j] != 0.0) {
+        set_error("A_hi must be strictly lower triangular (entry %d,%d)", i, j);
+        return RK_ERR_ARG;
+      }
+      if (j > i && A_lo[i * q + j] != 0.0) {
+        set_error("A_lo must be lower triangular (entry %d,%d)", i, j);
+        return RK_ERR_ARG;
+      }
+    }
+    if (A_lo[i * q + i] < 0.0) {
+      set_error("implicit diagonal entries must be >= 0");
+      return RK_ERR_ARG;
+    }
+  }
+  const size_t N = (size_t)p->N, s = dtype_size(p->sol.storage);
+  for (int i = 0; i < q; ++i) {
+    if (!p->k[i]) RK_TRY(alloc_dev(p, (void**)&p->k[i], N * 8));
+    const bool implicit = A_lo[i * q + i] != 0.0;
+    const bool alias = (p->sol.storage == RK_F64 && !p->sol.correct);
+    if (implicit && !p->ke[i]) {
+      if (alias) {
+        p->ke[i] = p->k[i];
+        p->ke_alias[i] = true;
+      } else {
+        RK_TRY(alloc_dev(p, &p->ke[i], N * s));
+      }
+    }
+  }
+  p->q = q;
+  std::memcpy(p->Ah, A_hi, sizeof(double) * q * q);
+  std::memcpy(p->Al, A_lo, sizeof(double) * q * q);
+  std::memcpy(p->b, b, sizeof(double) * q);
+  return RK_OK;
+}
+
+rk_status rk_set_state(rk_problem* p, const double* u, int is_device_ptr) {
+  if (!p || !u) {
+    set_error("rk_set_state: NULL argument");
+    return RK_ERR_ARG;
+  }
+  RK_CUDA(cudaMemcpyAsync(p->u, u, (size_t)p->N * 8,
+                          is_device_ptr ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, p->st));
+  RK_CUDA(cudaStreamSynchronize(p->st));
+  p->has_state = true;
+  return RK_OK;
+}
+
+rk_status rk_get_state(const rk_problem* p, double* u, int is_device_ptr) {
+  if (!p || !u) {
+    set_error("rk_get_state: NULL argument");
+    return RK_ERR_ARG;
+  }
+  RK_CUDA(cudaMemcpyAsync(u, p->u, (size_t)p->N * 8,
+                          is_device_ptr ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, p->st));
+  RK_CUDA(cudaStreamSynchronize(p->st));
+  return RK_OK;
+}
+
+rk_status rk_step(rk_problem* p, double dt, rk_stats* stats) { return rk_integrate(p, dt, 1, stats); }
+
+rk_status rk_integrate(rk_problem* p, double dt, int nsteps, rk_stats* stats) {
+  if (!p) {
+    set_error("problem is NULL");
+    return RK_ERR_ARG;
+  }
+  if (p->q == 0) {
+    set_error("no tableau set");
+    return RK_ERR_ARG;
+  }
+  if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0) {
+    set_error("dt must be positive and finite, nsteps >= 0");
+    return RK_ERR_ARG;
+  }
+  auto t0 = std::chrono::steady_clock::now();
+  rk_stats acc{};
+  acc.true_res = -1.0;
+  rk_status worst = RK_OK;
+  for (int s = 0; s < nsteps; ++s) {
+    rk_status st = step_impl(p, dt, &acc);
+    if (st == RK_ERR_NOT_CONVERGED) {
+      worst = st;
+      continue;
+    }
+    if (st != RK_OK) {
+      if (stats) *stats = acc;
+      return st;
+    }
+  }
+  RK_CUDA(cudaStreamSynchronize(p->st));
+  acc.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (stats) *stats = acc;
+  return worst;
+}
+
+rk_status rk_apply_op(rk_problem* p, const double* x, double* y, int is_device_ptr) {
+  if (!p || !x || !y) {
+    set_error("rk_apply_op: NULL argument");
+    return RK_ERR_ARG;
+  }
+  const size_t bytes = (size_t)p->N * 8;
+  const double* xin = x;
+  double* yout = y;
+  if (!is_device_ptr) {
+    RK_CUDA(cudaMemcpyAsync(p->r, x, bytes, cudaMemcpyHostToDevice, p->st));
+    xin = p->r;
+    yout = p->g64;
+  }
+  RK_TRY(op_apply_f64(p, xin, yout, nullptr));
+  if (!is_device_ptr) RK_CUDA(cudaMemcpyAsync(y, yout, bytes, cudaMemcpyDeviceToHost, p->st));
+  RK_CUDA(cudaStreamSynchronize(p->st));
+  return RK_OK;
+}
+
+rk_status rk_solve(rk_problem* p, double shift, const double* g, double* k, int is_device_ptr, rk_stats* stats) {
+  if (!p || !g || !k) {
+    set_error("rk_solve: NULL argument");
+    return RK_ERR_ARG;
+  }
+  if (!(shift >= 0.0) || !std::isfinite(shift)) {
+    set_error("shift must be finite and >= 0");
+    return RK_ERR_ARG;
+  }
+  auto t0 = std::chrono::steady_clock::now();
+  const size_t bytes = (size_t)p->N * 8;
+  RK_CUDA(cudaMemcpyAsync(p->g64, g, bytes, is_device_ptr ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                          p->st));
+  RhsScalars* rs = p->rs + 8;
+  {
+    auto kern = vec_norms_f64;
+    kern<<<grid_for((const void*)kern, p->N), kThreads, 0, p->st>>>(p->g64, p->N, rs, p->partials);
+    RK_CUDA(cudaGetLastError());
+  }
+  // solve into the delta workspace (storage precision), then widen
+  if (!p->wdelta) RK_TRY(alloc_dev(p, &p->wdelta, (size_t)p->N * dtype_size(p->sol.storage)));
+  int iters = 0, status = 0;
+  RK_TRY(krylov_solve(p, shift, p->g64, rs, p->wdelta, 8, &iters, &status));
+  double* kout = is_device_ptr ? k : p->r;
+  RK_TRY(launch_typed(p, [&](auto ts) {
+    using S = typename decltype(ts)::type;
+    auto kern = widen_f64<S>;
+    kern<<<grid_for((const void*)kern, p->N), kThreads, 0, p->st>>>(static_cast<const S*>(p->wdelta), rs, kout,
+                                                                     p->N);
+  }));
+  if (!is_device_ptr) RK_CUDA(cudaMemcpyAsync(k, kout, bytes, cudaMemcpyDeviceToHost, p->st));
+  RK_CUDA(cudaStreamSynchronize(p->st));
+  if (stats) {
+    *stats = rk_stats{};
+    stats->iters_total = iters;
+    stats->iters_max = iters;
+    stats->solves = 1;
+    stats->not_converged = (status == 4);
+    stats->true_res = -1.0;
+    stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  if (status == 5) {
+    set_error("solve: non-finite value or Krylov breakdown");
+    return RK_ERR_NONFINITE;
+  }
+  return status == 4 ? RK_ERR_NOT_CONVERGED : RK_OK;
+}
+
+rk_status rk_apply_precond(rk_problem* p, double shift, const double* r, double* z, int is_device_ptr) {
+  if (!p || !r || !z) {
+    set_error("rk_apply_precond: NULL argument");
+    return RK_ERR_ARG;
+  }
+  const size_t bytes = (size_t)p->N * 8;
+  const double* rin = r;
+  double* zout = z;
+  if (!is_device_ptr) {
+    RK_CUDA(cudaMemcpyAsync(p->r, r, bytes, cudaMemcpyHostToDevice, p->st));
+    rin = p->r;
+    zout = p->g64;
+  }
+  if (p->desc.op != RK_OP_HEAT7) {
+    RK_TRY(csr_precond_f64(p, shift, rin, zout));
+  } else {
+    const void* minv = nullptr;
+    RK_TRY(get_minv(p, shift, &minv));
+    rk_status lst = RK_OK;
+    dispatch_st(p->sol.storage, [&](auto ts, auto tt) {
+      using S = typename decltype(ts)::type;
+      using T = typename decltype(tt)::type;
+      dispatch_bs(p->sol.bj_block, [&](auto bsc) {
+        constexpr int BS = decltype(bsc)::value;
+        constexpr int SEG = seg_of<S, BS>();
+        HeatGeo g = heat_geo(p, SEG);
+        auto kern = bj_apply_f64io<S, T, BS, SEG>;
+        kern<<<grid_for((const void*)kern, g.n2 * g.nseg), kThreads, 0, p->st>>>(g, rin, static_cast<const T*>(minv),
+                                                                                  zout);
+        if (cudaGetLastError() != cudaSuccess) lst = RK_ERR_CUDA;
+      });
+    });
+    RK_TRY(lst);
+  }
+  if (!is_device_ptr) RK_CUDA(cudaMemcpyAsync(z, zout, bytes, cudaMemcpyDeviceToHost, p->st));
+  RK_CUDA(cudaStreamSynchronize(p->st));
+  return RK_OK;
+}
+
+}  // extern "C"

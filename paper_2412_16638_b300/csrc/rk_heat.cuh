@@ -1,0 +1,393 @@
+// Kernels of the constant-coefficient heat path (7-point stencil applied
+// matrix-free) and the FP64 stage operations on it.
+//
+// Thread mapping: one thread owns a segment of SEG consecutive x-nodes of one
+// x-line (the last segment of a line may be shorter); block-Jacobi blocks are
+// x-line segments of BS <= SEG nodes, so every block lies inside one thread's
+// segment and z = D^{-1} r is computed in registers.  Neighbours in y and z
+// are read from global memory (they are L1/L2 hits: adjacent lines are
+// processed by adjacent threads, adjacent planes by CTAs in flight together).
+#pragma once
+#include "rk_device.cuh"
+
+namespace rk {
+
+struct HeatGeo {
+  int n;          // nodes per direction
+  int nseg;       // segments per x-line = ceil(n / SEG)
+  long long n2;   // n*n
+  long long N;    // n^3
+};
+
+// Device-resident state of one CG solve.  Written by the last CTA of each
+// sweep, read by the next sweep, so no host round trip per iteration.
+struct CgScalars {
+  double rz;       // r . z of the current residual
+  double pAp;      // p . A p
+  double rr;       // ||r||^2 (scaled right-hand side units)
+  double gg;       // ||g||^2
+  double alpha, beta;
+  double thresh2;  // squared stopping threshold
+  double tol_rel, tol_abs;
+  int iter, max_iter;
+  int done;        // 1: stop launching sweeps
+  int status;      // 0 converged / running, 4 not converged, 5 non-finite/breakdown
+  unsigned ticket;
+  int pad;
+};
+
+// Per-solve right-hand-side statistics written by heat_apply_f64 / vec_norms.
+struct RhsScalars {
+  double gg;     // ||g||_2^2 of the FP64 right-hand side
+  double gmax;   // ||g||_inf
+  double sigma;  // storage scale (1/||g||_inf for FP16, else 1)
+  double res2;   // ||true residual||^2 from the FP64 correction
+  unsigned ticket;
+  int want_scale;
+};
+
+// Sum of the six neighbours of every element of a segment (zero outside the
+// grid).  own[] holds the field on the segment (zeros past m); seg(off, m, v)
+// loads the field on the segment that starts at element index off; pt(idx)
+// loads one value.
+template <typename T, int SEG, typename SegF, typename PtF>
+__device__ __forceinline__ void nb_sum(const HeatGeo& g, int i0, int m, int j, int k, long long base,
+                                       const T (&own)[SEG], SegF seg, PtF pt, T (&nb)[SEG]) {
+  const T left = (i0 > 0) ? pt(base - 1) : T(0);
+  const T right = (i0 + SEG < g.n) ? pt(base + SEG) : T(0);
+#pragma unroll
+  for (int e = 0; e < SEG; ++e) {
+    T l = (e > 0) ? own[e - 1] : left;
+    T r = (e + 1 < SEG) ? own[e + 1] : right;
+    nb[e] = l + r;
+  }
+  T tmp[SEG];
+  if (j > 0) {
+    seg(base - g.n, m, tmp);
+#pragma unroll
+    for (int e = 0; e < SEG; ++e) nb[e] += tmp[e];
+  }
+  if (j < g.n - 1) {
+    seg(base + g.n, m, tmp);
+#pragma unroll
+    for (int e = 0; e < SEG; ++e) nb[e] += tmp[e];
+  }
+  if (k > 0) {
+    seg(base - g.n2, m, tmp);
+#pragma unroll
+    for (int e = 0; e < SEG; ++e) nb[e] += tmp[e];
+  }
+  if (k < g.n - 1) {
+    seg(base + g.n2, m, tmp);
+#pragma unroll
+    for (int e = 0; e < SEG; ++e) nb[e] += tmp[e];
+  }
+}
+
+#define RK_SEG_LOOP(g, SEG)                                                            \
+  const long long nsegs_ = (long long)(g).n2 * (g).nseg;                               \
+  for (long long t_ = (long long)blockIdx.x * blockDim.x + threadIdx.x; t_ < nsegs_;   \
+       t_ += (long long)gridDim.x * blockDim.x) {                                      \
+    const long long line = t_ / (g).nseg;                                              \
+    const int sidx = (int)(t_ - line * (g).nseg);                                      \
+    const int i0 = sidx * (SEG);                                                       \
+    const int m = min((SEG), (g).n - i0);                                              \
+    const int j = (int)(line % (g).n);                                                 \
+    const int k = (int)(line / (g).n);                                                 \
+    const long long base = line * (g).n + i0;
+
+#define RK_SEG_LOOP_END }
+
+// ------------------------------------------------------------- FP64 operator
+// y = d*x + o*(sum of neighbours of x) in FP64 (L: d = -6c, o = c with
+// c = kappa/h^2).  If rs != null, also ||y||^2, ||y||_inf and the storage
+// scale are reduced into *rs (the stage right-hand side g = L r_i).
+template <int SEG>
+__global__ void __launch_bounds__(kThreads) heat_apply_f64(HeatGeo g, const double* __restrict__ x,
+                                                           double* __restrict__ y, double d, double o,
+                                                           RhsScalars* rs, double* partials) {
+  double acc[2] = {0.0, 0.0};
+  RK_SEG_LOOP(g, SEG)
+    double xv[SEG], nb[SEG];
+    load_seg<double, double, SEG>(x + base, m, xv);
+    nb_sum<double, SEG>(
+        g, i0, m, j, k, base, xv,
+        [&](long long off, int mm, double (&v)[SEG]) { load_seg<double, double, SEG>(x + off, mm, v); },
+        [&](long long idx) { return x[idx]; }, nb);
+    double yv[SEG];
+#pragma unroll
+    for (int e = 0; e < SEG; ++e) {
+      yv[e] = fma(d, xv[e], o * nb[e]);
+      if (e < m) {
+        acc[0] = fma(yv[e], yv[e], acc[0]);
+        acc[1] = fmax(acc[1], fabs(yv[e]));
+      }
+    }
+    store_seg<double, double, SEG>(y + base, m, yv);
+  RK_SEG_LOOP_END
+  if (rs == nullptr) return;
+  double tot[2];
+  if (grid_reduce<2, 2u>(acc, partials, &rs->ticket, tot)) {
+    rs->gg = tot[0];
+    rs->gmax = tot[1];
+    rs->sigma = (rs->want_scale && tot[1] > 0.0 && isfinite(tot[1])) ? 1.0 / tot[1] : 1.0;
+  }
+}
+
+// ------------------------------------------------------ FP64 explicit correction
+// k = g + c_s * (sum of neighbours of v - 6 v),  v = ke / sigma widened to FP64,
+// c_s = shift * kappa/h^2.  This is k_i = L y_i with y_i = r_i + shift k^eps_i
+// (g = L r_i precomputed), and k - v is the true residual of the stage solve;
+// its squared norm is reduced into rs->res2.
+template <typename S, int SEG>
+__global__ void __launch_bounds__(kThreads) heat_correct_f64(HeatGeo g, const double* __restrict__ gv,
+                                                             const S* __restrict__ ke, double cs,
+                                                             double* __restrict__ kout, RhsScalars* rs,
+                                                             double* partials) {
+  const double inv_sigma = 1.0 / rs->sigma;
+  double acc[1] = {0.0};
+  RK_SEG_LOOP(g, SEG)
+    double v[SEG], nb[SEG], gs[SEG];
+    load_seg<double, S, SEG>(ke + base, m, v);
+    nb_sum<double, SEG>(
+        g, i0, m, j, k, base, v,
+        [&](long long off, int mm, double (&w)[SEG]) { load_seg<double, S, SEG>(ke + off, mm, w); },
+        [&](long long idx) { return wid<double>(ke[idx]); }, nb);
+    load_seg<double, double, SEG>(gv + base, m, gs);
+    double kv[SEG];
+#pragma unroll
+    for (int e = 0; e < SEG; ++e) {
+      const double lap = fma(-6.0, v[e], nb[e]);
+      kv[e] = fma(cs * inv_sigma, lap, gs[e]);
+      const double res = kv[e] - v[e] * inv_sigma;
+      if (e < m) acc[0] = fma(res, res, acc[0]);
+    }
+    store_seg<double, double, SEG>(kout + base, m, kv);
+  RK_SEG_LOOP_END
+  double tot[1];
+  if (grid_reduce<1, 0u>(acc, partials, &rs->ticket, tot)) rs->res2 = tot[0];
+}
+
+// ------------------------------------------------------------- CG sweeps
+// Block-Jacobi inverse in shared memory: [0] full BS-block, [1] the tail
+// block of a line (n mod BS nodes, zero padded).
+template <typename T, int BS>
+__device__ __forceinline__ void load_minv(const T* __restrict__ minv, T* sM) {
+  for (int i = threadIdx.x; i < 2 * BS * BS; i += blockDim.x) sM[i] = minv[i];
+  __syncthreads();
+}
+
+// z = D^{-1} r on every block of the segment.
+template <typename T, int BS, int SEG>
+__device__ __forceinline__ void bj_apply(const T* sM, int n, int i0, const T (&r)[SEG], T (&z)[SEG]) {
+#pragma unroll
+  for (int cb = 0; cb < SEG / BS; ++cb) {
+    const bool tail = (i0 + (cb + 1) * BS > n);
+    const T* M = sM + (tail ? BS * BS : 0);
+#pragma unroll
+    for (int i = 0; i < BS; ++i) {
+      T a = T(0);
+#pragma unroll
+      for (int jj = 0; jj < BS; ++jj) a = fma(M[i * BS + jj], r[cb * BS + jj], a);
+      z[cb * BS + i] = a;
+    }
+  }
+}
+
+// Initialise: r = sigma*g (rounded to S), z = D^{-1} r, x = 0, and the first
+// reductions r.z, r.r.  g is the FP64 right-hand side.
+template <typename S, typename T, int BS, int SEG>
+__global__ void __launch_bounds__(kThreads) cg_init(HeatGeo g, const double* __restrict__ gv,
+                                                    const RhsScalars* rs, const T* __restrict__ minv,
+                                                    S* __restrict__ r, S* __restrict__ z, S* __restrict__ x,
+                                                    CgScalars* sc, double* partials) {
+  __shared__ T sM[2 * BS * BS];
+  load_minv<T, BS>(minv, sM);
+  const double sigma = rs->sigma;
+  double acc[2] = {0.0, 0.0};
+  RK_SEG_LOOP(g, SEG)
+    double gd[SEG];
+    load_seg<double, double, SEG>(gv + base, m, gd);
+    T rv[SEG], zv[SEG], zero[SEG];
+#pragma unroll
+    for (int e = 0; e < SEG; ++e) {
+      rv[e] = (e < m) ? rnd<S, T>((T)(gd[e] * sigma)) : T(0);
+      zero[e] = T(0);
+    }
+    bj_apply<T, BS, SEG>(sM, g.n, i0, rv, zv);
+#pragma unroll
+    for (int e = 0; e < SEG; ++e) {
+      zv[e] = rnd<S, T>(zv[e]);
+      if (e < m) {
+        acc[0] += (double)(rv[e] * zv[e]);
+        acc[1] += (double)(rv[e] * rv[e]);
+      }
+    }
+    store_seg<S, T, SEG>(r + base, m, rv);
+    store_seg<S, T, SEG>(z + base, m, zv);
+    store_seg<S, T, SEG>(x + base, m, zero);
+  RK_SEG_LOOP_END
+  double tot[2];
+  if (grid_reduce<2, 0u>(acc, partials, &sc->ticket, tot)) {
+    sc->rz = tot[0];
+    sc->rr = tot[1];
+    sc->gg = tot[1];
+    const double ta = sc->tol_abs * sigma;
+    sc->thresh2 = fmax(sc->tol_rel * sc->tol_rel * tot[1], ta * ta);
+    sc->iter = 0;
+    sc->beta = 0.0;
+    sc->alpha = 0.0;
+    sc->pAp = 0.0;
+    if (!isfinite(tot[0]) || !isfinite(tot[1])) {
+      sc->done = 1;
+      sc->status = 5;
+    } else if (tot[1] <= sc->thresh2 || tot[1] == 0.0) {
+      sc->done = 1;
+      sc->status = 0;
+    } else {
+      sc->done = 0;
+      sc->status = 0;
+    }
+  }
+}
+
+// Sweep A: p = z + beta*p_old (rounded to S), w = A p with A = d I + o*(neighbour
+// sum), partial p.w.  Writes p to pnew (ping-pong buffer).  Last CTA: alpha.
+template <typename S, typename T, int SEG>
+__global__ void __launch_bounds__(kThreads) cg_sweep_a(HeatGeo g, T d, T o, const S* __restrict__ z,
+                                                       const S* __restrict__ pold, S* __restrict__ pnew,
+                                                       CgScalars* sc, double* partials) {
+  if (sc->done) return;
+  const T beta = (T)sc->beta;
+  const bool first = (sc->iter == 0);
+  double acc[1] = {0.0};
+  RK_SEG_LOOP(g, SEG)
+    auto pseg = [&](long long off, int mm, T (&v)[SEG]) {
+      load_seg<T, S, SEG>(z + off, mm, v);
+      if (!first) {
+        T q[SEG];
+        load_seg<T, S, SEG>(pold + off, mm, q);
+#pragma unroll
+        for (int e = 0; e < SEG; ++e) v[e] = rnd<S, T>(fma(beta, q[e], v[e]));
+      }
+    };
+    auto ppt = [&](long long idx) {
+      T v = wid<T>(z[idx]);
+      if (!first) v = rnd<S, T>(fma(beta, wid<T>(pold[idx]), v));
+      return v;
+    };
+    T p[SEG], nb[SEG];
+    pseg(base, m, p);
+    nb_sum<T, SEG>(g, i0, m, j, k, base, p, pseg, ppt, nb);
+    T pw = T(0);
+#pragma unroll
+    for (int e = 0; e < SEG; ++e) {
+      const T w = fma(d, p[e], o * nb[e]);
+      if (e < m) pw = fma(p[e], w, pw);
+    }
+    acc[0] += (double)pw;
+    store_seg<S, T, SEG>(pnew + base, m, p);
+  RK_SEG_LOOP_END
+  double tot[1];
+  if (grid_reduce<1, 0u>(acc, partials, &sc->ticket, tot)) {
+    sc->pAp = tot[0];
+    const double alpha = sc->rz / tot[0];
+    sc->alpha = alpha;
+    if (!(tot[0] > 0.0) || !isfinite(alpha)) {
+      sc->done = 1;
+      sc->status = 5;
+    }
+  }
+}
+
+// Sweep B: recompute w = A p, x += alpha p, r -= alpha w, z = D^{-1} r,
+// partials r.z and r.r.  Last CTA: beta, convergence test, iteration count.
+template <typename S, typename T, int BS, int SEG>
+__global__ void __launch_bounds__(kThreads) cg_sweep_b(HeatGeo g, T d, T o, const S* __restrict__ p,
+                                                       S* __restrict__ x, S* __restrict__ r, S* __restrict__ z,
+                                                       const T* __restrict__ minv, CgScalars* sc,
+                                                       double* partials) {
+  if (sc->done) return;
+  __shared__ T sM[2 * BS * BS];
+  load_minv<T, BS>(minv, sM);
+  const T alpha = (T)sc->alpha;
+  const bool first = (sc->iter == 0);
+  double acc[2] = {0.0, 0.0};
+  RK_SEG_LOOP(g, SEG)
+    T pv[SEG], nb[SEG];
+    load_seg<T, S, SEG>(p + base, m, pv);
+    nb_sum<T, SEG>(
+        g, i0, m, j, k, base, pv, [&](long long off, int mm, T (&v)[SEG]) { load_seg<T, S, SEG>(p + off, mm, v); },
+        [&](long long idx) { return wid<T>(p[idx]); }, nb);
+    T rv[SEG], xv[SEG], zv[SEG];
+    load_seg<T, S, SEG>(r + base, m, rv);
+    if (!first) {
+      load_seg<T, S, SEG>(x + base, m, xv);
+    } else {
+#pragma unroll
+      for (int e = 0; e < SEG; ++e) xv[e] = T(0);
+    }
+#pragma unroll
+    for (int e = 0; e < SEG; ++e) {
+      const T w = fma(d, pv[e], o * nb[e]);
+      rv[e] = (e < m) ? rnd<S, T>(fma(-alpha, w, rv[e])) : T(0);
+      xv[e] = fma(alpha, pv[e], xv[e]);
+    }
+    bj_apply<T, BS, SEG>(sM, g.n, i0, rv, zv);
+    T rz = T(0), rr = T(0);
+#pragma unroll
+    for (int e = 0; e < SEG; ++e) {
+      zv[e] = rnd<S, T>(zv[e]);
+      if (e < m) {
+        rz = fma(rv[e], zv[e], rz);
+        rr = fma(rv[e], rv[e], rr);
+      }
+    }
+    acc[0] += (double)rz;
+    acc[1] += (double)rr;
+    store_seg<S, T, SEG>(x + base, m, xv);
+    store_seg<S, T, SEG>(r + base, m, rv);
+    store_seg<S, T, SEG>(z + base, m, zv);
+  RK_SEG_LOOP_END
+  double tot[2];
+  if (grid_reduce<2, 0u>(acc, partials, &sc->ticket, tot)) {
+    const double rz_new = tot[0];
+    sc->beta = rz_new / sc->rz;
+    sc->rz = rz_new;
+    sc->rr = tot[1];
+    sc->iter += 1;
+    if (!isfinite(tot[0]) || !isfinite(tot[1])) {
+      sc->done = 1;
+      sc->status = 5;
+    } else if (tot[1] <= sc->thresh2) {
+      sc->done = 1;
+      sc->status = 0;
+    } else if (sc->iter >= sc->max_iter) {
+      sc->done = 1;
+      sc->status = 4;
+    }
+  }
+}
+
+// Standalone block-Jacobi apply on an FP64 vector: z = D^{-1} round_S(r),
+// returned widened to FP64 (for testing the preconditioner).
+template <typename S, typename T, int BS, int SEG>
+__global__ void __launch_bounds__(kThreads) bj_apply_f64io(HeatGeo g, const double* __restrict__ r,
+                                                           const T* __restrict__ minv, double* __restrict__ z) {
+  __shared__ T sM[2 * BS * BS];
+  load_minv<T, BS>(minv, sM);
+  RK_SEG_LOOP(g, SEG)
+    double rd[SEG];
+    load_seg<double, double, SEG>(r + base, m, rd);
+    T rv[SEG], zv[SEG];
+#pragma unroll
+    for (int e = 0; e < SEG; ++e) rv[e] = (e < m) ? rnd<S, T>((T)rd[e]) : T(0);
+    bj_apply<T, BS, SEG>(sM, g.n, i0, rv, zv);
+    double zd[SEG];
+#pragma unroll
+    for (int e = 0; e < SEG; ++e) zd[e] = (double)rnd<S, T>(zv[e]);
+    store_seg<double, double, SEG>(z + base, m, zd);
+  RK_SEG_LOOP_END
+}
+
+}  // namespace rk

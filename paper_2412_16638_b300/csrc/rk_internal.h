@@ -1,0 +1,159 @@
+// Host-side definitions shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/rk.h"
+#include "rk_device.cuh"
+#include "rk_heat.cuh"
+#include "rk_vec.cuh"
+
+namespace rk {
+
+void set_error(const char* fmt, ...);
+
+#define RK_CUDA(call)                                                                   \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) {                                                            \
+      ::rk::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                      __LINE__);                                                        \
+      return RK_ERR_CUDA;                                                               \
+    }                                                                                   \
+  } while (0)
+
+#define RK_TRY(expr)            \
+  do {                          \
+    rk_status s_ = (expr);      \
+    if (s_ != RK_OK) return s_; \
+  } while (0)
+
+template <typename T> struct Tag { using type = T; };
+template <int V> struct IntC { static constexpr int value = V; };
+
+inline size_t dtype_size(int dt) { return dt == RK_F64 ? 8 : dt == RK_F32 ? 4 : 2; }
+
+// storage x arithmetic dispatch: (f64,f64), (f32,f32), (f16,f32), (bf16,f32)
+template <typename F>
+inline void dispatch_st(int storage, F&& f) {
+  switch (storage) {
+    case RK_F64: f(Tag<double>{}, Tag<double>{}); break;
+    case RK_F32: f(Tag<float>{}, Tag<float>{}); break;
+    case RK_F16: f(Tag<__half>{}, Tag<float>{}); break;
+    default: f(Tag<__nv_bfloat16>{}, Tag<float>{}); break;
+  }
+}
+
+template <typename F>
+inline void dispatch_bs(int bs, F&& f) {
+  switch (bs) {
+    case 1: f(IntC<1>{}); break;
+    case 2: f(IntC<2>{}); break;
+    case 4: f(IntC<4>{}); break;
+    case 8: f(IntC<8>{}); break;
+    case 16: f(IntC<16>{}); break;
+    default: f(IntC<32>{}); break;
+  }
+}
+
+// elements per thread segment for storage S and block size BS
+template <typename S, int BS>
+constexpr int seg_of() {
+  constexpr int v = (sizeof(S) == 2) ? 8 : 4;
+  return BS > v ? BS : v;
+}
+
+int device_sms();
+int grid_for(const void* kernel, long long work_items, int threads = kThreads);
+
+struct MinvEntry {
+  double shift = 0.0;
+  void* dev = nullptr;  // heat: 2*BS*BS values of the arithmetic type;
+                        // CSR: per-block inverses in the storage type
+  bool valid = false;
+};
+
+// CSR operator data (advection-diffusion)
+struct Csr {
+  int* rowptr = nullptr;   // N+1
+  int* cols = nullptr;     // nnz
+  double* v64 = nullptr;   // nnz FP64 values of L
+  void* vS = nullptr;      // nnz values of L * lscale in the storage precision
+  double lscale = 1.0;     // storage scale of L (1 / max |L_ij|)
+  long long nnz = 0;
+};
+
+struct GmresWork;  // defined in rk_csr.cu
+
+}  // namespace rk
+
+struct rk_problem {
+  rk_problem_desc desc{};
+  rk_solver_desc sol{};
+  cudaStream_t st = nullptr;
+  int n = 0;
+  long long N = 0;
+  double h = 0.0, c = 0.0;  // c = kappa/h^2 (heat)
+  // tableau
+  int q = 0;
+  double Ah[64]{}, Al[64]{}, b[8]{};
+  // state
+  double* u = nullptr;
+  double* r = nullptr;
+  double* g64 = nullptr;
+  double* res64 = nullptr;
+  double* k[8]{};
+  void* ke[8]{};
+  bool ke_alias[8]{};
+  // Krylov workspace (storage precision)
+  void* wr = nullptr;
+  void* wz = nullptr;
+  void* wp[2]{};
+  void* wdelta = nullptr;
+  // reductions / device scalars
+  double* partials = nullptr;
+  rk::CgScalars* sc = nullptr;
+  rk::RhsScalars* rs = nullptr;  // [0..7] per stage, [8] scratch solve, [9] refinement
+  rk::CgScalars* h_sc = nullptr; // pinned mirror
+  rk::RhsScalars* h_rs = nullptr;
+  // preconditioner cache
+  rk::MinvEntry minv[8];
+  int minv_next = 0;
+  int last_iters[10]{};
+  bool has_state = false;
+  // CSR path
+  rk::Csr csr;
+  rk::GmresWork* gw = nullptr;
+  size_t bytes = 0;  // device footprint
+};
+
+namespace rk {
+rk_status alloc_dev(rk_problem* p, void** ptr, size_t bytes);
+rk_status get_minv(rk_problem* p, double shift, const void** out);
+// Solve (I - shift L) x = sigma*g with RHS stats in *rs (device).  Result in x
+// (storage precision, scaled by sigma).  Returns iterations in *iters.
+rk_status krylov_solve(rk_problem* p, double shift, const double* g64, RhsScalars* rs, void* x,
+                       int slot, int* iters, int* status);
+// FP64 operator: y = L x; if rs != null also the RHS statistics.
+rk_status op_apply_f64(rk_problem* p, const double* x, double* y, RhsScalars* rs);
+// FP64 correction k = g + shift * L(ke/sigma) and true-residual norm into rs->res2.
+rk_status op_correct_f64(rk_problem* p, double shift, const double* g, const void* ke, double* kout,
+                         RhsScalars* rs);
+rk_status step_impl(rk_problem* p, double dt, rk_stats* acc);
+// CSR path
+rk_status csr_setup(rk_problem* p);
+rk_status csr_free(rk_problem* p);
+rk_status gmres_solve(rk_problem* p, double shift, const double* g64, RhsScalars* rs, void* x, int slot,
+                      int* iters, int* status);
+rk_status csr_precond_f64(rk_problem* p, double shift, const double* r, double* z);
+rk_status csr_apply_f64(rk_problem* p, const double* x, double* y, RhsScalars* rs);
+rk_status csr_correct_f64(rk_problem* p, double shift, const double* g, const void* ke, double* kout,
+                          RhsScalars* rs);
+}  // namespace rk

@@ -1,0 +1,97 @@
+// Element-wise FP64 kernels of the stage loop: stage right-hand sides and the
+// solution update (linear combinations in high precision, Sec. 4.2), plus
+// small helpers (norms, widening, refinement updates).
+#pragma once
+#include "rk_device.cuh"
+#include "rk_heat.cuh"
+
+namespace rk {
+
+constexpr int kMaxStages = 8;
+
+// out = u + sum_j ch[j]*kh[j] + sum_j ce[j]*ke[j]/sigma_j   (FP64 arithmetic)
+// Stage right-hand side r_i = u_n + tau sum_{j<i}(a^h_ij k_j + a^eps_ij k^eps_j)
+// (Eqs. mpAstep1-4) and the update u_{n+1} = u_n + tau sum_j b_j k_j (Eq. RKstep).
+struct CombineArgs {
+  const double* u;
+  const double* kh[kMaxStages];
+  double ch[kMaxStages];
+  const void* ke[kMaxStages];
+  double ce[kMaxStages];
+  const RhsScalars* rs[kMaxStages];
+  int nh, ne;
+  double* out;
+  long long N;
+};
+
+template <typename S>
+__global__ void __launch_bounds__(kThreads) combine_f64(CombineArgs a) {
+  double ce[kMaxStages];
+#pragma unroll
+  for (int j = 0; j < kMaxStages; ++j) ce[j] = (j < a.ne) ? a.ce[j] / a.rs[j]->sigma : 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.N;
+       i += (long long)gridDim.x * blockDim.x) {
+    double v = a.u ? a.u[i] : 0.0;
+#pragma unroll
+    for (int j = 0; j < kMaxStages; ++j)
+      if (j < a.nh) v = fma(a.ch[j], a.kh[j][i], v);
+#pragma unroll
+    for (int j = 0; j < kMaxStages; ++j)
+      if (j < a.ne) v = fma(ce[j], wid<double>(static_cast<const S*>(a.ke[j])[i]), v);
+    a.out[i] = v;
+  }
+}
+
+// ||g||^2, ||g||_inf and the storage scale of an FP64 vector into *rs.
+static __global__ void __launch_bounds__(kThreads) vec_norms_f64(const double* __restrict__ g, long long N,
+                                                                 RhsScalars* rs, double* partials) {
+  double acc[2] = {0.0, 0.0};
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double v = g[i];
+    acc[0] = fma(v, v, acc[0]);
+    acc[1] = fmax(acc[1], fabs(v));
+  }
+  double tot[2];
+  if (grid_reduce<2, 2u>(acc, partials, &rs->ticket, tot)) {
+    rs->gg = tot[0];
+    rs->gmax = tot[1];
+    rs->sigma = (rs->want_scale && tot[1] > 0.0 && isfinite(tot[1])) ? 1.0 / tot[1] : 1.0;
+  }
+}
+
+// out = x / sigma widened to FP64.
+template <typename S>
+__global__ void __launch_bounds__(kThreads) widen_f64(const S* __restrict__ x, const RhsScalars* rs,
+                                                      double* __restrict__ out, long long N) {
+  const double inv = 1.0 / rs->sigma;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = wid<double>(x[i]) * inv;
+}
+
+// x holds sigma_x * k, dx holds sigma_dx * delta: x <- x + (sigma_x/sigma_dx) dx
+// (refinement update of k^eps, arithmetic in FP64).
+template <typename S>
+__global__ void __launch_bounds__(kThreads) add_scaled_inplace(S* __restrict__ x, const S* __restrict__ dx,
+                                                               const RhsScalars* rs_x, const RhsScalars* rs_dx,
+                                                               long long N) {
+  const double f = rs_x->sigma / rs_dx->sigma;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x)
+    x[i] = nar<S>(fma(f, wid<double>(dx[i]), wid<double>(x[i])));
+}
+
+// res = k - ke/sigma (FP64): the true residual of the last stage solve, used
+// as the right-hand side of a refinement solve.
+template <typename S>
+__global__ void __launch_bounds__(kThreads) true_residual_f64(const double* __restrict__ kfull,
+                                                              const S* __restrict__ ke, const RhsScalars* rs,
+                                                              double* __restrict__ res, long long N) {
+  const double inv = 1.0 / rs->sigma;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x)
+    res[i] = kfull[i] - wid<double>(ke[i]) * inv;
+}
+
+}  // namespace rk

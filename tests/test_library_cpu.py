@@ -1,0 +1,65 @@
+"""The C-ABI library without a GPU: it loads, exports every entry point that
+include/rk.h declares, and rejects bad descriptors before any CUDA call."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def rk():
+    from paper_2412_16638_b300.build import build
+    build()
+    import paper_2412_16638_b300 as mod
+    return mod
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "rk.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(rk_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(rk):
+    names = declared_symbols()
+    assert len(names) >= 18
+    lib = ctypes.CDLL(rk.LIB_PATH)
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(rk.EXPORTED)
+    assert "sm_103a" in rk.rk_version()
+
+
+def test_argument_checks_without_gpu(rk):
+    h = ctypes.c_void_p()
+    d = rk.problem_desc(n=0)
+    s = rk.solver_desc()
+    assert rk._lib.rk_create_problem(ctypes.byref(d), ctypes.byref(s), None, ctypes.byref(h)) == rk.RK_ERR_ARG
+    assert "n must be" in rk.rk_last_error()
+    d = rk.problem_desc(n=8)
+    s = rk.solver_desc(bj_block=3)
+    assert rk._lib.rk_create_problem(ctypes.byref(d), ctypes.byref(s), None, ctypes.byref(h)) == rk.RK_ERR_ARG
+    assert "bj_block" in rk.rk_last_error()
+    s = rk.solver_desc(storage="f16", arith=rk.RK_F64)
+    assert rk._lib.rk_create_problem(ctypes.byref(d), ctypes.byref(s), None, ctypes.byref(h)) == rk.RK_ERR_ARG
+    d = rk.problem_desc(op=rk.RK_OP_ADVDIFF_CSR, n=8)
+    s = rk.solver_desc(krylov=rk.RK_KRYLOV_GMRES)
+    assert rk._lib.rk_create_problem(ctypes.byref(d), ctypes.byref(s), None, ctypes.byref(h)) == rk.RK_ERR_ARG
+    assert "kappa_field" in rk.rk_last_error()
+    assert rk._lib.rk_step(None, 1e-3, None) == rk.RK_ERR_ARG
+    assert rk._lib.rk_destroy_problem(None) == rk.RK_ERR_ARG
+
+
+def test_package_tableaux_match_oracle(rk):
+    """The library's tableau table and the oracle's are typed independently
+    from the paper; they must agree."""
+    from oracle import tableau
+    for name in rk.tableaux.PRESETS:
+        mine = [np.array(x) for x in rk.tableaux.get(name)]
+        ref = tableau.get(name)
+        for a, b in zip(mine, ref):
+            np.testing.assert_allclose(a, b, rtol=0, atol=1e-15)
