@@ -45,9 +45,11 @@ class BlockJacobi:
             by_size.setdefault(m, []).append(off)
         for m, offs in by_size.items():
             starts = (np.arange(nlines)[:, None] * n + np.array(offs)[None, :]).ravel()
+            rows = starts[:, None] + np.arange(m)[None, :]
             blocks = np.empty((starts.size, m, m))
-            for b, s0 in enumerate(starts):
-                blocks[b] = Mc[s0:s0 + m, s0:s0 + m].toarray()
+            for a in range(m):          # entry (a, b) of every block at once
+                for b in range(m):
+                    blocks[:, a, b] = np.asarray(Mc[rows[:, a], rows[:, b]]).ravel()
             inv = np.linalg.inv(blocks)  # LU with partial pivoting per block
             self.groups.append((m, starts, inv))
 
