@@ -1,0 +1,379 @@
+"""Benchmark: mixed-precision perturbed DIRK steps of the 3D heat equation on B300.
+
+One step = one pass of the whole stage loop (stage right-hand sides, FP64
+operator, low-precision block-Jacobi CG solve, FP64 explicit correction and
+true residual, FP64 update) over the workload below.
+
+Default workload (heat256): kappa = 1 on the 256^3 interior grid, u0 = unit
+sine mode + 32 seeded random low modes (amplitudes N(0, 0.1^2)), Grant's
+method 4s3pB, dt = 1e-3, FP32 storage/arithmetic CG with x-line block-Jacobi
+(8), tol_rel 1e-6; FP64 correction and update.  The plain FP64 DIRK step of
+the same problem is timed beside it.
+
+Metric: DOF*steps/s = n^3 * steps / seconds (device time, CUDA events on the
+library's stream), inputs resident in HBM, working set (> 1.5 GB) larger than
+L2.  Usage:
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank runs an independent replica on its own GPU (the
+single problem does not shard): value = total DOF*steps over all ranks / the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "DOF*steps/s"
+WORKLOADS = {
+    "heat256": dict(n=256, kappa=1.0, tableau="4s3pB", dt=1e-3, bs=8, tol=1e-6, storage="f32"),
+    "heat128": dict(n=128, kappa=1.0, tableau="4s3pB", dt=1e-3, bs=8, tol=1e-6, storage="f32"),
+}
+HBM_FALLBACK_GBS = 6400.0
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def ncu_traffic(kernel, workload):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, or None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        e = d[workload][kernel]
+        return float(e["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.lines, self.proc = index, [], None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(self.index)],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=2)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def closed_form(n, kappa, dt, steps, tab, modes):
+    """Exact fully discrete solution sum_m a_m R(dt lambda_m)^steps phi_m and the
+    continuous solution sum_m a_m exp(lambda^c_m t) phi_m (written out here
+    from the sine-mode eigenvalues; not the library, not the oracle)."""
+    A = np.array(tab[0]) + np.array(tab[1])
+    b = np.array(tab[2])
+    q = len(b)
+    h = 1.0 / (n + 1)
+    disc = np.zeros(n ** 3)
+    cont = np.zeros(n ** 3)
+    for a, kx, ky, kz in modes:
+        lam = -4.0 * kappa / h ** 2 * sum(math.sin(k * math.pi * h / 2) ** 2 for k in (kx, ky, kz))
+        z = dt * lam
+        R = 1.0 + z * (b @ np.linalg.solve(np.eye(q) - z * A, np.ones(q)))
+        phi = synth.sine_mode(n, kx, ky, kz)
+        disc += a * R ** steps * phi
+        cont += a * math.exp(-math.pi ** 2 * kappa * (kx * kx + ky * ky + kz * kz) * dt * steps) * phi
+    return disc, cont
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def oracle_step_seconds(cfg, iters_per_step):
+    """Oracle (float64 numpy, one thread) cost of one step of the workload.
+
+    Bounded sample: after the oracle's setup (excluded, as for the GPU), one
+    step is run with every stage solve capped at 1 CG iteration and once with
+    2; the difference gives the cost per iteration and the remainder the
+    per-step cost outside the iterations; the step time is extrapolated to
+    `iters_per_step` iterations.  Returns (seconds per step, sample text)."""
+    from threadpoolctl import threadpool_limits
+
+    from oracle import dirk, operators, tableau
+
+    with threadpool_limits(1):
+        n = cfg["n"]
+        op = operators.HeatOperator(n, cfg["kappa"])
+        tab = tableau.get(cfg["tableau"])
+        u0 = synth.heat_modes(seed=0).evaluate(n)
+        solver = dirk.Solver("cg", bs=cfg["bs"], tol_rel=cfg["tol"], max_iter=1)
+        shifts = sorted({cfg["dt"] * a for a in np.diag(tab[1]) if a != 0.0})
+        for s in shifts:  # preconditioner setup, untimed
+            solver.solve(op, s, np.zeros(n ** 3))
+        nsolves = int(np.count_nonzero(np.diag(tab[1])))
+        times = {}
+        for cap in (1, 2):
+            solver.max_iter = cap
+            t0 = time.perf_counter()
+            dirk.rk_step(u0, cfg["dt"], tab, op, solver)
+            times[cap] = time.perf_counter() - t0
+    per_iter = max((times[2] - times[1]) / nsolves, 1e-9)
+    fixed = max(times[1] - nsolves * per_iter, 0.0)
+    sample = ("oracle float64 numpy, 1 thread: one %d^3 step with each of the %d stage solves capped at 1 and "
+              "at 2 CG iterations (%.1f s, %.1f s); per-iteration %.3f s and per-step %.2f s extrapolated to %.1f "
+              "iterations per step" % (n, nsolves, times[1], times[2], per_iter, fixed, iters_per_step))
+    return fixed + iters_per_step * per_iter, sample
+
+
+def run_reference(args, cfg):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    ipath = os.path.join(ROOT, "profiles", "traffic.json")
+    iters = None
+    try:
+        with open(ipath) as f:
+            iters = float(json.load(f)[args.workload]["iters_per_step"])
+    except Exception:
+        iters = 240.0
+    t_step, sample = oracle_step_seconds(cfg, iters)
+    N = cfg["n"] ** 3
+    value = N / t_step
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "DOF*steps/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args.workload, cfg),
+        "cpu_baseline": {"value": value, "unit": "DOF*steps/s", "cores": 1, "kind": "oracle",
+                         "sample": sample + " (iterations per step from profiles/traffic.json)"},
+        "e2e": {"value": value, "unit": "DOF*steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def workload_config(name, cfg):
+    return {"workload": name, "grid": "%d^3" % cfg["n"], "dof": cfg["n"] ** 3, "kappa": cfg["kappa"],
+            "tableau": cfg["tableau"], "dt": cfg["dt"], "krylov": "cg", "bj_block": cfg["bs"],
+            "tol_rel": cfg["tol"], "storage": cfg["storage"], "arith": "f32", "high_precision": "f64",
+            "u0": "sine mode + 32 random modes (seed 0)", "l2": "working set > L2 (no flush needed)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="heat256", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
+    args = ap.parse_args()
+    cfg = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, cfg)
+
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2412_16638_b300 as rk
+
+    n, dt = cfg["n"], cfg["dt"]
+    N = n ** 3
+    modes = synth.heat_modes(seed=0).modes
+    u0 = synth.ModeSum(modes).evaluate(n)
+    tab = rk.tableaux.get(cfg["tableau"])
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+
+    def make(storage, tol, correct):
+        return rk.Problem(rk.problem_desc(n=n, kappa=cfg["kappa"]),
+                          rk.solver_desc(bj_block=cfg["bs"], tol_rel=tol, storage=storage, correct=correct,
+                                         max_iter=2000),
+                          tableau=tab, u0=u0, stream=sptr)
+
+    # ---------------- mixed-precision path, device-resident inputs
+    p = make(cfg["storage"], cfg["tol"], 1)
+    rk.rk_integrate(p.h, dt, args.warmup)
+    rk.rk_profile(p.h, True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    st = rk.rk_integrate(p.h, dt, args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    prof, launches = rk.rk_profile_read(p.h)
+    rk.rk_profile(p.h, False)
+    secs = e0.elapsed_time(e1) / 1e3
+    if dist is not None:
+        t = torch.tensor([secs], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        secs = float(t.item())
+    value = world * N * args.steps / secs
+    iters_per_step = st.iters_total / args.steps
+    u = p.state()
+    disc, cont = closed_form(n, cfg["kappa"], dt, args.warmup + args.steps, tab, modes)
+    err_disc, err_cont = rel(u, disc), rel(u, cont)
+
+    # ---------------- end to end through the public API: host state in/out every step
+    hin = torch.from_numpy(u0.copy()).pin_memory()
+    hout = torch.empty(N, dtype=torch.float64).pin_memory()
+    k_e2e = max(1, min(args.steps, 10))
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        rk.rk_set_state(p.h, hin)
+        rk.rk_step(p.h, dt)
+        rk.rk_get_state(p.h, hout)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_secs = time.perf_counter() - t0
+    e2e_value = world * N * k_e2e / e2e_secs
+    p.close()
+
+    # ---------------- roofline of the dominant kernel
+    peak, peak_kind = measured_peaks()
+    dom = max(prof.items(), key=lambda kv: kv[1]["ms_total"])
+    dname, d = dom
+    achieved = d["bytes_total"] / (d["ms_total"] / 1e3) / 1e9
+    kernels = {k: {"launches": v["launches"], "noop_launches": v["noop_launches"],
+                   "ms_total": round(v["ms_total"], 3),
+                   "avg_us": round(1e3 * v["ms_total"] / max(v["launches"], 1), 2),
+                   "GBps": round(v["bytes_total"] / max(v["ms_total"], 1e-9) / 1e6, 1),
+                   "share": round(v["ms_total"] / sum(x["ms_total"] for x in prof.values()), 4)}
+               for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms_total"])}
+    traffic = ncu_traffic(dname, args.workload)
+    roofline = {"bound": "hbm", "kernel": dname, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+                "traffic": traffic,
+                "bytes_per_launch": d["bytes_total"] / max(d["launches"], 1),
+                "avg_launch_us": 1e3 * d["ms_total"] / max(d["launches"], 1)}
+
+    # ---------------- plain FP64 DIRK step of the same problem
+    fp64 = None
+    if not args.no_fp64:
+        q = make("f64", cfg["tol"], 0)
+        rk.rk_integrate(q.h, dt, 1)
+        k64 = max(2, args.steps // 4)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        s64 = rk.rk_integrate(q.h, dt, k64)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        sec64 = f0.elapsed_time(f1) / 1e3
+        u64 = q.state()
+        q.close()
+        d64, c64 = closed_form(n, cfg["kappa"], dt, 1 + k64, tab, modes)
+        fp64 = {"value": N * k64 / sec64, "ms_per_step": 1e3 * sec64 / k64, "steps": k64,
+                "iters_per_step": s64.iters_total / k64, "err_vs_discrete": rel(u64, d64),
+                "err_vs_continuous": rel(u64, c64)}
+
+    # ---------------- oracle on the host cores
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        t_step, sample = oracle_step_seconds(cfg, iters_per_step)
+        cpu = {"value": N / t_step, "unit": "DOF*steps/s", "cores": 1, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "DOF*steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(workload_config(args.workload, cfg), parallelism="replicas" if world > 1 else "single"),
+            "e2e": {"value": e2e_value, "unit": "DOF*steps/s", "h2d_bytes_per_step": 8 * N,
+                    "d2h_bytes_per_step": 8 * N, "steps": k_e2e},
+            "gpu_launches": launches,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "iters_per_step": iters_per_step,
+            "true_res_max": st.true_res,
+            "err_vs_discrete": err_disc,
+            "err_vs_continuous": err_cont,
+            "fp64_plain": fp64,
+            "speedup_vs_fp64": (value / world / fp64["value"]) if fp64 else None,
+            "kernels": kernels,
+        }
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -181,6 +181,28 @@ rk_status rk_wait_job(rk_server* s, uint64_t job_id, double* u_out, rk_stats* st
 
 rk_status rk_server_destroy(rk_server* s);
 
+/* ---- profiling: CUDA events around every kernel launch of a problem ------ */
+
+typedef struct {
+  char name[32];           /* kernel name                                       */
+  long long launches;      /* launches that did work                            */
+  long long noop_launches; /* sweeps launched after their solve had finished     */
+  double ms_total;         /* summed event time of the working launches          */
+  double bytes_total;      /* algorithmic bytes (compulsory HBM traffic) of the
+                              working launches: every vector element the kernel
+                              must read or write once                            */
+} rk_kernel_stat;
+
+/* enable = 1: record a CUDA event pair on the problem's stream around every
+ * kernel launch from now on; 0: stop.  Either way the counters are cleared. */
+rk_status rk_profile(rk_problem* p, int enable);
+
+/* Synchronise the problem's stream and return per-kernel totals since the
+ * last rk_profile() call (up to max entries; *count = entries written) and
+ * the number of kernel launches the problem issued (profiled or not). */
+rk_status rk_profile_read(rk_problem* p, rk_kernel_stat* out, int max, int* count,
+                          long long* launches_total);
+
 /* Thread-local description of the last error on this thread ("" if none). */
 const char* rk_last_error(void);
 

@@ -52,6 +52,11 @@ class rk_stats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class rk_kernel_stat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_longlong), ("noop_launches", ctypes.c_longlong),
+                ("ms_total", ctypes.c_double), ("bytes_total", ctypes.c_double)]
+
+
 _P = ctypes.c_void_p
 _D = ctypes.c_double
 _I = ctypes.c_int
@@ -74,6 +79,8 @@ _SIGS = {
     "rk_poll_job": [_P, ctypes.c_uint64, ctypes.POINTER(_I)],
     "rk_wait_job": [_P, ctypes.c_uint64, _P, ctypes.POINTER(rk_stats), _DP],
     "rk_server_destroy": [_P],
+    "rk_profile": [_P, _I],
+    "rk_profile_read": [_P, ctypes.POINTER(rk_kernel_stat), _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_longlong)],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -255,6 +262,26 @@ def rk_wait_job(server, job_id, u_out=None, allow_not_converged=False):
 
 def rk_server_destroy(server):
     return _check(_lib.rk_server_destroy(server))
+
+
+def rk_profile(p, enable=True):
+    return _check(_lib.rk_profile(p, 1 if enable else 0))
+
+
+def rk_profile_read(p):
+    """Per-kernel totals since the last rk_profile() call, and the number of
+    kernel launches issued: ({name: {launches, noop_launches, ms_total,
+    bytes_total}}, launches_total)."""
+    buf = (rk_kernel_stat * 64)()
+    cnt = ctypes.c_int()
+    tot = ctypes.c_longlong()
+    _check(_lib.rk_profile_read(p, buf, 64, ctypes.byref(cnt), ctypes.byref(tot)))
+    out = {}
+    for i in range(cnt.value):
+        b = buf[i]
+        out[b.name.decode()] = {"launches": b.launches, "noop_launches": b.noop_launches,
+                                "ms_total": b.ms_total, "bytes_total": b.bytes_total}
+    return out, tot.value
 
 
 class Problem:

@@ -155,7 +155,8 @@ rk_status op_apply_f64(rk_problem* p, const double* x, double* y, RhsScalars* rs
   HeatGeo g = heat_geo(p, SEG);
   auto kern = heat_apply_f64<SEG>;
   int grid = grid_for((const void*)kern, g.n2 * g.nseg);
-  kern<<<grid, kThreads, 0, p->st>>>(g, x, y, -6.0 * p->c, p->c, rs, p->partials);
+  launch(p, K_OP, 16.0 * p->N,
+         [&] { kern<<<grid, kThreads, 0, p->st>>>(g, x, y, -6.0 * p->c, p->c, rs, p->partials); });
   RK_CUDA(cudaGetLastError());
   return RK_OK;
 }
@@ -170,7 +171,9 @@ rk_status op_correct_f64(rk_problem* p, double shift, const double* gv, const vo
     using S = typename decltype(ts)::type;
     auto kern = heat_correct_f64<S, SEG>;
     int grid = grid_for((const void*)kern, g.n2 * g.nseg);
-    kern<<<grid, kThreads, 0, p->st>>>(g, gv, static_cast<const S*>(ke), shift * p->c, kout, rs, p->partials);
+    launch(p, K_CORRECT, (16.0 + sizeof(S)) * p->N, [&] {
+      kern<<<grid, kThreads, 0, p->st>>>(g, gv, static_cast<const S*>(ke), shift * p->c, kout, rs, p->partials);
+    });
     if (cudaGetLastError() != cudaSuccess) st = RK_ERR_CUDA;
   });
   if (st != RK_OK) set_error("heat_correct_f64 launch failed");
@@ -210,7 +213,10 @@ static rk_status heat_cg_solve(rk_problem* p, double shift, const double* g64, R
       auto kb = cg_sweep_b<S, T, BS, SEG>;
       const int gi = grid_for((const void*)ki, work), ga = grid_for((const void*)ka, work),
                 gb = grid_for((const void*)kb, work);
-      ki<<<gi, kThreads, 0, p->st>>>(g, g64, rs, M, r, z, xs, p->sc, p->partials);
+      const double Ns = (double)p->N * sizeof(S);
+      const int solve = ++p->solve_seq;
+      launch(p, K_CG_INIT, 8.0 * p->N + 3.0 * Ns,
+             [&] { ki<<<gi, kThreads, 0, p->st>>>(g, g64, rs, M, r, z, xs, p->sc, p->partials); });
       int launched = 0, cur = 0;
       const int predicted = p->last_iters[slot] > 0 ? p->last_iters[slot] : 8;
       int chunk = std::max(2, predicted - 1);
@@ -218,8 +224,13 @@ static rk_status heat_cg_solve(rk_problem* p, double shift, const double* g64, R
         for (int c = 0; c < chunk; ++c) {
           S* pn = static_cast<S*>(p->wp[cur]);
           const S* po = static_cast<const S*>(p->wp[cur ^ 1]);
+          const int idx = launched + c;
+          prof_begin(p, K_CG_A, (idx == 0 ? 2.0 : 3.0) * Ns, solve, idx);
           ka<<<ga, kThreads, 0, p->st>>>(g, d, o, z, po, pn, p->sc, p->partials);
+          prof_end(p);
+          prof_begin(p, K_CG_B, (idx == 0 ? 5.0 : 6.0) * Ns, solve, idx);
           kb<<<gb, kThreads, 0, p->st>>>(g, d, o, pn, xs, r, z, M, p->sc, p->partials);
+          prof_end(p);
           cur ^= 1;
         }
         launched += chunk;
@@ -234,7 +245,10 @@ static rk_status heat_cg_solve(rk_problem* p, double shift, const double* g64, R
           set_error("CG status readback failed: %s", cudaGetErrorString(cudaGetLastError()));
           return;
         }
-        if (p->h_sc->done) break;
+        if (p->h_sc->done) {
+          prof_finish_solve(p, solve, p->h_sc->iter);
+          break;
+        }
         if (launched > p->sol.max_iter + 4) {  // the device caps iterations itself
           st = RK_ERR_TIMEOUT;
           set_error("CG did not stop after %d sweeps", launched);
@@ -270,7 +284,8 @@ static rk_status launch_combine(rk_problem* p, const CombineArgs& a) {
     using S = typename decltype(ts)::type;
     auto kern = combine_f64<S>;
     int grid = grid_for((const void*)kern, a.N);
-    kern<<<grid, kThreads, 0, p->st>>>(a);
+    const double bytes = (double)a.N * ((a.u ? 8.0 : 0.0) + 8.0 * a.nh + (double)sizeof(S) * a.ne + 8.0);
+    launch(p, K_COMBINE, bytes, [&] { kern<<<grid, kThreads, 0, p->st>>>(a); });
     if (cudaGetLastError() != cudaSuccess) st = RK_ERR_CUDA;
   });
   if (st != RK_OK) set_error("combine launch failed");
@@ -361,12 +376,16 @@ rk_status step_impl(rk_problem* p, double dt, rk_stats* acc) {
         RK_TRY(launch_typed(p, [&](auto ts) {
           using S = typename decltype(ts)::type;
           auto kern = true_residual_f64<S>;
-          kern<<<grid_for((const void*)kern, p->N), kThreads, 0, p->st>>>(
-              p->k[i], static_cast<const S*>(p->ke[i]), rs, p->res64, p->N);
+          launch(p, K_TRUERES, (16.0 + sizeof(S)) * p->N, [&] {
+            kern<<<grid_for((const void*)kern, p->N), kThreads, 0, p->st>>>(
+                p->k[i], static_cast<const S*>(p->ke[i]), rs, p->res64, p->N);
+          });
         }));
         {
           auto kern = vec_norms_f64;
-          kern<<<grid_for((const void*)kern, p->N), kThreads, 0, p->st>>>(p->res64, p->N, rsd, p->partials);
+          launch(p, K_NORMS, 8.0 * p->N, [&] {
+            kern<<<grid_for((const void*)kern, p->N), kThreads, 0, p->st>>>(p->res64, p->N, rsd, p->partials);
+          });
           RK_CUDA(cudaGetLastError());
         }
         int it2 = 0, st2 = 0;
@@ -378,8 +397,10 @@ rk_status step_impl(rk_problem* p, double dt, rk_stats* acc) {
         RK_TRY(launch_typed(p, [&](auto ts) {
           using S = typename decltype(ts)::type;
           auto kern = add_scaled_inplace<S>;
-          kern<<<grid_for((const void*)kern, p->N), kThreads, 0, p->st>>>(
-              static_cast<S*>(p->ke[i]), static_cast<const S*>(p->wdelta), rs, rsd, p->N);
+          launch(p, K_ADDSCALED, 3.0 * sizeof(S) * p->N, [&] {
+            kern<<<grid_for((const void*)kern, p->N), kThreads, 0, p->st>>>(
+                static_cast<S*>(p->ke[i]), static_cast<const S*>(p->wdelta), rs, rsd, p->N);
+          });
         }));
         RK_TRY(op_correct_f64(p, shift, p->g64, p->ke[i], p->k[i], rs));
       }
@@ -387,8 +408,10 @@ rk_status step_impl(rk_problem* p, double dt, rk_stats* acc) {
       RK_TRY(launch_typed(p, [&](auto ts) {
         using S = typename decltype(ts)::type;
         auto kern = widen_f64<S>;
-        kern<<<grid_for((const void*)kern, p->N), kThreads, 0, p->st>>>(static_cast<const S*>(p->ke[i]), rs,
-                                                                         p->k[i], p->N);
+        launch(p, K_WIDEN, (8.0 + sizeof(S)) * p->N, [&] {
+          kern<<<grid_for((const void*)kern, p->N), kThreads, 0, p->st>>>(static_cast<const S*>(p->ke[i]), rs,
+                                                                           p->k[i], p->N);
+        });
       }));
     }
   }
@@ -486,6 +509,7 @@ static void free_problem(rk_problem* p) {
   if (p->h_sc) cudaFreeHost(p->h_sc);
   if (p->h_rs) cudaFreeHost(p->h_rs);
   csr_free(p);
+  prof_free(p);
   delete p;
 }
 
@@ -743,7 +767,8 @@ rk_status rk_solve(rk_problem* p, double shift, const double* g, double* k, int 
   RhsScalars* rs = p->rs + 8;
   {
     auto kern = vec_norms_f64;
-    kern<<<grid_for((const void*)kern, p->N), kThreads, 0, p->st>>>(p->g64, p->N, rs, p->partials);
+    launch(p, K_NORMS, 8.0 * p->N,
+           [&] { kern<<<grid_for((const void*)kern, p->N), kThreads, 0, p->st>>>(p->g64, p->N, rs, p->partials); });
     RK_CUDA(cudaGetLastError());
   }
   // solve into the delta workspace (storage precision), then widen
@@ -754,8 +779,10 @@ rk_status rk_solve(rk_problem* p, double shift, const double* g, double* k, int 
   RK_TRY(launch_typed(p, [&](auto ts) {
     using S = typename decltype(ts)::type;
     auto kern = widen_f64<S>;
-    kern<<<grid_for((const void*)kern, p->N), kThreads, 0, p->st>>>(static_cast<const S*>(p->wdelta), rs, kout,
-                                                                     p->N);
+    launch(p, K_WIDEN, (8.0 + sizeof(S)) * p->N, [&] {
+      kern<<<grid_for((const void*)kern, p->N), kThreads, 0, p->st>>>(static_cast<const S*>(p->wdelta), rs, kout,
+                                                                       p->N);
+    });
   }));
   if (!is_device_ptr) RK_CUDA(cudaMemcpyAsync(k, kout, bytes, cudaMemcpyDeviceToHost, p->st));
   RK_CUDA(cudaStreamSynchronize(p->st));
@@ -802,8 +829,10 @@ rk_status rk_apply_precond(rk_problem* p, double shift, const double* r, double*
         constexpr int SEG = seg_of<S, BS>();
         HeatGeo g = heat_geo(p, SEG);
         auto kern = bj_apply_f64io<S, T, BS, SEG>;
-        kern<<<grid_for((const void*)kern, g.n2 * g.nseg), kThreads, 0, p->st>>>(g, rin, static_cast<const T*>(minv),
-                                                                                  zout);
+        launch(p, K_BJ, 16.0 * p->N, [&] {
+          kern<<<grid_for((const void*)kern, g.n2 * g.nseg), kThreads, 0, p->st>>>(
+              g, rin, static_cast<const T*>(minv), zout);
+        });
         if (cudaGetLastError() != cudaSuccess) lst = RK_ERR_CUDA;
       });
     });

@@ -92,6 +92,30 @@ struct Csr {
 
 struct GmresWork;  // defined in rk_csr.cu
 
+// Kernel ids for the launch profiler.
+enum Kid {
+  K_CG_INIT, K_CG_A, K_CG_B, K_OP, K_CORRECT, K_COMBINE, K_NORMS, K_WIDEN, K_TRUERES, K_ADDSCALED, K_BJ,
+  K_CSR_SPMV, K_CSR_CORRECT, K_CSR_BJ_SETUP, K_GM_INIT, K_GM_ARNOLDI, K_GM_ORTH, K_GM_NORM, K_GM_UPDATE,
+  K_GM_PREC, K_BATCH, K_COUNT
+};
+extern const char* const kKernelNames[K_COUNT];
+
+struct ProfRec {
+  int kid;
+  double bytes;
+  cudaEvent_t a, b;
+  int solve, idx;
+  bool noop;
+};
+
+struct Prof {
+  bool on = false;
+  std::vector<ProfRec> pending;
+  std::vector<cudaEvent_t> pool;
+  long long n[K_COUNT]{}, noop[K_COUNT]{};
+  double ms[K_COUNT]{}, bytes[K_COUNT]{};
+};
+
 }  // namespace rk
 
 struct rk_problem {
@@ -132,6 +156,10 @@ struct rk_problem {
   rk::Csr csr;
   rk::GmresWork* gw = nullptr;
   size_t bytes = 0;  // device footprint
+  // launch accounting / profiler
+  long long launches = 0;
+  rk::Prof* prof = nullptr;
+  int solve_seq = 0;
 };
 
 namespace rk {
@@ -147,6 +175,19 @@ rk_status op_apply_f64(rk_problem* p, const double* x, double* y, RhsScalars* rs
 rk_status op_correct_f64(rk_problem* p, double shift, const double* g, const void* ke, double* kout,
                          RhsScalars* rs);
 rk_status step_impl(rk_problem* p, double dt, rk_stats* acc);
+// Launch accounting: count the launch and, when profiling, bracket it with
+// CUDA events.  solve/idx tag Krylov sweeps so launches issued after their
+// solve converged can be marked as no-ops (prof_finish_solve).
+void prof_begin(rk_problem* p, int kid, double bytes, int solve = -1, int idx = -1);
+void prof_end(rk_problem* p);
+void prof_finish_solve(rk_problem* p, int solve, int iters);
+void prof_free(rk_problem* p);
+template <typename F>
+inline void launch(rk_problem* p, int kid, double bytes, F&& f) {
+  prof_begin(p, kid, bytes);
+  f();
+  prof_end(p);
+}
 // CSR path
 rk_status csr_setup(rk_problem* p);
 rk_status csr_free(rk_problem* p);

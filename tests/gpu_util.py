@@ -8,8 +8,7 @@ def require_gpu():
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    from paper_2412_16638_b300.build import build
-    build()
+    _load_build().build()
     import paper_2412_16638_b300 as rk
     return rk
 
@@ -21,3 +20,18 @@ def rel_l2(a, b):
 def rng_vec(n, seed):
     """Seeded test vector (numpy's PCG64; input only)."""
     return np.random.default_rng(seed).standard_normal(n ** 3)
+
+
+def _load_build():
+    """The build module, loaded by file path so that building never imports
+    a stale copy of the library."""
+    import importlib.util
+    import os
+    here = os.path.dirname(os.path.abspath(__file__))
+    path = os.path.join(here, "paper_2412_16638_b300", "build.py")
+    if not os.path.exists(path):
+        path = os.path.join(os.path.dirname(here), "paper_2412_16638_b300", "build.py")
+    spec = importlib.util.spec_from_file_location("_rk_build", path)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod

@@ -12,8 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 @pytest.fixture(scope="module")
 def rk():
-    from paper_2412_16638_b300.build import build
-    build()
+    _load_build().build()
     import paper_2412_16638_b300 as mod
     return mod
 
@@ -63,3 +62,18 @@ def test_package_tableaux_match_oracle(rk):
         ref = tableau.get(name)
         for a, b in zip(mine, ref):
             np.testing.assert_allclose(a, b, rtol=0, atol=1e-15)
+
+
+def _load_build():
+    """The build module, loaded by file path so that building never imports
+    a stale copy of the library."""
+    import importlib.util
+    import os
+    here = os.path.dirname(os.path.abspath(__file__))
+    path = os.path.join(here, "paper_2412_16638_b300", "build.py")
+    if not os.path.exists(path):
+        path = os.path.join(os.path.dirname(here), "paper_2412_16638_b300", "build.py")
+    spec = importlib.util.spec_from_file_location("_rk_build", path)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
