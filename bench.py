@@ -149,7 +149,13 @@ def oracle_step_seconds(cfg, iters_per_step):
     2; the difference gives the cost per iteration and the remainder the
     per-step cost outside the iterations; the step time is extrapolated to
     `iters_per_step` iterations.  Returns (seconds per step, sample text)."""
-    from threadpoolctl import threadpool_limits
+    try:
+        from threadpoolctl import threadpool_limits
+    except ImportError:  # numpy's element-wise kernels are single-threaded anyway
+        import contextlib
+
+        def threadpool_limits(_):
+            return contextlib.nullcontext()
 
     from oracle import dirk, operators, tableau
 

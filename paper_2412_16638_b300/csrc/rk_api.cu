@@ -168,11 +168,11 @@ rk_status op_correct_f64(rk_problem* p, double shift, const double* gv, const vo
   HeatGeo g = heat_geo(p, SEG);
   rk_status st = RK_OK;
   dispatch_st(p->sol.storage, [&](auto ts, auto) {
-    using S = typename decltype(ts)::type;
-    auto kern = heat_correct_f64<S, SEG>;
+    using X = typename XOf<typename decltype(ts)::type>::type;
+    auto kern = heat_correct_f64<X, SEG>;
     int grid = grid_for((const void*)kern, g.n2 * g.nseg);
-    launch(p, K_CORRECT, (16.0 + sizeof(S)) * p->N, [&] {
-      kern<<<grid, kThreads, 0, p->st>>>(g, gv, static_cast<const S*>(ke), shift * p->c, kout, rs, p->partials);
+    launch(p, K_CORRECT, (16.0 + sizeof(X)) * p->N, [&] {
+      kern<<<grid, kThreads, 0, p->st>>>(g, gv, static_cast<const X*>(ke), shift * p->c, kout, rs, p->partials);
     });
     if (cudaGetLastError() != cudaSuccess) st = RK_ERR_CUDA;
   });
@@ -206,7 +206,8 @@ static rk_status heat_cg_solve(rk_problem* p, double shift, const double* g64, R
       const T d = (T)(1.0 + 6.0 * shift * p->c), o = (T)(-shift * p->c);
       S* r = static_cast<S*>(p->wr);
       S* z = static_cast<S*>(p->wz);
-      S* xs = static_cast<S*>(x);
+      using X = typename XOf<S>::type;
+      X* xs = static_cast<X*>(x);
       const T* M = static_cast<const T*>(minv);
       auto ki = cg_init<S, T, BS, SEG>;
       auto ka = cg_sweep_a<S, T, SEG>;
@@ -215,7 +216,8 @@ static rk_status heat_cg_solve(rk_problem* p, double shift, const double* g64, R
                 gb = grid_for((const void*)kb, work);
       const double Ns = (double)p->N * sizeof(S);
       const int solve = ++p->solve_seq;
-      launch(p, K_CG_INIT, 8.0 * p->N + 3.0 * Ns,
+      const double Nx = (double)p->N * sizeof(X);
+      launch(p, K_CG_INIT, 8.0 * p->N + 2.0 * Ns + Nx,
              [&] { ki<<<gi, kThreads, 0, p->st>>>(g, g64, rs, M, r, z, xs, p->sc, p->partials); });
       int launched = 0, cur = 0;
       const int predicted = p->last_iters[slot] > 0 ? p->last_iters[slot] : 8;
@@ -228,7 +230,7 @@ static rk_status heat_cg_solve(rk_problem* p, double shift, const double* g64, R
           prof_begin(p, K_CG_A, (idx == 0 ? 2.0 : 3.0) * Ns, solve, idx);
           ka<<<ga, kThreads, 0, p->st>>>(g, d, o, z, po, pn, p->sc, p->partials);
           prof_end(p);
-          prof_begin(p, K_CG_B, (idx == 0 ? 5.0 : 6.0) * Ns, solve, idx);
+          prof_begin(p, K_CG_B, (idx == 0 ? 4.0 * Ns + Nx : 4.0 * Ns + 2.0 * Nx), solve, idx);
           kb<<<gb, kThreads, 0, p->st>>>(g, d, o, pn, xs, r, z, M, p->sc, p->partials);
           prof_end(p);
           cur ^= 1;
@@ -281,7 +283,7 @@ rk_status krylov_solve(rk_problem* p, double shift, const double* g64, RhsScalar
 static rk_status launch_combine(rk_problem* p, const CombineArgs& a) {
   rk_status st = RK_OK;
   dispatch_st(p->sol.storage, [&](auto ts, auto) {
-    using S = typename decltype(ts)::type;
+    using S = typename XOf<typename decltype(ts)::type>::type;
     auto kern = combine_f64<S>;
     int grid = grid_for((const void*)kern, a.N);
     const double bytes = (double)a.N * ((a.u ? 8.0 : 0.0) + 8.0 * a.nh + (double)sizeof(S) * a.ne + 8.0);
@@ -296,8 +298,8 @@ template <typename F>
 static rk_status launch_typed(rk_problem* p, F&& f) {
   rk_status st = RK_OK;
   dispatch_st(p->sol.storage, [&](auto ts, auto) {
-    using S = typename decltype(ts)::type;
-    f(Tag<S>{});
+    using X = typename XOf<typename decltype(ts)::type>::type;
+    f(Tag<X>{});
     if (cudaGetLastError() != cudaSuccess) st = RK_ERR_CUDA;
   });
   if (st != RK_OK) set_error("kernel launch failed");
@@ -371,7 +373,7 @@ rk_status step_impl(rk_problem* p, double dt, rk_stats* acc) {
         if (!(rel > p->sol.tol_true)) break;
         // refinement: solve (I - shift L) delta = res, k^eps += delta
         if (!p->res64) RK_TRY(alloc_dev(p, (void**)&p->res64, (size_t)p->N * 8));
-        if (!p->wdelta) RK_TRY(alloc_dev(p, &p->wdelta, (size_t)p->N * dtype_size(p->sol.storage)));
+        if (!p->wdelta) RK_TRY(alloc_dev(p, &p->wdelta, (size_t)p->N * xsize(p->sol.storage)));
         RhsScalars* rsd = p->rs + 9;
         RK_TRY(launch_typed(p, [&](auto ts) {
           using S = typename decltype(ts)::type;
@@ -662,7 +664,7 @@ rk_status rk_set_tableau(rk_problem* p, int q, const double* A_hi, const double*
         p->ke[i] = p->k[i];
         p->ke_alias[i] = true;
       } else {
-        RK_TRY(alloc_dev(p, &p->ke[i], N * s));
+        RK_TRY(alloc_dev(p, &p->ke[i], N * xsize(p->sol.storage)));
       }
     }
   }
@@ -772,7 +774,7 @@ rk_status rk_solve(rk_problem* p, double shift, const double* g, double* k, int 
     RK_CUDA(cudaGetLastError());
   }
   // solve into the delta workspace (storage precision), then widen
-  if (!p->wdelta) RK_TRY(alloc_dev(p, &p->wdelta, (size_t)p->N * dtype_size(p->sol.storage)));
+  if (!p->wdelta) RK_TRY(alloc_dev(p, &p->wdelta, (size_t)p->N * xsize(p->sol.storage)));
   int iters = 0, status = 0;
   RK_TRY(krylov_solve(p, shift, p->g64, rs, p->wdelta, 8, &iters, &status));
   double* kout = is_device_ptr ? k : p->r;

@@ -29,6 +29,14 @@ template <> __device__ __forceinline__ float nar<float>(double v) { return (floa
 template <> __device__ __forceinline__ __half nar<__half>(double v) { return __double2half(v); }
 template <> __device__ __forceinline__ __nv_bfloat16 nar<__nv_bfloat16>(double v) { return __double2bfloat16(v); }
 
+// Type of the Krylov solution vector x = k^eps for work-vector storage S: with
+// 16-bit work vectors the solution is accumulated and kept in FP32, because
+// k^eps feeds the FP64 explicit correction and later stages, where a 16-bit
+// rounding of it would dominate the error.
+template <typename S> struct XOf { using type = S; };
+template <> struct XOf<__half> { using type = float; };
+template <> struct XOf<__nv_bfloat16> { using type = float; };
+
 // value as it will be read back after a store in S
 template <typename S, typename T> __device__ __forceinline__ T rnd(T v) { return wid<T>(nar<S>(v)); }
 

@@ -199,8 +199,10 @@ __device__ __forceinline__ void bj_apply(const T* sM, int n, int i0, const T (&r
 template <typename S, typename T, int BS, int SEG>
 __global__ void __launch_bounds__(kThreads) cg_init(HeatGeo g, const double* __restrict__ gv,
                                                     const RhsScalars* rs, const T* __restrict__ minv,
-                                                    S* __restrict__ r, S* __restrict__ z, S* __restrict__ x,
-                                                    CgScalars* sc, double* partials) {
+                                                    S* __restrict__ r, S* __restrict__ z,
+                                                    typename XOf<S>::type* __restrict__ x, CgScalars* sc,
+                                                    double* partials) {
+  using X = typename XOf<S>::type;
   __shared__ T sM[2 * BS * BS];
   load_minv<T, BS>(minv, sM);
   const double sigma = rs->sigma;
@@ -225,7 +227,7 @@ __global__ void __launch_bounds__(kThreads) cg_init(HeatGeo g, const double* __r
     }
     store_seg<S, T, SEG>(r + base, m, rv);
     store_seg<S, T, SEG>(z + base, m, zv);
-    store_seg<S, T, SEG>(x + base, m, zero);
+    store_seg<X, T, SEG>(x + base, m, zero);
   RK_SEG_LOOP_END
   double tot[2];
   if (grid_reduce<2, 0u>(acc, partials, &sc->ticket, tot)) {
@@ -304,9 +306,10 @@ __global__ void __launch_bounds__(kThreads) cg_sweep_a(HeatGeo g, T d, T o, cons
 // partials r.z and r.r.  Last CTA: beta, convergence test, iteration count.
 template <typename S, typename T, int BS, int SEG>
 __global__ void __launch_bounds__(kThreads) cg_sweep_b(HeatGeo g, T d, T o, const S* __restrict__ p,
-                                                       S* __restrict__ x, S* __restrict__ r, S* __restrict__ z,
-                                                       const T* __restrict__ minv, CgScalars* sc,
-                                                       double* partials) {
+                                                       typename XOf<S>::type* __restrict__ x, S* __restrict__ r,
+                                                       S* __restrict__ z, const T* __restrict__ minv,
+                                                       CgScalars* sc, double* partials) {
+  using X = typename XOf<S>::type;
   if (sc->done) return;
   __shared__ T sM[2 * BS * BS];
   load_minv<T, BS>(minv, sM);
@@ -322,7 +325,7 @@ __global__ void __launch_bounds__(kThreads) cg_sweep_b(HeatGeo g, T d, T o, cons
     T rv[SEG], xv[SEG], zv[SEG];
     load_seg<T, S, SEG>(r + base, m, rv);
     if (!first) {
-      load_seg<T, S, SEG>(x + base, m, xv);
+      load_seg<T, X, SEG>(x + base, m, xv);
     } else {
 #pragma unroll
       for (int e = 0; e < SEG; ++e) xv[e] = T(0);
@@ -345,7 +348,7 @@ __global__ void __launch_bounds__(kThreads) cg_sweep_b(HeatGeo g, T d, T o, cons
     }
     acc[0] += (double)rz;
     acc[1] += (double)rr;
-    store_seg<S, T, SEG>(x + base, m, xv);
+    store_seg<X, T, SEG>(x + base, m, xv);
     store_seg<S, T, SEG>(r + base, m, rv);
     store_seg<S, T, SEG>(z + base, m, zv);
   RK_SEG_LOOP_END

@@ -39,6 +39,8 @@ template <typename T> struct Tag { using type = T; };
 template <int V> struct IntC { static constexpr int value = V; };
 
 inline size_t dtype_size(int dt) { return dt == RK_F64 ? 8 : dt == RK_F32 ? 4 : 2; }
+// bytes per element of the Krylov solution k^eps (FP32 when work vectors are 16-bit)
+inline size_t xsize(int dt) { return dt == RK_F64 ? 8 : 4; }
 
 // storage x arithmetic dispatch: (f64,f64), (f32,f32), (f16,f32), (bf16,f32)
 template <typename F>
