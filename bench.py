@@ -55,13 +55,19 @@ def measured_peaks():
 
 
 def ncu_traffic(kernel, workload):
-    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, or None."""
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, or None
+    when there is none or the kernel source changed since it was taken."""
+    import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
-            d = json.load(f)
-        e = d[workload][kernel]
-        return float(e["dram_bytes_per_launch"])
+            d = json.load(f)[workload]
+        src = os.path.join(ROOT, "paper_2412_16638_b300", "csrc", "rk_heat.cuh")
+        with open(src, "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()[:16]
+        if d.get("heat_src_sha256_16") != sha:
+            return None
+        return float(d[kernel]["dram_bytes_per_launch"])
     except Exception:
         return None
 
@@ -333,8 +339,8 @@ def main():
     fp64 = None
     if not args.no_fp64:
         q = make("f64", cfg["tol"], 0)
-        rk.rk_integrate(q.h, dt, 1)
-        k64 = max(2, args.steps // 4)
+        rk.rk_integrate(q.h, dt, args.warmup)
+        k64 = args.steps
         torch.cuda.synchronize()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         f0.record(stream)
@@ -344,7 +350,7 @@ def main():
         sec64 = f0.elapsed_time(f1) / 1e3
         u64 = q.state()
         q.close()
-        d64, c64 = closed_form(n, cfg["kappa"], dt, 1 + k64, tab, modes)
+        d64, c64 = closed_form(n, cfg["kappa"], dt, args.warmup + k64, tab, modes)
         fp64 = {"value": N * k64 / sec64, "ms_per_step": 1e3 * sec64 / k64, "steps": k64,
                 "iters_per_step": s64.iters_total / k64, "err_vs_discrete": rel(u64, d64),
                 "err_vs_continuous": rel(u64, c64)}
