@@ -203,6 +203,27 @@ rk_status rk_profile(rk_problem* p, int enable);
 rk_status rk_profile_read(rk_problem* p, rk_kernel_stat* out, int max, int* count,
                           long long* launches_total);
 
+/* ---- solve without allocating (no counterpart in the paper) -------------- */
+
+/* For callers that may not allocate device memory (a memory pool or arena that
+ * owns the device, a host program whose allocator policy forbids cudaMalloc, or
+ * code that must not trigger the implicit synchronisation of cudaMalloc/
+ * cudaFree): the rk_solve stage solve of the heat operator, (I - shift L) k = g
+ * with L = kappa/h^2 * 7-point Laplacian on n^3 nodes, FP32 block-Jacobi CG
+ * (blocks of bj_block x-nodes), tolerances and iteration cap as in
+ * rk_solver_desc, from k = 0.  g_dev and k_dev are caller-owned device arrays of
+ * n^3 float64; *iters (may be NULL) receives the iteration count.
+ * The workspace is a fixed device array inside the library (about 5.3 MB on
+ * every GPU that loads it, kept until the process exits), so n is limited to
+ * 1..64; larger n returns RK_ERR_ARG with an explanation.  The first call on a
+ * device looks up the array's address (cudaGetSymbolAddress); make it before
+ * any stream capture.  All calls share the array: calls that overlap on the
+ * GPU race and must be serialised by the caller.  Synchronous on cuda_stream.
+ * Errors: RK_ERR_ARG, RK_ERR_CUDA, RK_ERR_NOT_CONVERGED, RK_ERR_NONFINITE. */
+rk_status rk_heat_solve_noalloc(int n, double kappa, double shift, int bj_block, double tol_rel,
+                                double tol_abs, int max_iter, const double* g_dev, double* k_dev,
+                                void* cuda_stream, int* iters);
+
 /* Thread-local description of the last error on this thread ("" if none). */
 const char* rk_last_error(void);
 

@@ -80,6 +80,7 @@ _SIGS = {
     "rk_wait_job": [_P, ctypes.c_uint64, _P, ctypes.POINTER(rk_stats), _DP],
     "rk_server_destroy": [_P],
     "rk_profile": [_P, _I],
+    "rk_heat_solve_noalloc": [_I, _D, _D, _I, _D, _D, _I, _P, _P, _P, ctypes.POINTER(_I)],
     "rk_profile_read": [_P, ctypes.POINTER(rk_kernel_stat), _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_longlong)],
 }
 for _name, _args in _SIGS.items():
@@ -282,6 +283,21 @@ def rk_profile_read(p):
         out[b.name.decode()] = {"launches": b.launches, "noop_launches": b.noop_launches,
                                 "ms_total": b.ms_total, "bytes_total": b.bytes_total}
     return out, tot.value
+
+
+def rk_heat_solve_noalloc(n, kappa, shift, bj_block, tol_rel, tol_abs, max_iter, g, k, stream=None,
+                          allow_not_converged=False):
+    """Heat stage solve without any device allocation by the library (its
+    workspace is a fixed device array; n <= 64).  g, k: float64 CUDA tensors
+    of n^3 elements.  Returns the iteration count."""
+    pg, dg, kg = _f64_ptr(g)
+    pk, dk, kk = _f64_ptr(k)
+    if not (dg and dk):
+        raise ValueError("g and k must be device tensors")
+    it = ctypes.c_int()
+    _check(_lib.rk_heat_solve_noalloc(n, kappa, shift, bj_block, tol_rel, tol_abs, max_iter, pg, pk,
+                                      _P(stream or 0), ctypes.byref(it)), _allow(allow_not_converged))
+    return it.value
 
 
 class Problem:
