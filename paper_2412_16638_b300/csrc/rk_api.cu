@@ -479,6 +479,10 @@ static rk_status check_solver(const rk_solver_desc* s, const rk_problem_desc* d)
     set_error("CG needs the symmetric heat operator");
     return RK_ERR_ARG;
   }
+  if (s->krylov == RK_KRYLOV_GMRES && d && d->op != RK_OP_ADVDIFF_CSR) {
+    set_error("GMRES is implemented for the CSR advection-diffusion operator");
+    return RK_ERR_ARG;
+  }
   if (s->max_refine < 0 || s->max_refine > 10) {
     set_error("max_refine must be in 0..10");
     return RK_ERR_ARG;

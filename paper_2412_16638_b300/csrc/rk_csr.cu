@@ -1,16 +1,415 @@
-// Advection-diffusion CSR path (placeholder until the GMRES kernels land).
+// Advection-diffusion path: CSR assembly, FP64 operator and correction,
+// block-Jacobi with per-block inverses, and the GMRES(m) driver.
+#include <cmath>
+
+#include "rk_csr.cuh"
 #include "rk_internal.h"
 
 namespace rk {
-struct GmresWork {};
-rk_status csr_setup(rk_problem*) { set_error("RK_OP_ADVDIFF_CSR is not built yet"); return RK_ERR_ARG; }
-rk_status csr_free(rk_problem*) { return RK_OK; }
-rk_status gmres_solve(rk_problem*, double, const double*, RhsScalars*, void*, int, int*, int*) {
-  set_error("GMRES is not built yet"); return RK_ERR_ARG;
+
+__global__ void __launch_bounds__(kThreads) csr_apply_f64_kernel(CsrView A, const double* __restrict__ vals,
+                                                                 long long N, const double* __restrict__ x,
+                                                                 double* __restrict__ y, RhsScalars* rs,
+                                                                 double* partials) {
+  double acc[2] = {0.0, 0.0};
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < N;
+       r += (long long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int e = A.rowptr[r]; e < A.rowptr[r + 1]; ++e) s = fma(vals[e], x[A.cols[e]], s);
+    y[r] = s;
+    acc[0] = fma(s, s, acc[0]);
+    acc[1] = fmax(acc[1], fabs(s));
+  }
+  if (rs == nullptr) return;
+  double tot[2];
+  if (grid_reduce<2, 2u>(acc, partials, &rs->ticket, tot)) {
+    rs->gg = tot[0];
+    rs->gmax = tot[1];
+    rs->sigma = (rs->want_scale && tot[1] > 0.0 && isfinite(tot[1])) ? 1.0 / tot[1] : 1.0;
+  }
 }
-rk_status csr_precond_f64(rk_problem*, double, const double*, double*) { set_error("not built"); return RK_ERR_ARG; }
-rk_status csr_apply_f64(rk_problem*, const double*, double*, RhsScalars*) { set_error("not built"); return RK_ERR_ARG; }
-rk_status csr_correct_f64(rk_problem*, double, const double*, const void*, double*, RhsScalars*) {
-  set_error("not built"); return RK_ERR_ARG;
+
+struct CsrMinv {
+  double shift = 0.0;
+  void* dev = nullptr;
+  bool valid = false;
+};
+
+struct GmresWork {
+  void* V = nullptr;          // (m+1) basis vectors, storage type
+  void* z = nullptr;          // preconditioned vector
+  double* partials = nullptr; // per-CTA multi-dot partials
+  GmScalars* sc = nullptr;
+  GmScalars* h_sc = nullptr;  // pinned header mirror
+  CsrMinv minv[4];
+  int minv_next = 0;
+  long long npart = 0;
+};
+
+static constexpr size_t kGmHeader = offsetof(GmScalars, h1);
+
+// L u = div(kappa grad u) - v.grad u on the n^3 interior nodes (h = 1/(n+1),
+// homogeneous Dirichlet): face diffusivity = mean of the two nodes (kappa_P on
+// a boundary face), first-order upwind advection.  Columns of a row ascending.
+static void assemble(int n, const double* kap, const double vel[3], std::vector<int>& rowptr,
+                     std::vector<int>& cols, std::vector<double>& vals) {
+  const long long N = (long long)n * n * n;
+  const double h = 1.0 / (n + 1), ih2 = 1.0 / (h * h);
+  rowptr.assign(N + 1, 0);
+  cols.clear();
+  vals.clear();
+  cols.reserve(N * 7);
+  vals.reserve(N * 7);
+  const long long stride[3] = {1, n, (long long)n * n};
+  for (int k = 0; k < n; ++k)
+    for (int j = 0; j < n; ++j)
+      for (int i = 0; i < n; ++i) {
+        const long long P = i + (long long)j * n + (long long)k * n * n;
+        const int idx[3] = {i, j, k};
+        double diag = 0.0;
+        double nbv[6] = {0, 0, 0, 0, 0, 0};
+        bool nbin[6] = {false, false, false, false, false, false};
+        for (int d = 0; d < 3; ++d) {
+          for (int s = 0; s < 2; ++s) {  // s = 0: minus side, 1: plus side
+            const bool inside = s == 0 ? idx[d] > 0 : idx[d] < n - 1;
+            const int slot = d * 2 + s;
+            if (inside) {
+              const long long Q = s == 0 ? P - stride[d] : P + stride[d];
+              const double kf = 0.5 * (kap[P] + kap[Q]);
+              nbv[slot] += kf * ih2;
+              diag -= kf * ih2;
+              nbin[slot] = true;
+            } else {
+              diag -= kap[P] * ih2;
+            }
+          }
+          const double v = vel[d];
+          diag -= std::fabs(v) / h;
+          const int up = v >= 0.0 ? d * 2 : d * 2 + 1;  // upstream neighbour
+          if (nbin[up]) nbv[up] += std::fabs(v) / h;
+        }
+        // ascending column order: z-, y-, x-, P, x+, y+, z+
+        const int order[6] = {4, 2, 0, 1, 3, 5};
+        for (int o = 0; o < 3; ++o) {
+          const int slot = order[o];
+          if (nbin[slot]) {
+            cols.push_back((int)(P - stride[slot / 2]));
+            vals.push_back(nbv[slot]);
+          }
+        }
+        cols.push_back((int)P);
+        vals.push_back(diag);
+        for (int o = 3; o < 6; ++o) {
+          const int slot = order[o];
+          if (nbin[slot]) {
+            cols.push_back((int)(P + stride[slot / 2]));
+            vals.push_back(nbv[slot]);
+          }
+        }
+        rowptr[P + 1] = (int)cols.size();
+      }
 }
+
+template <typename S>
+__global__ void to_storage(const double* __restrict__ v, double scale, S* __restrict__ out, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = nar<S>(v[i] * scale);
+}
+
+static int gm_seg(int storage, int bs) {
+  const int v = dtype_size(storage) == 2 ? 8 : 4;
+  return bs > v ? bs : v;
+}
+
+rk_status csr_setup(rk_problem* p) {
+  std::vector<int> rowptr, cols;
+  std::vector<double> vals;
+  assemble(p->n, p->desc.kappa_field, p->desc.vel, rowptr, cols, vals);
+  Csr& c = p->csr;
+  c.nnz = (long long)vals.size();
+  double vmax = 0.0;
+  for (double v : vals) vmax = std::max(vmax, std::fabs(v));
+  if (!(vmax > 0.0) || !std::isfinite(vmax)) {
+    set_error("CSR operator has no finite nonzero entries (check kappa_field)");
+    return RK_ERR_ARG;
+  }
+  c.lscale = 1.0 / vmax;
+  RK_TRY(alloc_dev(p, (void**)&c.rowptr, rowptr.size() * sizeof(int)));
+  RK_TRY(alloc_dev(p, (void**)&c.cols, cols.size() * sizeof(int)));
+  RK_TRY(alloc_dev(p, (void**)&c.v64, vals.size() * sizeof(double)));
+  RK_TRY(alloc_dev(p, &c.vS, vals.size() * dtype_size(p->sol.storage)));
+  RK_CUDA(cudaMemcpy(c.rowptr, rowptr.data(), rowptr.size() * sizeof(int), cudaMemcpyHostToDevice));
+  RK_CUDA(cudaMemcpy(c.cols, cols.data(), cols.size() * sizeof(int), cudaMemcpyHostToDevice));
+  RK_CUDA(cudaMemcpy(c.v64, vals.data(), vals.size() * sizeof(double), cudaMemcpyHostToDevice));
+  rk_status st = RK_OK;
+  dispatch_st(p->sol.storage, [&](auto ts, auto) {
+    using S = typename decltype(ts)::type;
+    auto kern = to_storage<S>;
+    kern<<<grid_for((const void*)kern, c.nnz), kThreads, 0, p->st>>>(c.v64, c.lscale, static_cast<S*>(c.vS), c.nnz);
+    if (cudaGetLastError() != cudaSuccess) st = RK_ERR_CUDA;
+  });
+  RK_TRY(st);
+  if (p->sol.krylov == RK_KRYLOV_GMRES) {
+    GmresWork* w = new GmresWork();
+    p->gw = w;
+    const size_t s = dtype_size(p->sol.storage);
+    const int m = p->sol.restart;
+    RK_TRY(alloc_dev(p, &w->V, (size_t)(m + 1) * p->N * s));
+    RK_TRY(alloc_dev(p, &w->z, (size_t)p->N * s));
+    const int seg = gm_seg(p->sol.storage, p->sol.bj_block);
+    const int R = std::max(1, 32 / seg);
+    const long long nsegs = (long long)p->n * p->n * ((p->n + seg - 1) / seg);
+    const long long ctas = ((nsegs + R - 1) / R + kThreads - 1) / kThreads;
+    w->npart = std::max<long long>(ctas, (long long)device_sms() * 32) * kGmMax;
+    RK_TRY(alloc_dev(p, (void**)&w->partials, (size_t)w->npart * sizeof(double)));
+    RK_TRY(alloc_dev(p, (void**)&w->sc, sizeof(GmScalars)));
+    RK_CUDA(cudaMemset(w->sc, 0, sizeof(GmScalars)));
+    RK_CUDA(cudaMallocHost((void**)&w->h_sc, sizeof(GmScalars)));
+  }
+  RK_CUDA(cudaStreamSynchronize(p->st));
+  return RK_OK;
+}
+
+rk_status csr_free(rk_problem* p) {
+  Csr& c = p->csr;
+  if (c.rowptr) cudaFree(c.rowptr);
+  if (c.cols) cudaFree(c.cols);
+  if (c.v64) cudaFree(c.v64);
+  if (c.vS) cudaFree(c.vS);
+  c = Csr{};
+  if (p->gw) {
+    GmresWork* w = p->gw;
+    if (w->V) cudaFree(w->V);
+    if (w->z) cudaFree(w->z);
+    if (w->partials) cudaFree(w->partials);
+    if (w->sc) cudaFree(w->sc);
+    if (w->h_sc) cudaFreeHost(w->h_sc);
+    for (auto& e : w->minv)
+      if (e.dev) cudaFree(e.dev);
+    delete w;
+    p->gw = nullptr;
+  }
+  return RK_OK;
+}
+
+static CsrView view(const rk_problem* p) { return CsrView{p->csr.rowptr, p->csr.cols}; }
+
+rk_status csr_apply_f64(rk_problem* p, const double* x, double* y, RhsScalars* rs) {
+  auto kern = csr_apply_f64_kernel;
+  const int grid = grid_for((const void*)kern, p->N);
+  const double bytes = (double)p->csr.nnz * 12.0 + 4.0 * (p->N + 1) + 16.0 * p->N;
+  launch(p, K_CSR_SPMV, bytes,
+         [&] { kern<<<grid, kThreads, 0, p->st>>>(view(p), p->csr.v64, p->N, x, y, rs, p->partials); });
+  RK_CUDA(cudaGetLastError());
+  return RK_OK;
+}
+
+rk_status csr_correct_f64(rk_problem* p, double shift, const double* gv, const void* ke, double* kout,
+                          RhsScalars* rs) {
+  rk_status st = RK_OK;
+  dispatch_st(p->sol.storage, [&](auto ts, auto) {
+    using X = typename XOf<typename decltype(ts)::type>::type;
+    auto kern = csr_correct_f64_kernel<X>;
+    const int grid = grid_for((const void*)kern, p->N);
+    const double bytes = (double)p->csr.nnz * 12.0 + 4.0 * (p->N + 1) + (16.0 + sizeof(X)) * p->N;
+    launch(p, K_CSR_CORRECT, bytes, [&] {
+      kern<<<grid, kThreads, 0, p->st>>>(view(p), p->csr.v64, p->N, gv, static_cast<const X*>(ke), shift, kout, rs,
+                                         p->partials);
+    });
+    if (cudaGetLastError() != cudaSuccess) st = RK_ERR_CUDA;
+  });
+  if (st != RK_OK) set_error("csr_correct_f64 launch failed");
+  return st;
+}
+
+// Per-block inverses of I - shift L for this shift (cached, 4 shifts).
+static rk_status csr_minv(rk_problem* p, double shift, const void** out) {
+  if (!p->gw) {
+    GmresWork* w = new GmresWork();
+    p->gw = w;
+  }
+  GmresWork* w = p->gw;
+  for (auto& e : w->minv)
+    if (e.valid && e.shift == shift) {
+      *out = e.dev;
+      return RK_OK;
+    }
+  CsrMinv& e = w->minv[w->minv_next];
+  w->minv_next = (w->minv_next + 1) % 4;
+  const int bs = p->sol.bj_block;
+  const long long nbl = (p->n + bs - 1) / bs;
+  const long long nblocks = (long long)p->n * p->n * nbl;
+  if (!e.dev) RK_TRY(alloc_dev(p, &e.dev, (size_t)nblocks * bs * bs * dtype_size(p->sol.storage)));
+  rk_status st = RK_OK;
+  dispatch_st(p->sol.storage, [&](auto ts, auto) {
+    using S = typename decltype(ts)::type;
+    dispatch_bs(bs, [&](auto bsc) {
+      constexpr int BS = decltype(bsc)::value;
+      auto kern = csr_bj_setup<S, BS>;
+      launch(p, K_CSR_BJ_SETUP, (double)p->csr.nnz * 12.0 + (double)nblocks * BS * BS * sizeof(S), [&] {
+        kern<<<grid_for((const void*)kern, nblocks), kThreads, 0, p->st>>>(view(p), p->csr.v64, p->n, shift,
+                                                                          static_cast<S*>(e.dev));
+      });
+      if (cudaGetLastError() != cudaSuccess) st = RK_ERR_CUDA;
+    });
+  });
+  if (st != RK_OK) {
+    set_error("csr_bj_setup launch failed");
+    return st;
+  }
+  e.shift = shift;
+  e.valid = true;
+  *out = e.dev;
+  return RK_OK;
+}
+
+rk_status csr_precond_f64(rk_problem* p, double shift, const double* r, double* z) {
+  const void* minv = nullptr;
+  RK_TRY(csr_minv(p, shift, &minv));
+  rk_status st = RK_OK;
+  dispatch_st(p->sol.storage, [&](auto ts, auto tt) {
+    using S = typename decltype(ts)::type;
+    using T = typename decltype(tt)::type;
+    dispatch_bs(p->sol.bj_block, [&](auto bsc) {
+      constexpr int BS = decltype(bsc)::value;
+      constexpr int SEG = seg_of<S, BS>();
+      HeatGeo g{p->n, (p->n + SEG - 1) / SEG, (long long)p->n * p->n, p->N};
+      auto kern = csr_bj_apply_f64io<S, T, BS, SEG>;
+      launch(p, K_BJ, (16.0 + BS * sizeof(S)) * p->N, [&] {
+        kern<<<grid_for((const void*)kern, g.n2 * g.nseg), kThreads, 0, p->st>>>(g, static_cast<const S*>(minv), r, z);
+      });
+      if (cudaGetLastError() != cudaSuccess) st = RK_ERR_CUDA;
+    });
+  });
+  if (st != RK_OK) set_error("csr block-Jacobi launch failed");
+  return st;
+}
+
+// Right-preconditioned restarted GMRES(m) on (I - shift L) x = sigma g, x0 = 0.
+// Each Arnoldi step launches four kernels (precondition, SpMV + first
+// projection dots, second CGS pass, norm + Hessenberg/Givens); they return at
+// once when the device state says the cycle or the solve has ended.  The host
+// polls the state once per chunk of steps and launches the cycle-end update
+// and the restart.
+rk_status gmres_solve(rk_problem* p, double shift, const double* g64, RhsScalars* rs, void* x, int slot, int* iters,
+                      int* status) {
+  if (p->desc.op != RK_OP_ADVDIFF_CSR || !p->gw || !p->gw->V) {
+    set_error("GMRES is implemented for the CSR advection-diffusion operator");
+    return RK_ERR_ARG;
+  }
+  GmresWork* w = p->gw;
+  const void* minv = nullptr;
+  RK_TRY(csr_minv(p, shift, &minv));
+  const int m = p->sol.restart;
+  GmScalars* hs = w->h_sc;
+  std::memset(hs, 0, kGmHeader);
+  hs->max_iter = p->sol.max_iter;
+  hs->m = m;
+  hs->tol_rel = p->sol.tol_rel;
+  hs->tol_abs = p->sol.tol_abs;
+  RK_CUDA(cudaMemcpyAsync(w->sc, hs, kGmHeader, cudaMemcpyHostToDevice, p->st));
+  const int solve = ++p->solve_seq;
+  rk_status st = RK_OK;
+  dispatch_st(p->sol.storage, [&](auto ts, auto tt) {
+    using S = typename decltype(ts)::type;
+    using T = typename decltype(tt)::type;
+    using X = typename XOf<S>::type;
+    dispatch_bs(p->sol.bj_block, [&](auto bsc) {
+      constexpr int BS = decltype(bsc)::value;
+      constexpr int SEG = seg_of<S, BS>();
+      constexpr int R = (32 / SEG) > 1 ? 32 / SEG : 1;
+      HeatGeo g{p->n, (p->n + SEG - 1) / SEG, (long long)p->n * p->n, p->N};
+      const long long nsegs = g.n2 * g.nseg;
+      const int gdots = (int)(((nsegs + R - 1) / R + kThreads - 1) / kThreads);
+      S* V = static_cast<S*>(w->V);
+      S* z = static_cast<S*>(w->z);
+      X* xs = static_cast<X*>(x);
+      const S* lv = static_cast<const S*>(p->csr.vS);
+      const S* M = static_cast<const S*>(minv);
+      const T cs = (T)(shift / p->csr.lscale);
+      const long long ldv = p->N;
+      const double Ns = (double)p->N * sizeof(S), Nx = (double)p->N * sizeof(X);
+      const double mat = (double)p->csr.nnz * (4.0 + sizeof(S)) + 4.0 * (p->N + 1);
+      auto k_start = gm_start<S, T, SEG>;
+      auto k_restart = gm_restart<S, T, SEG>;
+      auto k_prec = gm_prec<S, T, BS, SEG>;
+      auto k_spmv = gm_spmv_dots<S, T, SEG, R>;
+      auto k_orth = gm_orth<S, T, SEG, R>;
+      auto k_norm = gm_norm<S, T, SEG, R>;
+      auto k_upd = gm_update<S, T, BS, SEG>;
+      const int gs = grid_for((const void*)k_start, nsegs), gp = grid_for((const void*)k_prec, nsegs);
+      launch(p, K_GM_INIT, 8.0 * p->N + Ns + Nx,
+             [&] { k_start<<<gs, kThreads, 0, p->st>>>(g, g64, rs, V, xs, w->sc, w->partials); });
+      int launched = 0, worked = 0, rounds = 0;
+      const int maxlaunch = p->sol.max_iter + 2 * m + 64;
+      const int maxrounds = 2 * (maxlaunch / 8) + 16;  // every round advances the device state
+      while (true) {
+        if (++rounds > maxrounds) {
+          st = RK_ERR_TIMEOUT;
+          set_error("GMRES made no progress after %d polling rounds", rounds);
+          return;
+        }
+        const int chunk = 8;
+        for (int c = 0; c < chunk; ++c) {
+          const int idx = launched + c;
+          // bytes use the basis size at the step's expected index (j = idx mod m)
+          const double jb = (double)(idx % m) + 1.0;
+          prof_begin(p, K_GM_PREC, 3.0 * Ns + BS * Ns, solve, idx);
+          k_prec<<<gp, kThreads, 0, p->st>>>(g, V, ldv, M, z, w->sc);
+          prof_end(p);
+          prof_begin(p, K_GM_ARNOLDI, mat + Ns + jb * Ns + Ns, solve, idx);
+          k_spmv<<<gdots, kThreads, 0, p->st>>>(g, view(p), lv, cs, z, V, ldv, w->sc, w->partials);
+          prof_end(p);
+          prof_begin(p, K_GM_ORTH, 2.0 * jb * Ns + 2.0 * Ns, solve, idx);
+          k_orth<<<gdots, kThreads, 0, p->st>>>(g, V, ldv, w->sc, w->partials);
+          prof_end(p);
+          prof_begin(p, K_GM_NORM, jb * Ns + 2.0 * Ns, solve, idx);
+          k_norm<<<gdots, kThreads, 0, p->st>>>(g, V, ldv, w->sc, w->partials);
+          prof_end(p);
+        }
+        launched += chunk;
+        if (cudaGetLastError() != cudaSuccess) {
+          st = RK_ERR_CUDA;
+          set_error("GMRES launch failed");
+          return;
+        }
+        if (cudaMemcpyAsync(hs, w->sc, kGmHeader, cudaMemcpyDeviceToHost, p->st) != cudaSuccess ||
+            cudaStreamSynchronize(p->st) != cudaSuccess) {
+          st = RK_ERR_CUDA;
+          set_error("GMRES status readback failed");
+          return;
+        }
+        const int did = hs->iter - worked;
+        prof_mark_noops(p, solve, launched - chunk + did, launched);
+        worked = hs->iter;
+        launched = worked;  // launch indices continue from the device step count
+        if (hs->cycle_end) {
+          launch(p, K_GM_UPDATE, (double)hs->jused * Ns + 2.0 * Nx + BS * Ns,
+                 [&] { k_upd<<<gp, kThreads, 0, p->st>>>(g, V, ldv, M, xs, w->sc); });
+          if (hs->done) break;
+          launch(p, K_GM_INIT, mat + Nx + 8.0 * p->N + Ns, [&] {
+            k_restart<<<gs, kThreads, 0, p->st>>>(g, view(p), lv, cs, g64, rs, xs, V, w->sc, w->partials);
+          });
+        } else if (hs->done) {
+          break;
+        }
+        if (launched > maxlaunch || hs->iter > p->sol.max_iter + 1) {
+          st = RK_ERR_TIMEOUT;
+          set_error("GMRES did not stop after %d steps", launched);
+          return;
+        }
+      }
+      if (cudaStreamSynchronize(p->st) != cudaSuccess) {
+        st = RK_ERR_CUDA;
+        set_error("GMRES final synchronisation failed");
+      }
+    });
+  });
+  if (st != RK_OK) return st;
+  *iters = hs->iter;
+  *status = hs->status;
+  p->last_iters[slot] = hs->iter;
+  return RK_OK;
+}
+
 }  // namespace rk

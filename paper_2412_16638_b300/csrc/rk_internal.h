@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <atomic>
 #include <chrono>
 #include <cstdio>
@@ -183,6 +184,7 @@ rk_status step_impl(rk_problem* p, double dt, rk_stats* acc);
 void prof_begin(rk_problem* p, int kid, double bytes, int solve = -1, int idx = -1);
 void prof_end(rk_problem* p);
 void prof_finish_solve(rk_problem* p, int solve, int iters);
+void prof_mark_noops(rk_problem* p, int solve, int idx_from, int idx_to);
 void prof_free(rk_problem* p);
 template <typename F>
 inline void launch(rk_problem* p, int kid, double bytes, F&& f) {

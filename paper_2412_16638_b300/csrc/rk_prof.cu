@@ -71,6 +71,18 @@ void prof_finish_solve(rk_problem* p, int solve, int iters) {
   }
 }
 
+void prof_mark_noops(rk_problem* p, int solve, int idx_from, int idx_to) {
+  Prof* pr = p->prof;
+  if (!pr || !pr->on || idx_from >= idx_to) return;
+  for (auto it = pr->pending.rbegin(); it != pr->pending.rend(); ++it) {
+    if (it->solve != solve) {
+      if (it->solve >= 0 && it->solve < solve) break;
+      continue;
+    }
+    if (it->idx >= idx_from && it->idx < idx_to) it->noop = true;
+  }
+}
+
 void prof_free(rk_problem* p) {
   if (!p->prof) return;
   harvest(p);

@@ -1,0 +1,130 @@
+"""Parity of the advection-diffusion path (CSR operator, per-block
+block-Jacobi, restarted GMRES, DIRK stages) against the float64 oracle."""
+import functools
+
+import numpy as np
+import pytest
+
+import synth
+from gpu_util import rel_l2, require_gpu, rng_vec
+from oracle import dirk, krylov, operators, tableau
+
+pytestmark = pytest.mark.gpu
+VEL = (1.0, 0.5, 0.25)
+
+
+@pytest.fixture(scope="module")
+def rk():
+    return require_gpu()
+
+
+def make(rk, n, storage="f64", bs=8, tol=1e-12, restart=30, correct=None, max_iter=4000, tab=None, u0=None,
+         seed=0, vel=VEL):
+    kap = synth.kappa_field(n, seed=seed)
+    return rk.Problem(rk.problem_desc(op=rk.RK_OP_ADVDIFF_CSR, n=n, kappa_field=kap, vel=vel),
+                      rk.solver_desc(krylov=rk.RK_KRYLOV_GMRES, restart=restart, bj_block=bs, tol_rel=tol,
+                                     storage=storage, correct=correct, max_iter=max_iter),
+                      tableau=tab, u0=u0)
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_L(n, seed=0, vel=VEL):
+    return operators.advdiff_csr(n, synth.kappa_field(n, seed=seed), vel)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 7, 16, 33])
+def test_csr_operator_f64(rk, n):
+    x = rng_vec(n, 40 + n)
+    with make(rk, n) as p:
+        y = np.empty_like(x)
+        rk.rk_apply_op(p.h, x, y)
+    ref = oracle_L(n) @ x
+    np.testing.assert_allclose(y, ref, rtol=1e-13, atol=1e-13 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-13), ("f32", 2e-6), ("f16", 2e-3)])
+@pytest.mark.parametrize("n,bs", [(9, 4), (16, 8), (20, 16), (13, 32), (6, 1)])
+def test_csr_block_jacobi(rk, n, bs, storage, tol):
+    shift = 5e-4
+    r = rng_vec(n, 7 + n)
+    with make(rk, n, storage=storage, bs=bs) as p:
+        z = np.empty_like(r)
+        rk.rk_apply_precond(p.h, shift, r, z)
+    M = krylov.shifted(oracle_L(n), shift)
+    ref = krylov.BlockJacobi(M, n, bs).apply(r)
+    assert rel_l2(z, ref) < tol
+
+
+@pytest.mark.parametrize("n,bs,restart", [(4, 2, 5), (12, 8, 30), (21, 16, 10), (24, 8, 64)])
+def test_gmres_f64_matches_oracle(rk, n, bs, restart):
+    shift = 5e-4
+    g = oracle_L(n) @ synth.gaussian_bump(n)
+    with make(rk, n, bs=bs, restart=restart, tol=1e-11) as p:
+        k = np.empty_like(g)
+        st = rk.rk_solve(p.h, shift, g, k)
+    M = krylov.shifted(oracle_L(n), shift)
+    ref = krylov.gmres(lambda v: M @ v, krylov.BlockJacobi(M, n, bs).apply, g, restart=restart, tol_rel=1e-11,
+                       max_iter=4000)
+    assert ref.converged
+    assert rel_l2(k, ref.x) < 1e-9
+    assert abs(st.iters_total - ref.iters) <= 2
+    if n <= 12:
+        np.testing.assert_allclose(k, np.linalg.solve(M.toarray(), g), rtol=1e-8, atol=1e-9 * np.abs(g).max())
+
+
+@pytest.mark.parametrize("storage,tol,bound", [("f32", 1e-6, 1e-5), ("f16", 1e-3, 5e-3), ("bf16", 1e-3, 2e-2)])
+def test_gmres_low_precision(rk, storage, tol, bound):
+    n, shift = 20, 5e-4
+    g = oracle_L(n) @ synth.gaussian_bump(n)
+    with make(rk, n, storage=storage, bs=8, tol=tol, max_iter=600) as p:
+        k = np.empty_like(g)
+        rk.rk_solve(p.h, shift, g, k, allow_not_converged=True)
+    M = krylov.shifted(oracle_L(n), shift)
+    assert rel_l2(k, np.linalg.solve(M.toarray(), g) if n <= 12 else
+                  krylov.gmres(lambda v: M @ v, krylov.BlockJacobi(M, n, 8).apply, g, tol_rel=1e-13).x) < bound
+
+
+@pytest.mark.parametrize("name", ["dirk3", "sdirk2", "4s3pC"])
+def test_step_f64_parity(rk, name):
+    n, dt, steps = 14, 5e-4, 3
+    u0 = synth.gaussian_bump(n)
+    with make(rk, n, bs=8, tol=1e-12, correct=1, tab=name, u0=u0) as p:
+        rk.rk_integrate(p.h, dt, steps)
+        u = p.state()
+    ref = dirk.integrate(u0, dt, steps, tableau.get(name), operators.CSROperator(n, oracle_L(n)),
+                         dirk.Solver("gmres", bs=8, tol_rel=1e-12, restart=30))
+    assert rel_l2(u, ref) < 1e-10
+
+
+@pytest.mark.parametrize("storage,tol,bound", [("f32", 1e-7, 1e-6), ("f16", 1e-3, 5e-3)])
+def test_step_mixed_within_bound(rk, storage, tol, bound):
+    n, dt, steps = 18, 5e-4, 4
+    u0 = synth.gaussian_bump(n)
+    with make(rk, n, storage=storage, bs=8, tol=tol, correct=1, tab="dirk3", u0=u0, max_iter=800) as p:
+        rk.rk_integrate(p.h, dt, steps, allow_not_converged=True)
+        u = p.state()
+    ref = dirk.integrate(u0, dt, steps, tableau.dirk3(), operators.CSROperator(n, oracle_L(n)),
+                         dirk.Solver("gmres", bs=8, tol_rel=1e-13, restart=30))
+    assert rel_l2(u, ref) < bound
+
+
+def test_config3_full_size_sampled_rows_and_true_residual(rk):
+    """192^3 (the advection-diffusion configuration): operator rows sampled
+    and evaluated one by one by the oracle's CSR, and the solve's residual
+    recomputed by the oracle's CSR product at full size."""
+    n, shift = 192, 0.435866521508459 * 5e-4
+    N = n ** 3
+    u0 = synth.gaussian_bump(n)
+    L = oracle_L(n)
+    with make(rk, n, storage="f32", bs=8, tol=1e-6, max_iter=600) as p:
+        y = np.empty(N)
+        rk.rk_apply_op(p.h, u0, y)
+        g = y.copy()
+        k = np.empty(N)
+        st = rk.rk_solve(p.h, shift, g, k)
+    rows = np.random.default_rng(0).choice(N, 2000, replace=False)
+    ref_rows = L[rows] @ u0
+    np.testing.assert_allclose(y[rows], ref_rows, rtol=1e-12, atol=1e-12 * np.abs(ref_rows).max())
+    res = g - (k - shift * (L @ k))
+    assert np.linalg.norm(res) / np.linalg.norm(g) < 5e-5
+    assert st.iters_total < 600
