@@ -1,0 +1,94 @@
+"""Batched stepping (rk_integrate_batch): every problem of a batch matches
+its solo run and the oracle, whatever the batch composition."""
+import numpy as np
+import pytest
+
+import synth
+from closed_forms import R_scalar, rel_l2, sine_eigenvalue
+from gpu_util import require_gpu
+from oracle import dirk, operators, tableau
+
+pytestmark = pytest.mark.gpu
+BOUND = {"f64": 1e-10, "f32": 1e-6, "f16": 5e-3}
+
+
+@pytest.fixture(scope="module")
+def rk():
+    return require_gpu()
+
+
+def make(rk, n, kappa, storage, tab, u0, bs=8, tol=None):
+    tol = tol if tol is not None else {"f64": 1e-12, "f32": 1e-7, "f16": 1e-3}[storage]
+    return rk.Problem(rk.problem_desc(n=n, kappa=kappa),
+                      rk.solver_desc(bj_block=bs, tol_rel=tol, storage=storage, max_iter=2000,
+                                     correct=(1 if storage != "f64" else 0)),
+                      tableau=tab, u0=u0)
+
+
+SPECS = [(17, 0.3, "f32", "sdirk2", 8), (23, 2.0, "f32", "dirk3", 8), (40, 1.0, "f32", "4s3pB", 8),
+         (12, 5.0, "f32", "midpoint1", 8), (33, 0.7, "f64", "sdirk2", 4), (20, 1.5, "f64", "dirk3", 4),
+         (28, 1.0, "f16", "sdirk2", 8), (9, 0.2, "f16", "dirk3", 8), (64, 0.5, "f32", "sdirk2", 8),
+         (5, 1.0, "f32", "sdirk2", 8)]
+
+
+def test_batch_matches_solo_and_oracle(rk):
+    dt, steps = 1e-3, 3
+    u0s = [synth.heat_modes(seed=i, n_random=6).evaluate(n) for i, (n, *_rest) in enumerate(SPECS)]
+    batch = [make(rk, n, kap, st, tab, u0, bs) for (n, kap, st, tab, bs), u0 in zip(SPECS, u0s)]
+    stats = rk.rk_integrate_batch([p.h for p in batch], dt, steps)
+    got = [p.state() for p in batch]
+    assert stats.solves > 0 and stats.not_converged == 0
+    for (n, kap, st, tab, bs), u0, ub in zip(SPECS, u0s, got):
+        with make(rk, n, kap, st, tab, u0, bs) as solo:
+            rk.rk_integrate(solo.h, dt, steps)
+            us = solo.state()
+        ref = dirk.integrate(u0, dt, steps, tableau.get(tab), operators.HeatOperator(n, kap),
+                             dirk.Solver("cg", bs=bs, tol_rel=1e-13))
+        assert rel_l2(ub, us) < BOUND[st], (n, st, tab)
+        assert rel_l2(ub, ref) < BOUND[st], (n, st, tab)
+    for p in batch:
+        p.close()
+
+
+def test_batch_composition_invariance(rk):
+    """A problem stepped alone in a batch and inside a larger batch agree."""
+    dt, steps = 1e-3, 2
+    n, kap = 24, 1.0
+    u0 = synth.heat_modes(seed=9, n_random=4).evaluate(n)
+    one = make(rk, n, kap, "f32", "sdirk2", u0)
+    rk.rk_integrate_batch([one.h], dt, steps)
+    alone = one.state()
+    one.close()
+    others = [make(rk, m, 1.0, "f32", "sdirk2", synth.sine_mode(m)) for m in (16, 31, 48, 60)]
+    target = make(rk, n, kap, "f32", "sdirk2", u0)
+    rk.rk_integrate_batch([o.h for o in others] + [target.h], dt, steps)
+    mixed = target.state()
+    assert rel_l2(mixed, alone) < 1e-6
+    for o in others + [target]:
+        o.close()
+
+
+def test_batched_workload_slice_closed_form(rk):
+    """64 problems of the batched workload (n in 16..64, kappa log-uniform,
+    amplitude * sine mode, SDIRK2, dt 1e-3, FP32 solves / FP64 corrections),
+    5 steps: each equals amplitude * R(dt lambda)^5 * phi to 1e-6."""
+    dt, steps = 1e-3, 5
+    probs = synth.batch_problems(64, seed=0)
+    A_hi, A_lo, b = tableau.sdirk2()
+    batch = [make(rk, pr.n, pr.kappa, "f32", "sdirk2", pr.amplitude * synth.sine_mode(pr.n)) for pr in probs]
+    st = rk.rk_integrate_batch([p.h for p in batch], dt, steps)
+    assert st.solves == 64 * 2 * steps
+    for pr, p in zip(probs, batch):
+        lam = sine_eigenvalue(pr.n, pr.kappa, 1, 1, 1)
+        exact = pr.amplitude * R_scalar(A_hi + A_lo, b, dt * lam).real ** steps * synth.sine_mode(pr.n)
+        assert rel_l2(p.state(), exact) < 1e-6, (pr.n, pr.kappa)
+        p.close()
+
+
+def test_batch_rejects_bad_input(rk):
+    with pytest.raises(rk.RKError):
+        rk.rk_integrate_batch([], 1e-3, 1)
+    p = make(rk, 8, 1.0, "f32", "sdirk2", synth.sine_mode(8))
+    with pytest.raises(rk.RKError):
+        rk.rk_integrate_batch([p.h, p.h], 1e-3, 1)
+    p.close()
