@@ -1,0 +1,109 @@
+"""Serving with continuous batching: jobs admitted by HBM footprint, stepped
+together, and each result the same alone and in the mix."""
+import time
+
+import numpy as np
+import pytest
+
+import synth
+from closed_forms import rel_l2
+from gpu_util import require_gpu
+
+pytestmark = pytest.mark.gpu
+BOUND = {"f32": 1e-6, "f16": 5e-3}
+
+
+@pytest.fixture(scope="module")
+def rk():
+    return require_gpu()
+
+
+def job_args(rk, n, kappa, tab, storage, seed):
+    desc = rk.problem_desc(n=n, kappa=kappa)
+    sol = rk.solver_desc(bj_block=8, tol_rel={"f32": 1e-7, "f16": 1e-3}[storage], storage=storage, max_iter=2000)
+    u0 = synth.heat_modes(seed=seed, n_random=4).evaluate(n)
+    return desc, sol, rk.tableaux.get(tab), u0
+
+
+MIX = [(24, 1.0, "sdirk2", "f32"), (40, 0.5, "dirk3", "f32"), (96, 1.0, "sdirk2", "f32"),
+       (17, 3.0, "midpoint1", "f16"), (64, 0.2, "dirk3", "f16"), (80, 2.0, "midpoint1", "f32"),
+       (33, 1.0, "sdirk2", "f32"), (12, 7.0, "dirk3", "f32")]
+
+
+def solo(rk, n, kappa, tab, storage, seed, dt, steps):
+    desc, sol, t, u0 = job_args(rk, n, kappa, tab, storage, seed)
+    with rk.Problem(desc, sol, tableau=t, u0=u0) as p:
+        rk.rk_integrate(p.h, dt, steps, allow_not_converged=True)
+        return p.state()
+
+
+def test_results_same_alone_and_in_mix(rk):
+    dt = 1e-3
+    steps = [3, 5, 4, 6, 2, 3, 5, 4]
+    srv = rk.rk_server_create(8 << 30, 16)
+    try:
+        # the first job alone
+        n, kap, tab, st = MIX[0]
+        d, s, t, u0 = job_args(rk, n, kap, tab, st, 0)
+        jid = rk.rk_submit_job(srv, d, s, *t, u0, dt, steps[0])
+        alone = np.empty(n ** 3)
+        rk.rk_wait_job(srv, jid, alone, allow_not_converged=True)
+        # the whole mix, submitted back to back so that jobs overlap
+        ids = []
+        for i, (n, kap, tab, st) in enumerate(MIX):
+            d, s, t, u0 = job_args(rk, n, kap, tab, st, i)
+            ids.append(rk.rk_submit_job(srv, d, s, *t, u0, dt, steps[i]))
+        outs, lats = [], []
+        for i, jid in enumerate(ids):
+            out = np.empty(MIX[i][0] ** 3)
+            stats, lat = rk.rk_wait_job(srv, jid, out, allow_not_converged=True)
+            outs.append(out)
+            lats.append(lat)
+    finally:
+        rk.rk_server_destroy(srv)
+    assert rel_l2(outs[0], alone) < BOUND["f32"]
+    for i, (n, kap, tab, st) in enumerate(MIX):
+        ref = solo(rk, n, kap, tab, st, i, dt, steps[i])
+        assert rel_l2(outs[i], ref) < BOUND[st], (i, n, tab, st)
+        assert lats[i] > 0
+
+
+def test_admission_under_budget_and_errors(rk):
+    dt = 1e-3
+    n = 48
+    d, s, t, u0 = job_args(rk, n, 1.0, "sdirk2", "f32", 3)
+    one = 8 * n ** 3 * 3 + 4 * n ** 3 * 4 + 8 * n ** 3 * 2 + 4 * n ** 3 * 3 + (1 << 20)
+    srv = rk.rk_server_create(int(2.5 * one), 4)  # about two jobs resident at a time
+    try:
+        ids = [rk.rk_submit_job(srv, d, s, *t, u0, dt, 2) for _ in range(5)]
+        outs = []
+        for jid in ids:
+            out = np.empty(n ** 3)
+            rk.rk_wait_job(srv, jid, out)
+            outs.append(out)
+        for o in outs[1:]:
+            assert rel_l2(o, outs[0]) < 1e-6
+        big = rk.problem_desc(n=256, kappa=1.0)
+        with pytest.raises(rk.RKError) as e:
+            rk.rk_submit_job(srv, big, s, *t, synth.sine_mode(256), dt, 1)
+        assert e.value.status == rk.RK_ERR_OOM
+        with pytest.raises(rk.RKError) as e:
+            rk.rk_poll_job(srv, 123456)
+        assert e.value.status == rk.RK_ERR_NOT_FOUND
+    finally:
+        rk.rk_server_destroy(srv)
+
+
+def test_poll_reports_completion(rk):
+    srv = rk.rk_server_create(1 << 30, 4)
+    try:
+        d, s, t, u0 = job_args(rk, 16, 1.0, "sdirk2", "f32", 1)
+        jid = rk.rk_submit_job(srv, d, s, *t, u0, 1e-3, 2)
+        t0 = time.time()
+        while not rk.rk_poll_job(srv, jid):
+            assert time.time() - t0 < 60
+            time.sleep(0.01)
+        st, lat = rk.rk_wait_job(srv, jid)
+        assert st.solves >= 1 and lat > 0
+    finally:
+        rk.rk_server_destroy(srv)
