@@ -230,6 +230,91 @@ def workload_config(name, cfg):
             "u0": "sine mode + 32 random modes (seed 0)", "l2": "working set > L2 (no flush needed)"}
 
 
+def run_batch(args):
+    """Batched workload: 512 independent heat problems (n uniform in 16..64,
+    kappa log-uniform in [0.1, 10], amplitude * sine mode), SDIRK2, dt 1e-3,
+    FP32 solves / FP64 corrections, --batch-steps steps in persistent
+    graph-captured launches.  Value = sum n^3 * steps / device seconds."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2412_16638_b300 as rk
+
+    torch.cuda.set_device(0)
+    probs = synth.batch_problems(512, seed=0)
+    tab = rk.tableaux.get("sdirk2")
+    dt = 1e-3
+    ps = [rk.Problem(rk.problem_desc(n=pr.n, kappa=pr.kappa),
+                     rk.solver_desc(bj_block=8, tol_rel=1e-6, storage="f32", max_iter=2000, correct=1),
+                     tableau=tab, u0=pr.amplitude * synth.sine_mode(pr.n)) for pr in probs]
+    handles = [p.h for p in ps]
+    rk.rk_integrate_batch(handles, dt, 1)  # warm-up (autotune)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = rk.rk_integrate_batch(handles, dt, args.batch_steps)
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    dof = sum(pr.n ** 3 for pr in probs)
+    line = {"metric": METRIC, "workload": "batch512", "value": dof * args.batch_steps / secs,
+            "unit": "DOF*steps/s", "problems": 512, "total_dof": dof, "steps": args.batch_steps,
+            "seconds": secs, "iters_per_solve": st.iters_total / max(st.solves, 1),
+            "true_res_max": st.true_res, "config": {"tableau": "sdirk2", "dt": dt, "storage": "f32",
+                                                    "bj_block": 8, "tol_rel": 1e-6, "n": "uniform 16..64",
+                                                    "kappa": "log-uniform [0.1, 10]"}}
+    for p in ps:
+        p.close()
+    print(json.dumps(line))
+    return 0
+
+
+def run_serve(args):
+    """Serving workload: Poisson arrivals (200 jobs/s) of --serve jobs, n in
+    {32, 64, 96, 128, 192}, tableau in {midpoint + 1 correction, SDIRK2,
+    DIRK3}, storage in {FP32, FP16}, 10..200 steps, kappa log-uniform in
+    [0.1, 10], dt 1e-3, 120 GB budget.  Reports p50/p99 latency (submit to
+    finish), aggregate DOF*steps/s over the makespan."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2412_16638_b300 as rk
+
+    torch.cuda.set_device(0)
+    jobs = synth.serve_jobs(args.serve, seed=0)
+    srv = rk.rk_server_create(120 << 30, args.serve_slots)
+    prepared = []
+    for jb in jobs:
+        d = rk.problem_desc(n=jb.n, kappa=jb.kappa)
+        sol = rk.solver_desc(bj_block=8, tol_rel=1e-6 if jb.storage == "f32" else 1e-3, storage=jb.storage,
+                             max_iter=2000, correct=1)
+        prepared.append((jb, d, sol, rk.tableaux.get(jb.tableau), jb.amplitude * synth.sine_mode(jb.n)))
+    t0 = time.perf_counter()
+    ids = []
+    for jb, d, sol, tab, u0 in prepared:
+        delay = jb.arrival - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        ids.append(rk.rk_submit_job(srv, d, sol, *tab, u0, 1e-3, jb.steps))
+    lats, service = [], []
+    for jid in ids:
+        st, lat = rk.rk_wait_job(srv, jid, None, allow_not_converged=True)
+        lats.append(lat)
+        service.append(st.seconds)
+    makespan = time.perf_counter() - t0
+    rk.rk_server_destroy(srv)
+    work = sum(jb.n ** 3 * jb.steps for jb in jobs)
+    line = {"metric": METRIC, "workload": "serve", "jobs": len(jobs), "value": work / makespan,
+            "unit": "DOF*steps/s", "makespan_s": makespan,
+            "latency_p50_s": float(np.percentile(lats, 50)), "latency_p99_s": float(np.percentile(lats, 99)),
+            "service_p50_s": float(np.percentile(service, 50)), "service_p99_s": float(np.percentile(service, 99)),
+            "config": {"arrival_rate_per_s": 200, "slots": args.serve_slots, "budget_bytes": 120 << 30,
+                       "sizes": [32, 64, 96, 128, 192], "tableaux": ["midpoint1", "sdirk2", "dirk3"],
+                       "storage": ["f32", "f16"], "steps": "uniform 10..200", "dt": 1e-3}}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -239,7 +324,15 @@ def main():
     ap.add_argument("--workload", default="heat256", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
+    ap.add_argument("--batch", action="store_true", help="run the 512-problem batched workload instead")
+    ap.add_argument("--batch-steps", type=int, default=50)
+    ap.add_argument("--serve", type=int, default=0, help="run the serving workload with this many jobs instead")
+    ap.add_argument("--serve-slots", type=int, default=64)
     args = ap.parse_args()
+    if args.batch:
+        return run_batch(args)
+    if args.serve:
+        return run_serve(args)
     cfg = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, cfg)
