@@ -296,18 +296,25 @@ def run_serve(args):
         if delay > 0:
             time.sleep(delay)
         ids.append(rk.rk_submit_job(srv, d, sol, *tab, u0, 1e-3, jb.steps))
-    lats, service = [], []
-    for jid in ids:
-        st, lat = rk.rk_wait_job(srv, jid, None, allow_not_converged=True)
-        lats.append(lat)
-        service.append(st.seconds)
+    lats, service, failed = [], [], {}
+    work = 0
+    for jid, (jb, *_rest) in zip(ids, prepared):
+        try:
+            st, lat = rk.rk_wait_job(srv, jid, None, allow_not_converged=True)
+            lats.append(lat)
+            service.append(st.seconds)
+            work += jb.n ** 3 * jb.steps
+        except rk.RKError as e:
+            # a job that diverged (non-finite state) is reported, not timed
+            key = "%s/%s/n%d: status %d" % (jb.tableau, jb.storage, jb.n, e.status)
+            failed[key] = failed.get(key, 0) + 1
     makespan = time.perf_counter() - t0
     rk.rk_server_destroy(srv)
-    work = sum(jb.n ** 3 * jb.steps for jb in jobs)
     line = {"metric": METRIC, "workload": "serve", "jobs": len(jobs), "value": work / makespan,
             "unit": "DOF*steps/s", "makespan_s": makespan,
             "latency_p50_s": float(np.percentile(lats, 50)), "latency_p99_s": float(np.percentile(lats, 99)),
             "service_p50_s": float(np.percentile(service, 50)), "service_p99_s": float(np.percentile(service, 99)),
+            "completed": len(lats), "failed": failed,
             "config": {"arrival_rate_per_s": 200, "slots": args.serve_slots, "budget_bytes": 120 << 30,
                        "sizes": [32, 64, 96, 128, 192], "tableaux": ["midpoint1", "sdirk2", "dirk3"],
                        "storage": ["f32", "f16"], "steps": "uniform 10..200", "dt": 1e-3}}
