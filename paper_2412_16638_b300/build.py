@@ -31,8 +31,23 @@ def _newest_header():
     return max((os.path.getmtime(h) for h in hs), default=0.0)
 
 
+def _deps_newer(obj):
+    """True when a header recorded in obj's dependency file is newer than obj."""
+    dep = obj[:-2] + ".d"
+    if not os.path.exists(dep):
+        return True
+    t = os.path.getmtime(obj)
+    text = open(dep).read().replace("\\\n", " ")
+    for tok in text.split(":", 1)[-1].split():
+        if tok.startswith("/usr/") or not os.path.exists(tok):
+            continue
+        if os.path.getmtime(tok) > t:
+            return True
+    return False
+
+
 def _compile(src, obj, verbose):
-    cmd = [NVCC] + ARCH + FLAGS + ["-c", src, "-o", obj]
+    cmd = [NVCC] + ARCH + FLAGS + ["-MD", "-MF", obj[:-2] + ".d", "-c", src, "-o", obj]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -44,13 +59,12 @@ def _compile(src, obj, verbose):
 def build(verbose: bool = False, jobs: int = 8) -> str:
     os.makedirs(BUILD, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
-    hdr = _newest_header()
     todo = []
     objs = []
     for s in srcs:
         o = os.path.join(BUILD, os.path.basename(s)[:-3] + ".o")
         objs.append(o)
-        if verbose or not os.path.exists(o) or os.path.getmtime(o) < max(os.path.getmtime(s), hdr):
+        if verbose or not os.path.exists(o) or os.path.getmtime(o) < os.path.getmtime(s) or _deps_newer(o):
             todo.append((s, o))
     with concurrent.futures.ThreadPoolExecutor(max_workers=jobs) as ex:
         for log in ex.map(lambda so: _compile(so[0], so[1], verbose), todo):

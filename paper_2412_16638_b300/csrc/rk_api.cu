@@ -2,7 +2,9 @@
 // driver and the kernel-level test entry points.
 #include <cmath>
 #include <cstdarg>
+#include <cstdlib>
 #include <mutex>
+#include <type_traits>
 #include <unordered_map>
 
 #include "rk_internal.h"
@@ -180,6 +182,89 @@ rk_status op_correct_f64(rk_problem* p, double shift, const double* gv, const vo
   return st;
 }
 
+// ------------------------------------------------------------ tiled sweeps
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!tried) {
+    tried = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(f);
+    cudaGetLastError();
+  }
+  return fn;
+}
+
+template <typename S>
+static CUtensorMapDataType tma_dtype() {
+  if (sizeof(S) == 8) return CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+  if (sizeof(S) == 4) return CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  return std::is_same<S, __half>::value ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+}
+
+// Decide once per problem whether the tiled sweeps apply (n <= 256, n a
+// multiple of the segment, 16-byte row stride, shared memory fits) and build
+// the tensor maps of r, p0, p1.  Returns false to keep the per-segment kernels.
+template <typename S, typename T, int BS, int SEG>
+static bool tiled_setup(rk_problem* p) {
+  if (!p->tiled) p->tiled = new TiledMaps();
+  TiledMaps& tm = *p->tiled;
+  if (tm.tried) return tm.ok;
+  tm.tried = true;
+  if (std::getenv("RK_NO_TILED")) return false;
+  const int n = p->n;
+  if (n > 256 || n % SEG != 0 || ((size_t)n * sizeof(S)) % 16 != 0) return false;
+  const int tpl = n / SEG;
+  if (tpl > 256) return false;
+  int ty = 0;
+  for (int c = 1; c <= n; ++c)
+    if (n % c == 0 && c * tpl <= 256 && c + 2 <= 256) ty = c;
+  if (ty == 0) return false;
+  const size_t sa = tiled_smem_a<S, T, BS>(n, ty), sb = tiled_smem_b<S, T, BS>(n, ty);
+  if (sa > 200 * 1024 || sb > 200 * 1024) return false;
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)n};
+  const cuuint64_t strides[2] = {(cuuint64_t)n * sizeof(S), (cuuint64_t)n * n * sizeof(S)};
+  const cuuint32_t box[3] = {(cuuint32_t)n, (cuuint32_t)(ty + 2), 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  void* bufs[3] = {p->wr, p->wp[0], p->wp[1]};
+  CUtensorMap* maps[3] = {&tm.r, &tm.p[0], &tm.p[1]};
+  for (int i = 0; i < 3; ++i) {
+    if (enc(maps[i], tma_dtype<S>(), 3, bufs[i], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  }
+  auto ka = cg_tiled_a<S, T, BS, SEG>;
+  auto kb = cg_tiled_b<S, T, BS, SEG>;
+  if (cudaFuncSetAttribute((const void*)ka, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa) != cudaSuccess ||
+      cudaFuncSetAttribute((const void*)kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  int occa = 0, occb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occa, ka, ty * tpl, sa) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occb, kb, ty * tpl, sb) != cudaSuccess || occa < 1 || occb < 1) {
+    cudaGetLastError();
+    return false;
+  }
+  const int nyt = n / ty;
+  const int slots = device_sms() * std::min(occa, occb);
+  tm.tg = TileGeo{n, tpl, ty, nyt, std::max(1, std::min(n, slots / nyt))};
+  tm.ok = true;
+  return true;
+}
+
 // Chunked device-resident CG: after cg_init, sweeps A and B are launched in
 // chunks; each sweep returns at once when the device flag `done` is set, and
 // the host reads the flag back once per chunk.  The first chunk is sized by
@@ -219,6 +304,11 @@ static rk_status heat_cg_solve(rk_problem* p, double shift, const double* g64, R
       const double Nx = (double)p->N * sizeof(X);
       launch(p, K_CG_INIT, 8.0 * p->N + 2.0 * Ns + Nx,
              [&] { ki<<<gi, kThreads, 0, p->st>>>(g, g64, rs, M, r, z, xs, p->sc, p->partials); });
+      const bool tiled = tiled_setup<S, T, BS, SEG>(p);
+      const TileGeo tg = tiled ? p->tiled->tg : TileGeo{};
+      const int tgrid = tg.nyt * tg.nzc, tthreads = tg.tpl * tg.ty;
+      const size_t sma = tiled ? tiled_smem_a<S, T, BS>(tg.n, tg.ty) : 0;
+      const size_t smb = tiled ? tiled_smem_b<S, T, BS>(tg.n, tg.ty) : 0;
       int launched = 0, cur = 0;
       const int predicted = p->last_iters[slot] > 0 ? p->last_iters[slot] : 8;
       int chunk = std::max(2, predicted - 1);
@@ -227,12 +317,24 @@ static rk_status heat_cg_solve(rk_problem* p, double shift, const double* g64, R
           S* pn = static_cast<S*>(p->wp[cur]);
           const S* po = static_cast<const S*>(p->wp[cur ^ 1]);
           const int idx = launched + c;
-          prof_begin(p, K_CG_A, (idx == 0 ? 2.0 : 3.0) * Ns, solve, idx);
-          ka<<<ga, kThreads, 0, p->st>>>(g, d, o, z, po, pn, p->sc, p->partials);
-          prof_end(p);
-          prof_begin(p, K_CG_B, (idx == 0 ? 4.0 * Ns + Nx : 4.0 * Ns + 2.0 * Nx), solve, idx);
-          kb<<<gb, kThreads, 0, p->st>>>(g, d, o, pn, xs, r, z, M, p->sc, p->partials);
-          prof_end(p);
+          if (tiled) {
+            // 8 vectors per iteration: A reads r, p_old, writes p; B reads p, r, x, writes r, x
+            prof_begin(p, K_CG_A, (idx == 0 ? 2.0 : 3.0) * Ns, solve, idx);
+            cg_tiled_a<S, T, BS, SEG><<<tgrid, tthreads, sma, p->st>>>(p->tiled->r, p->tiled->p[cur ^ 1], tg, d, o, M,
+                                                                       pn, p->sc, p->partials);
+            prof_end(p);
+            prof_begin(p, K_CG_B, (idx == 0 ? 3.0 * Ns + Nx : 3.0 * Ns + 2.0 * Nx), solve, idx);
+            cg_tiled_b<S, T, BS, SEG><<<tgrid, tthreads, smb, p->st>>>(p->tiled->p[cur], tg, d, o, M, xs, r, p->sc,
+                                                                       p->partials);
+            prof_end(p);
+          } else {
+            prof_begin(p, K_CG_A, (idx == 0 ? 2.0 : 3.0) * Ns, solve, idx);
+            ka<<<ga, kThreads, 0, p->st>>>(g, d, o, z, po, pn, p->sc, p->partials);
+            prof_end(p);
+            prof_begin(p, K_CG_B, (idx == 0 ? 4.0 * Ns + Nx : 4.0 * Ns + 2.0 * Nx), solve, idx);
+            kb<<<gb, kThreads, 0, p->st>>>(g, d, o, pn, xs, r, z, M, p->sc, p->partials);
+            prof_end(p);
+          }
           cur ^= 1;
         }
         launched += chunk;
@@ -361,6 +463,10 @@ rk_status step_impl(rk_problem* p, double dt, rk_stats* acc) {
     if (status == 5) {
       set_error("stage %d solve: non-finite value or Krylov breakdown", i);
       return RK_ERR_NONFINITE;
+    }
+    if (status == 6) {
+      set_error("stage %d solve: a bounded device wait for a TMA tile gave up", i);
+      return RK_ERR_TIMEOUT;
     }
     if (status == 4) worst = RK_ERR_NOT_CONVERGED;
     if (mixed) {
@@ -516,6 +622,7 @@ static void free_problem(rk_problem* p) {
   if (p->h_rs) cudaFreeHost(p->h_rs);
   csr_free(p);
   prof_free(p);
+  delete p->tiled;
   delete p;
 }
 
@@ -804,6 +911,10 @@ rk_status rk_solve(rk_problem* p, double shift, const double* g, double* k, int 
   if (status == 5) {
     set_error("solve: non-finite value or Krylov breakdown");
     return RK_ERR_NONFINITE;
+  }
+  if (status == 6) {
+    set_error("solve: a bounded device wait for a TMA tile gave up");
+    return RK_ERR_TIMEOUT;
   }
   return status == 4 ? RK_ERR_NOT_CONVERGED : RK_OK;
 }

@@ -199,8 +199,12 @@ struct BatchStep {
       cta_allreduce<1, 0u>(acc1, sred, sbc);
       const double pAp = acc1[0];
       const double alpha = rz / pAp;
-      if (!(pAp > 0.0) || !isfinite(alpha)) {
+      if (!isfinite(pAp) || !isfinite(rz)) {
         *status = 5;
+        return it;
+      }
+      if (!(pAp > 0.0) || !isfinite(alpha)) {  // attainable accuracy reached
+        *status = 4;
         return it;
       }
       // sweep B

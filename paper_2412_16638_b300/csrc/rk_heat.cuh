@@ -295,9 +295,14 @@ __global__ void __launch_bounds__(kThreads) cg_sweep_a(HeatGeo g, T d, T o, cons
     sc->pAp = tot[0];
     const double alpha = sc->rz / tot[0];
     sc->alpha = alpha;
-    if (!(tot[0] > 0.0) || !isfinite(alpha)) {
+    if (!isfinite(tot[0]) || !isfinite(sc->rz)) {
       sc->done = 1;
       sc->status = 5;
+    } else if (!(tot[0] > 0.0) || !isfinite(alpha)) {
+      // p.Ap <= 0 for an SPD operator: rounding has reached the attainable
+      // accuracy; stop with the current iterate (valid, not converged)
+      sc->done = 1;
+      sc->status = 4;
     }
   }
 }

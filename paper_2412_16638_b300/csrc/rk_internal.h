@@ -15,6 +15,7 @@
 #include "rk_device.cuh"
 #include "rk_heat.cuh"
 #include "rk_vec.cuh"
+#include "rk_tiled.cuh"
 
 namespace rk {
 
@@ -95,6 +96,14 @@ struct Csr {
 
 struct GmresWork;  // defined in rk_csr.cu
 
+// TMA descriptors of the CG work vectors for the tiled sweeps.
+struct TiledMaps {
+  bool ok = false;       // set up and usable
+  bool tried = false;    // eligibility already decided
+  TileGeo tg{};
+  CUtensorMap r, p[2];   // r and the two p buffers, box (n, ty+2, 1)
+};
+
 // Kernel ids for the launch profiler.
 enum Kid {
   K_CG_INIT, K_CG_A, K_CG_B, K_OP, K_CORRECT, K_COMBINE, K_NORMS, K_WIDEN, K_TRUERES, K_ADDSCALED, K_BJ,
@@ -158,6 +167,7 @@ struct rk_problem {
   // CSR path
   rk::Csr csr;
   rk::GmresWork* gw = nullptr;
+  rk::TiledMaps* tiled = nullptr;
   size_t bytes = 0;  // device footprint
   // launch accounting / profiler
   long long launches = 0;

@@ -1,0 +1,380 @@
+// TMA-fed 2.5D CG sweeps for the constant-coefficient heat stencil.
+//
+// A CTA owns a tile of TY full x-lines (y0 .. y0+TY-1) and marches in z over
+// a chunk of planes.  For every plane one elected thread issues 3-D TMA tile
+// loads (cp.async.bulk.tensor) of (n x (TY+2) x 1) elements -- the tile plus
+// one halo line on each side in y -- into a ring of shared-memory stages,
+// completion tracked by an mbarrier per stage.  Tiles that reach outside the
+// grid are zero-filled by the TMA unit, which is exactly the homogeneous
+// Dirichlet boundary, so no boundary test is needed in the stencil.
+//
+// Compared with the per-segment kernels, every input element is fetched from
+// global memory once per sweep (plus the y halo, shared with the neighbouring
+// tile through L2), and loads run two planes ahead of the arithmetic.  The
+// preconditioned residual z = D^{-1} r is recomputed from r inside sweep A
+// instead of being stored, so one CG iteration moves 8 vectors instead of 9:
+//   sweep A reads r, p_old and writes p        (3 vectors)
+//   sweep B reads p, r, x and writes r, x      (5 vectors)
+#pragma once
+#include <cuda.h>
+
+#include "rk_device.cuh"
+#include "rk_heat.cuh"
+
+namespace rk {
+
+struct TileGeo {
+  int n;    // nodes per direction (n % SEG == 0, n <= 256)
+  int tpl;  // threads per x-line = n / SEG
+  int ty;   // lines per tile (divides n)
+  int nyt;  // tiles in y = n / ty
+  int nzc;  // z chunks
+};
+
+constexpr int kStagesA = 3;  // input stages of sweep A (r, p_old tiles)
+constexpr int kStagesB = 4;  // p-tile stages of sweep B (planes k-1, k, k+1 + one in flight)
+constexpr unsigned kWaitSpins = 1u << 24;
+
+__host__ __device__ constexpr size_t align128(size_t v) { return (v + 127) / 128 * 128; }
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: false after kWaitSpins unsuccessful polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (unsigned i = 0; i < kWaitSpins; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 3-D tile load (x, y, z are element coordinates; x must be 0 here, which is
+// 16-byte aligned; y and z may be out of range and read as zero).
+__device__ __forceinline__ void tma_load3(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(
+          smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_addr(bar)), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+
+template <typename T, typename S, int SEG>
+__device__ __forceinline__ void lds_seg(const S* p, T (&v)[SEG]) {
+  // p is 16-byte aligned when SEG*sizeof(S) is a multiple of 16
+  load_seg<T, S, SEG>(p, SEG, v);
+}
+
+// ----------------------------------------------------------------- sweep A
+// p = D^{-1} r + beta p_old on every plane of the chunk (and its z halo, in a
+// 3-plane shared ring), then q = A p and the partial p.q on the owned lines;
+// p written to pnew.  Last CTA: alpha = r.z / p.q.
+template <typename S, typename T, int BS, int SEG>
+__global__ void __launch_bounds__(256, 2) cg_tiled_a(const __grid_constant__ CUtensorMap tm_r,
+                                                  const __grid_constant__ CUtensorMap tm_po, TileGeo tg, T d, T o,
+                                                  const T* __restrict__ minv, S* __restrict__ pnew, CgScalars* sc,
+                                                  double* partials) {
+  if (sc->done) return;
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int n = tg.n, TY = tg.ty, R = TY + 2;
+  const size_t tile = align128((size_t)R * n * sizeof(S));
+  unsigned char* base = smem;
+  auto st_r = [&](int s) { return reinterpret_cast<S*>(base + (size_t)s * 2 * tile); };
+  auto st_p = [&](int s) { return reinterpret_cast<S*>(base + (size_t)s * 2 * tile + tile); };
+  auto ring = [&](int s) { return reinterpret_cast<S*>(base + (size_t)kStagesA * 2 * tile + (size_t)s * tile); };
+  T* sM = reinterpret_cast<T*>(base + (size_t)(kStagesA * 2 + 3) * tile);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(base + (size_t)(kStagesA * 2 + 3) * tile +
+                                              align128(2 * BS * BS * sizeof(T)));
+  const int tid = threadIdx.x;
+  const int tx = tid % tg.tpl, ly = tid / tg.tpl;
+  const int yt = blockIdx.x % tg.nyt, zc = blockIdx.x / tg.nyt;
+  const int y0 = yt * TY;
+  const int z0 = (int)((long long)zc * n / tg.nzc), z1 = (int)((long long)(zc + 1) * n / tg.nzc);
+  const int L = z1 - z0 + 2;  // planes z0-1 .. z1
+  const T beta = (T)sc->beta;
+  const bool first = (sc->iter == 0);
+  const uint32_t tx_bytes = (first ? 1u : 2u) * (uint32_t)(R * n * sizeof(S));
+  for (int i = tid; i < 2 * BS * BS; i += blockDim.x) sM[i] = minv[i];
+  if (tid == 0) {
+    for (int s = 0; s < kStagesA; ++s) mbar_init(&bar[s], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  auto issue = [&](int t) {
+    const int s = t % kStagesA;
+    mbar_expect_tx(&bar[s], tx_bytes);
+    tma_load3(st_r(s), &tm_r, &bar[s], 0, y0 - 1, z0 - 1 + t);
+    if (!first) tma_load3(st_p(s), &tm_po, &bar[s], 0, y0 - 1, z0 - 1 + t);
+  };
+  if (tid == 0)
+    for (int t = 0; t < kStagesA && t < L; ++t) issue(t);
+  const int xs = tx * SEG;
+  double acc[1] = {0.0};
+  bool timed_out = false;
+  int issued = (kStagesA < L) ? kStagesA : L;
+  for (int t = 0; t < L; ++t) {
+    const int s = t % kStagesA;
+    const bool ok = mbar_wait(&bar[s], (uint32_t)((t / kStagesA) & 1));
+    if (__syncthreads_or(!ok)) {
+      timed_out = true;
+      break;
+    }
+    // p on plane z0-1+t for the owned line and, at the tile edges, the halo lines
+    S* rp = ring(t % 3);
+    auto compute_line = [&](int l) {
+      T rv[SEG], zv[SEG];
+      lds_seg<T, S, SEG>(st_r(s) + (size_t)l * n + xs, rv);
+      bj_apply<T, BS, SEG>(sM, n, xs, rv, zv);
+      if (!first) {
+        T pv[SEG];
+        lds_seg<T, S, SEG>(st_p(s) + (size_t)l * n + xs, pv);
+#pragma unroll
+        for (int e = 0; e < SEG; ++e) zv[e] = fma(beta, pv[e], zv[e]);
+      }
+#pragma unroll
+      for (int e = 0; e < SEG; ++e) zv[e] = rnd<S, T>(zv[e]);
+      store_seg<S, T, SEG>(rp + (size_t)l * n + xs, SEG, zv);
+    };
+    compute_line(ly + 1);
+    if (ly == 0) compute_line(0);
+    if (ly == TY - 1) compute_line(TY + 1);
+    __syncthreads();
+    if (tid == 0 && issued < L) {
+      fence_proxy_async();
+      issue(issued);
+      ++issued;
+    }
+    if (t >= 2) {
+      const S* pm = ring((t - 2) % 3);
+      const S* pc = ring((t - 1) % 3);
+      const S* pp = ring(t % 3);
+      const int l = ly + 1;
+      T c[SEG], a[SEG], b[SEG], zm[SEG], zp[SEG];
+      lds_seg<T, S, SEG>(pc + (size_t)l * n + xs, c);
+      lds_seg<T, S, SEG>(pc + (size_t)(l - 1) * n + xs, a);
+      lds_seg<T, S, SEG>(pc + (size_t)(l + 1) * n + xs, b);
+      lds_seg<T, S, SEG>(pm + (size_t)l * n + xs, zm);
+      lds_seg<T, S, SEG>(pp + (size_t)l * n + xs, zp);
+      const T left = (xs > 0) ? wid<T>(pc[(size_t)l * n + xs - 1]) : T(0);
+      const T right = (xs + SEG < n) ? wid<T>(pc[(size_t)l * n + xs + SEG]) : T(0);
+      T pw = T(0);
+#pragma unroll
+      for (int e = 0; e < SEG; ++e) {
+        const T xl = (e > 0) ? c[e - 1] : left;
+        const T xr = (e + 1 < SEG) ? c[e + 1] : right;
+        const T nb = ((xl + xr) + (a[e] + b[e])) + (zm[e] + zp[e]);
+        const T w = fma(d, c[e], o * nb);
+        pw = fma(c[e], w, pw);
+      }
+      acc[0] += (double)pw;
+      const int k = z0 + t - 2;
+      store_seg<S, T, SEG>(pnew + ((size_t)k * n + (y0 + ly)) * n + xs, SEG, c);
+    }
+    __syncthreads();
+  }
+  if (timed_out) {
+    // let copies that are still in flight land before the CTA exits
+    if (tid == 0) {
+      for (int t = issued - kStagesA; t < issued; ++t)
+        if (t >= 0) (void)mbar_wait(&bar[t % kStagesA], (uint32_t)((t / kStagesA) & 1));
+      sc->status = 6;
+      sc->done = 1;
+    }
+    __syncthreads();
+  }
+  double tot[1];
+  if (grid_reduce<1, 0u>(acc, partials, &sc->ticket, tot)) {
+    if (sc->status == 6) return;
+    sc->pAp = tot[0];
+    const double alpha = sc->rz / tot[0];
+    sc->alpha = alpha;
+    if (!isfinite(tot[0]) || !isfinite(sc->rz)) {
+      sc->done = 1;
+      sc->status = 5;
+    } else if (!(tot[0] > 0.0) || !isfinite(alpha)) {
+      sc->done = 1;
+      sc->status = 4;
+    }
+  }
+}
+
+// ----------------------------------------------------------------- sweep B
+// q = A p from the TMA ring, r -= alpha q, x += alpha p, z = D^{-1} r in
+// registers, partial r.z and r.r; r and x written.  Last CTA: beta and the
+// convergence test.
+template <typename S, typename T, int BS, int SEG>
+__global__ void __launch_bounds__(256, 2) cg_tiled_b(const __grid_constant__ CUtensorMap tm_p, TileGeo tg, T d, T o,
+                                                  const T* __restrict__ minv, typename XOf<S>::type* __restrict__ x,
+                                                  S* __restrict__ r, CgScalars* sc, double* partials) {
+  using X = typename XOf<S>::type;
+  if (sc->done) return;
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int n = tg.n, TY = tg.ty, R = TY + 2;
+  const size_t tile = align128((size_t)R * n * sizeof(S));
+  auto st = [&](int s) { return reinterpret_cast<S*>(smem + (size_t)s * tile); };
+  T* sM = reinterpret_cast<T*>(smem + (size_t)kStagesB * tile);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + (size_t)kStagesB * tile + align128(2 * BS * BS * sizeof(T)));
+  const int tid = threadIdx.x;
+  const int tx = tid % tg.tpl, ly = tid / tg.tpl;
+  const int yt = blockIdx.x % tg.nyt, zc = blockIdx.x / tg.nyt;
+  const int y0 = yt * TY;
+  const int z0 = (int)((long long)zc * n / tg.nzc), z1 = (int)((long long)(zc + 1) * n / tg.nzc);
+  const int L = z1 - z0 + 2;
+  const T alpha = (T)sc->alpha;
+  const bool first = (sc->iter == 0);
+  const uint32_t tx_bytes = (uint32_t)(R * n * sizeof(S));
+  for (int i = tid; i < 2 * BS * BS; i += blockDim.x) sM[i] = minv[i];
+  if (tid == 0) {
+    for (int s = 0; s < kStagesB; ++s) mbar_init(&bar[s], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  auto issue = [&](int t) {
+    const int s = t % kStagesB;
+    mbar_expect_tx(&bar[s], tx_bytes);
+    tma_load3(st(s), &tm_p, &bar[s], 0, y0 - 1, z0 - 1 + t);
+  };
+  if (tid == 0)
+    for (int t = 0; t < kStagesB && t < L; ++t) issue(t);
+  int issued = (kStagesB < L) ? kStagesB : L;
+  const int xs = tx * SEG;
+  const size_t line_off = (size_t)(y0 + ly) * n + xs;
+  // r and x of the first owned plane, prefetched into registers
+  T rn[SEG], xn[SEG];
+  load_seg<T, S, SEG>(r + (size_t)z0 * n * n + line_off, SEG, rn);
+  if (!first) {
+    load_seg<T, X, SEG>(x + (size_t)z0 * n * n + line_off, SEG, xn);
+  } else {
+#pragma unroll
+    for (int e = 0; e < SEG; ++e) xn[e] = T(0);
+  }
+  double acc[2] = {0.0, 0.0};
+  bool timed_out = false;
+  for (int t = 0; t < L; ++t) {
+    const int s = t % kStagesB;
+    const bool ok = mbar_wait(&bar[s], (uint32_t)((t / kStagesB) & 1));
+    if (__syncthreads_or(!ok)) {
+      timed_out = true;
+      break;
+    }
+    if (t >= 2) {
+      const int k = z0 + t - 2;
+      T rv[SEG], xv[SEG];
+#pragma unroll
+      for (int e = 0; e < SEG; ++e) {
+        rv[e] = rn[e];
+        xv[e] = xn[e];
+      }
+      if (k + 1 < z1) {
+        load_seg<T, S, SEG>(r + (size_t)(k + 1) * n * n + line_off, SEG, rn);
+        if (!first) load_seg<T, X, SEG>(x + (size_t)(k + 1) * n * n + line_off, SEG, xn);
+      }
+      const S* pm = st((t - 2) % kStagesB);
+      const S* pc = st((t - 1) % kStagesB);
+      const S* pp = st(t % kStagesB);
+      const int l = ly + 1;
+      T c[SEG], a[SEG], b[SEG], zm[SEG], zp[SEG];
+      lds_seg<T, S, SEG>(pc + (size_t)l * n + xs, c);
+      lds_seg<T, S, SEG>(pc + (size_t)(l - 1) * n + xs, a);
+      lds_seg<T, S, SEG>(pc + (size_t)(l + 1) * n + xs, b);
+      lds_seg<T, S, SEG>(pm + (size_t)l * n + xs, zm);
+      lds_seg<T, S, SEG>(pp + (size_t)l * n + xs, zp);
+      const T left = (xs > 0) ? wid<T>(pc[(size_t)l * n + xs - 1]) : T(0);
+      const T right = (xs + SEG < n) ? wid<T>(pc[(size_t)l * n + xs + SEG]) : T(0);
+#pragma unroll
+      for (int e = 0; e < SEG; ++e) {
+        const T xl = (e > 0) ? c[e - 1] : left;
+        const T xr = (e + 1 < SEG) ? c[e + 1] : right;
+        const T nb = ((xl + xr) + (a[e] + b[e])) + (zm[e] + zp[e]);
+        const T w = fma(d, c[e], o * nb);
+        rv[e] = rnd<S, T>(fma(-alpha, w, rv[e]));
+        xv[e] = fma(alpha, c[e], xv[e]);
+      }
+      T zv[SEG];
+      bj_apply<T, BS, SEG>(sM, n, xs, rv, zv);
+      T rz = T(0), rr = T(0);
+#pragma unroll
+      for (int e = 0; e < SEG; ++e) {
+        zv[e] = rnd<S, T>(zv[e]);
+        rz = fma(rv[e], zv[e], rz);
+        rr = fma(rv[e], rv[e], rr);
+      }
+      acc[0] += (double)rz;
+      acc[1] += (double)rr;
+      store_seg<S, T, SEG>(r + (size_t)k * n * n + line_off, SEG, rv);
+      store_seg<X, T, SEG>(x + (size_t)k * n * n + line_off, SEG, xv);
+    }
+    __syncthreads();
+    if (tid == 0 && t >= 2 && issued < L) {
+      fence_proxy_async();
+      issue(issued);
+      ++issued;
+    }
+  }
+  if (timed_out) {
+    if (tid == 0) {
+      for (int t = issued - kStagesB; t < issued; ++t)
+        if (t >= 0) (void)mbar_wait(&bar[t % kStagesB], (uint32_t)((t / kStagesB) & 1));
+      sc->status = 6;
+      sc->done = 1;
+    }
+    __syncthreads();
+  }
+  double tot[2];
+  if (grid_reduce<2, 0u>(acc, partials, &sc->ticket, tot)) {
+    if (sc->status == 6) return;
+    const double rz_new = tot[0];
+    sc->beta = rz_new / sc->rz;
+    sc->rz = rz_new;
+    sc->rr = tot[1];
+    sc->iter += 1;
+    if (!isfinite(tot[0]) || !isfinite(tot[1])) {
+      sc->done = 1;
+      sc->status = 5;
+    } else if (tot[1] <= sc->thresh2) {
+      sc->done = 1;
+      sc->status = 0;
+    } else if (sc->iter >= sc->max_iter) {
+      sc->done = 1;
+      sc->status = 4;
+    }
+  }
+}
+
+// Shared-memory bytes of the two sweeps.
+template <typename S, typename T, int BS>
+__host__ constexpr size_t tiled_smem_a(int n, int ty) {
+  return (size_t)(kStagesA * 2 + 3) * align128((size_t)(ty + 2) * n * sizeof(S)) +
+         align128(2 * BS * BS * sizeof(T)) + 8 * kStagesA;
+}
+template <typename S, typename T, int BS>
+__host__ constexpr size_t tiled_smem_b(int n, int ty) {
+  return (size_t)kStagesB * align128((size_t)(ty + 2) * n * sizeof(S)) + align128(2 * BS * BS * sizeof(T)) +
+         8 * kStagesB;
+}
+
+}  // namespace rk

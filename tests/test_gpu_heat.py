@@ -190,3 +190,29 @@ def test_full_size_256_closed_form(rk):
     exact = mode_sum_after(modes, n, 1.0, dt, steps, A_hi + A_lo, b)
     assert rel_l2(u, exact) < 1e-6
     assert st.solves == 4 and st.true_res < 1e-4
+
+
+@pytest.mark.parametrize("n,storage,bs", [(64, "f32", 8), (96, "f16", 8), (128, "f64", 4), (32, "bf16", 16),
+                                          (256, "f32", 32)])
+def test_tiled_sweeps_match_segment_sweeps(rk, n, storage, bs, monkeypatch):
+    """The TMA-tiled CG sweeps (chosen when n <= 256 and rows are 16-byte
+    aligned) and the per-segment sweeps solve the same system to the solver
+    tolerance; both agree with the oracle's converged solution."""
+    shift = 2.5e-4
+    tol = {"f64": 1e-11, "f32": 1e-6, "f16": 1e-3, "bf16": 5e-3}[storage]
+    g = operators.heat_apply(synth.heat_modes(seed=6, n_random=6).evaluate(n), n, 1.0)
+    out = {}
+    for mode in ("tiled", "segments"):
+        if mode == "segments":
+            monkeypatch.setenv("RK_NO_TILED", "1")
+        with make(rk, n, storage=storage, bs=bs, tol=tol, max_iter=3000) as p:
+            k = np.empty_like(g)
+            st = rk.rk_solve(p.h, shift, g, k, allow_not_converged=True)
+            out[mode] = (k, st.iters_total)
+    M = krylov.shifted(operators.heat_csr(n, 1.0), shift) if n <= 64 else None
+    bound = {"f64": 1e-9, "f32": 2e-5, "f16": 5e-3, "bf16": 3e-2}[storage]
+    assert rel_l2(out["tiled"][0], out["segments"][0]) < bound
+    assert abs(out["tiled"][1] - out["segments"][1]) <= max(2, out["segments"][1] // 10)
+    if M is not None:
+        ref = krylov.pcg(lambda v: M @ v, krylov.BlockJacobi(M, n, bs).apply, g, tol_rel=1e-12).x
+        assert rel_l2(out["tiled"][0], ref) < bound
