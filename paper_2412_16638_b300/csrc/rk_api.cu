@@ -225,9 +225,9 @@ static bool tiled_setup(rk_problem* p) {
   if (n > 256 || n % SEG != 0 || ((size_t)n * sizeof(S)) % 16 != 0) return false;
   const int tpl = n / SEG;
   if (tpl > 256) return false;
-  int ty = 0;
+  int ty = 0;  // sweep A runs tpl*(ty+2) threads (<= 320), sweep B tpl*ty (<= 256)
   for (int c = 1; c <= n; ++c)
-    if (n % c == 0 && c * tpl <= 256 && c + 2 <= 256) ty = c;
+    if (n % c == 0 && c * tpl <= 256 && (c + 2) * tpl <= 320 && c + 2 <= 256) ty = c;
   if (ty == 0) return false;
   const size_t sa = tiled_smem_a<S, T, BS>(n, ty), sb = tiled_smem_b<S, T, BS>(n, ty);
   if (sa > 200 * 1024 || sb > 200 * 1024) return false;
@@ -253,7 +253,7 @@ static bool tiled_setup(rk_problem* p) {
     return false;
   }
   int occa = 0, occb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occa, ka, ty * tpl, sa) != cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occa, ka, (ty + 2) * tpl, sa) != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occb, kb, ty * tpl, sb) != cudaSuccess || occa < 1 || occb < 1) {
     cudaGetLastError();
     return false;
@@ -306,7 +306,7 @@ static rk_status heat_cg_solve(rk_problem* p, double shift, const double* g64, R
              [&] { ki<<<gi, kThreads, 0, p->st>>>(g, g64, rs, M, r, z, xs, p->sc, p->partials); });
       const bool tiled = tiled_setup<S, T, BS, SEG>(p);
       const TileGeo tg = tiled ? p->tiled->tg : TileGeo{};
-      const int tgrid = tg.nyt * tg.nzc, tthreads = tg.tpl * tg.ty;
+      const int tgrid = tg.nyt * tg.nzc, tthreads = tg.tpl * tg.ty, athreads = tg.tpl * (tg.ty + 2);
       const size_t sma = tiled ? tiled_smem_a<S, T, BS>(tg.n, tg.ty) : 0;
       const size_t smb = tiled ? tiled_smem_b<S, T, BS>(tg.n, tg.ty) : 0;
       int launched = 0, cur = 0;
@@ -320,7 +320,7 @@ static rk_status heat_cg_solve(rk_problem* p, double shift, const double* g64, R
           if (tiled) {
             // 8 vectors per iteration: A reads r, p_old, writes p; B reads p, r, x, writes r, x
             prof_begin(p, K_CG_A, (idx == 0 ? 2.0 : 3.0) * Ns, solve, idx);
-            cg_tiled_a<S, T, BS, SEG><<<tgrid, tthreads, sma, p->st>>>(p->tiled->r, p->tiled->p[cur ^ 1], tg, d, o, M,
+            cg_tiled_a<S, T, BS, SEG><<<tgrid, athreads, sma, p->st>>>(p->tiled->r, p->tiled->p[cur ^ 1], tg, d, o, M,
                                                                        pn, p->sc, p->partials);
             prof_end(p);
             prof_begin(p, K_CG_B, (idx == 0 ? 3.0 * Ns + Nx : 3.0 * Ns + 2.0 * Nx), solve, idx);

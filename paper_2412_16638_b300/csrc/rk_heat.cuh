@@ -256,13 +256,13 @@ __global__ void __launch_bounds__(kThreads) cg_init(HeatGeo g, const double* __r
 // Sweep A: p = z + beta*p_old (rounded to S), w = A p with A = d I + o*(neighbour
 // sum), partial p.w.  Writes p to pnew (ping-pong buffer).  Last CTA: alpha.
 template <typename S, typename T, int SEG>
-__global__ void __launch_bounds__(kThreads) cg_sweep_a(HeatGeo g, T d, T o, const S* __restrict__ z,
+__global__ void __launch_bounds__(kThreads, 4) cg_sweep_a(HeatGeo g, T d, T o, const S* __restrict__ z,
                                                        const S* __restrict__ pold, S* __restrict__ pnew,
                                                        CgScalars* sc, double* partials) {
   if (sc->done) return;
   const T beta = (T)sc->beta;
   const bool first = (sc->iter == 0);
-  double acc[1] = {0.0};
+  T pw_t = T(0);  // per-thread partial in the arithmetic type
   RK_SEG_LOOP(g, SEG)
     auto pseg = [&](long long off, int mm, T (&v)[SEG]) {
       load_seg<T, S, SEG>(z + off, mm, v);
@@ -281,15 +281,14 @@ __global__ void __launch_bounds__(kThreads) cg_sweep_a(HeatGeo g, T d, T o, cons
     T p[SEG], nb[SEG];
     pseg(base, m, p);
     nb_sum<T, SEG>(g, i0, m, j, k, base, p, pseg, ppt, nb);
-    T pw = T(0);
 #pragma unroll
     for (int e = 0; e < SEG; ++e) {
       const T w = fma(d, p[e], o * nb[e]);
-      if (e < m) pw = fma(p[e], w, pw);
+      if (e < m) pw_t = fma(p[e], w, pw_t);
     }
-    acc[0] += (double)pw;
     store_seg<S, T, SEG>(pnew + base, m, p);
   RK_SEG_LOOP_END
+  double acc[1] = {(double)pw_t};
   double tot[1];
   if (grid_reduce<1, 0u>(acc, partials, &sc->ticket, tot)) {
     sc->pAp = tot[0];
@@ -310,7 +309,7 @@ __global__ void __launch_bounds__(kThreads) cg_sweep_a(HeatGeo g, T d, T o, cons
 // Sweep B: recompute w = A p, x += alpha p, r -= alpha w, z = D^{-1} r,
 // partials r.z and r.r.  Last CTA: beta, convergence test, iteration count.
 template <typename S, typename T, int BS, int SEG>
-__global__ void __launch_bounds__(kThreads) cg_sweep_b(HeatGeo g, T d, T o, const S* __restrict__ p,
+__global__ void __launch_bounds__(kThreads, 4) cg_sweep_b(HeatGeo g, T d, T o, const S* __restrict__ p,
                                                        typename XOf<S>::type* __restrict__ x, S* __restrict__ r,
                                                        S* __restrict__ z, const T* __restrict__ minv,
                                                        CgScalars* sc, double* partials) {
@@ -320,7 +319,7 @@ __global__ void __launch_bounds__(kThreads) cg_sweep_b(HeatGeo g, T d, T o, cons
   load_minv<T, BS>(minv, sM);
   const T alpha = (T)sc->alpha;
   const bool first = (sc->iter == 0);
-  double acc[2] = {0.0, 0.0};
+  T rz = T(0), rr = T(0);  // per-thread partials in the arithmetic type
   RK_SEG_LOOP(g, SEG)
     T pv[SEG], nb[SEG];
     load_seg<T, S, SEG>(p + base, m, pv);
@@ -342,7 +341,6 @@ __global__ void __launch_bounds__(kThreads) cg_sweep_b(HeatGeo g, T d, T o, cons
       xv[e] = fma(alpha, pv[e], xv[e]);
     }
     bj_apply<T, BS, SEG>(sM, g.n, i0, rv, zv);
-    T rz = T(0), rr = T(0);
 #pragma unroll
     for (int e = 0; e < SEG; ++e) {
       zv[e] = rnd<S, T>(zv[e]);
@@ -351,12 +349,11 @@ __global__ void __launch_bounds__(kThreads) cg_sweep_b(HeatGeo g, T d, T o, cons
         rr = fma(rv[e], rv[e], rr);
       }
     }
-    acc[0] += (double)rz;
-    acc[1] += (double)rr;
     store_seg<X, T, SEG>(x + base, m, xv);
     store_seg<S, T, SEG>(r + base, m, rv);
     store_seg<S, T, SEG>(z + base, m, zv);
   RK_SEG_LOOP_END
+  double acc[2] = {(double)rz, (double)rr};
   double tot[2];
   if (grid_reduce<2, 0u>(acc, partials, &sc->ticket, tot)) {
     const double rz_new = tot[0];

@@ -90,11 +90,14 @@ __device__ __forceinline__ void lds_seg(const S* p, T (&v)[SEG]) {
 }
 
 // ----------------------------------------------------------------- sweep A
-// p = D^{-1} r + beta p_old on every plane of the chunk (and its z halo, in a
-// 3-plane shared ring), then q = A p and the partial p.q on the owned lines;
-// p written to pnew.  Last CTA: alpha = r.z / p.q.
+// Thread rows 0..TY+1 each own one line of the (TY+2)-line tile (rows 0 and
+// TY+1 are the y halo).  Per plane: p = D^{-1} r + beta p_old for the own
+// line, kept in registers for the z neighbours and written to a 3-slot ring
+// for the y neighbours; the owned rows 1..TY then form q = A p for the
+// previous plane and the partial p.q, and write p.  One barrier per plane.
+// Last CTA: alpha = r.z / p.q.
 template <typename S, typename T, int BS, int SEG>
-__global__ void __launch_bounds__(256, 2) cg_tiled_a(const __grid_constant__ CUtensorMap tm_r,
+__global__ void __launch_bounds__(320, 2) cg_tiled_a(const __grid_constant__ CUtensorMap tm_r,
                                                   const __grid_constant__ CUtensorMap tm_po, TileGeo tg, T d, T o,
                                                   const T* __restrict__ minv, S* __restrict__ pnew, CgScalars* sc,
                                                   double* partials) {
@@ -110,7 +113,8 @@ __global__ void __launch_bounds__(256, 2) cg_tiled_a(const __grid_constant__ CUt
   uint64_t* bar = reinterpret_cast<uint64_t*>(base + (size_t)(kStagesA * 2 + 3) * tile +
                                               align128(2 * BS * BS * sizeof(T)));
   const int tid = threadIdx.x;
-  const int tx = tid % tg.tpl, ly = tid / tg.tpl;
+  const int tx = tid % tg.tpl, row = tid / tg.tpl;  // row in 0..TY+1
+  const bool owner = row >= 1 && row <= TY;
   const int yt = blockIdx.x % tg.nyt, zc = blockIdx.x / tg.nyt;
   const int y0 = yt * TY;
   const int z0 = (int)((long long)zc * n / tg.nzc), z1 = (int)((long long)(zc + 1) * n / tg.nzc);
@@ -132,69 +136,66 @@ __global__ void __launch_bounds__(256, 2) cg_tiled_a(const __grid_constant__ CUt
   };
   if (tid == 0)
     for (int t = 0; t < kStagesA && t < L; ++t) issue(t);
-  const int xs = tx * SEG;
-  double acc[1] = {0.0};
-  bool timed_out = false;
   int issued = (kStagesA < L) ? kStagesA : L;
+  const int xs = tx * SEG;
+  T pw = T(0);
+  T pprev[SEG], pcur[SEG];
+#pragma unroll
+  for (int e = 0; e < SEG; ++e) pprev[e] = pcur[e] = T(0);
+  bool timed_out = false;
   for (int t = 0; t < L; ++t) {
     const int s = t % kStagesA;
     const bool ok = mbar_wait(&bar[s], (uint32_t)((t / kStagesA) & 1));
+    // p on plane z0-1+t for the own line
+    T pn[SEG];
+    {
+      T rv[SEG];
+      lds_seg<T, S, SEG>(st_r(s) + (size_t)row * n + xs, rv);
+      bj_apply<T, BS, SEG>(sM, n, xs, rv, pn);
+      if (!first) {
+        T pv[SEG];
+        lds_seg<T, S, SEG>(st_p(s) + (size_t)row * n + xs, pv);
+#pragma unroll
+        for (int e = 0; e < SEG; ++e) pn[e] = fma(beta, pv[e], pn[e]);
+      }
+#pragma unroll
+      for (int e = 0; e < SEG; ++e) pn[e] = rnd<S, T>(pn[e]);
+      store_seg<S, T, SEG>(ring(t % 3) + (size_t)row * n + xs, SEG, pn);
+    }
     if (__syncthreads_or(!ok)) {
       timed_out = true;
       break;
     }
-    // p on plane z0-1+t for the owned line and, at the tile edges, the halo lines
-    S* rp = ring(t % 3);
-    auto compute_line = [&](int l) {
-      T rv[SEG], zv[SEG];
-      lds_seg<T, S, SEG>(st_r(s) + (size_t)l * n + xs, rv);
-      bj_apply<T, BS, SEG>(sM, n, xs, rv, zv);
-      if (!first) {
-        T pv[SEG];
-        lds_seg<T, S, SEG>(st_p(s) + (size_t)l * n + xs, pv);
-#pragma unroll
-        for (int e = 0; e < SEG; ++e) zv[e] = fma(beta, pv[e], zv[e]);
-      }
-#pragma unroll
-      for (int e = 0; e < SEG; ++e) zv[e] = rnd<S, T>(zv[e]);
-      store_seg<S, T, SEG>(rp + (size_t)l * n + xs, SEG, zv);
-    };
-    compute_line(ly + 1);
-    if (ly == 0) compute_line(0);
-    if (ly == TY - 1) compute_line(TY + 1);
-    __syncthreads();
+    // stage s has been read by every thread: refill it
     if (tid == 0 && issued < L) {
       fence_proxy_async();
       issue(issued);
       ++issued;
     }
-    if (t >= 2) {
-      const S* pm = ring((t - 2) % 3);
+    if (t >= 2 && owner) {
+      // q = A p on plane z0+t-2 (ring slot (t-1)%3), z neighbours from registers
       const S* pc = ring((t - 1) % 3);
-      const S* pp = ring(t % 3);
-      const int l = ly + 1;
-      T c[SEG], a[SEG], b[SEG], zm[SEG], zp[SEG];
-      lds_seg<T, S, SEG>(pc + (size_t)l * n + xs, c);
-      lds_seg<T, S, SEG>(pc + (size_t)(l - 1) * n + xs, a);
-      lds_seg<T, S, SEG>(pc + (size_t)(l + 1) * n + xs, b);
-      lds_seg<T, S, SEG>(pm + (size_t)l * n + xs, zm);
-      lds_seg<T, S, SEG>(pp + (size_t)l * n + xs, zp);
-      const T left = (xs > 0) ? wid<T>(pc[(size_t)l * n + xs - 1]) : T(0);
-      const T right = (xs + SEG < n) ? wid<T>(pc[(size_t)l * n + xs + SEG]) : T(0);
-      T pw = T(0);
+      T a[SEG], b[SEG];
+      lds_seg<T, S, SEG>(pc + (size_t)(row - 1) * n + xs, a);
+      lds_seg<T, S, SEG>(pc + (size_t)(row + 1) * n + xs, b);
+      const T left = (xs > 0) ? wid<T>(pc[(size_t)row * n + xs - 1]) : T(0);
+      const T right = (xs + SEG < n) ? wid<T>(pc[(size_t)row * n + xs + SEG]) : T(0);
 #pragma unroll
       for (int e = 0; e < SEG; ++e) {
-        const T xl = (e > 0) ? c[e - 1] : left;
-        const T xr = (e + 1 < SEG) ? c[e + 1] : right;
-        const T nb = ((xl + xr) + (a[e] + b[e])) + (zm[e] + zp[e]);
-        const T w = fma(d, c[e], o * nb);
-        pw = fma(c[e], w, pw);
+        const T xl = (e > 0) ? pcur[e - 1] : left;
+        const T xr = (e + 1 < SEG) ? pcur[e + 1] : right;
+        const T nb = ((xl + xr) + (a[e] + b[e])) + (pprev[e] + pn[e]);
+        const T w = fma(d, pcur[e], o * nb);
+        pw = fma(pcur[e], w, pw);
       }
-      acc[0] += (double)pw;
       const int k = z0 + t - 2;
-      store_seg<S, T, SEG>(pnew + ((size_t)k * n + (y0 + ly)) * n + xs, SEG, c);
+      store_seg<S, T, SEG>(pnew + ((size_t)k * n + (y0 + row - 1)) * n + xs, SEG, pcur);
     }
-    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < SEG; ++e) {
+      pprev[e] = pcur[e];
+      pcur[e] = pn[e];
+    }
   }
   if (timed_out) {
     // let copies that are still in flight land before the CTA exits
@@ -206,6 +207,7 @@ __global__ void __launch_bounds__(256, 2) cg_tiled_a(const __grid_constant__ CUt
     }
     __syncthreads();
   }
+  double acc[1] = {(double)pw};
   double tot[1];
   if (grid_reduce<1, 0u>(acc, partials, &sc->ticket, tot)) {
     if (sc->status == 6) return;
@@ -223,8 +225,12 @@ __global__ void __launch_bounds__(256, 2) cg_tiled_a(const __grid_constant__ CUt
 }
 
 // ----------------------------------------------------------------- sweep B
-// q = A p from the TMA ring, r -= alpha q, x += alpha p, z = D^{-1} r in
-// registers, partial r.z and r.r; r and x written.  Last CTA: beta and the
+// Thread rows 0..TY-1 own lines y0..y0+TY-1.  p tiles (with y halo) arrive
+// through the TMA ring; the own line of each plane is copied to registers
+// (z neighbours), the y neighbours of the centre plane are read from its
+// stage.  r and x of the next plane are prefetched into registers before
+// the wait.  q = A p, r -= alpha q, x += alpha p, z = D^{-1} r (registers),
+// partials r.z and r.r.  One barrier per plane.  Last CTA: beta and the
 // convergence test.
 template <typename S, typename T, int BS, int SEG>
 __global__ void __launch_bounds__(256, 2) cg_tiled_b(const __grid_constant__ CUtensorMap tm_p, TileGeo tg, T d, T o,
@@ -240,6 +246,7 @@ __global__ void __launch_bounds__(256, 2) cg_tiled_b(const __grid_constant__ CUt
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + (size_t)kStagesB * tile + align128(2 * BS * BS * sizeof(T)));
   const int tid = threadIdx.x;
   const int tx = tid % tg.tpl, ly = tid / tg.tpl;
+  const int l = ly + 1;  // row of the own line in the tile
   const int yt = blockIdx.x % tg.nyt, zc = blockIdx.x / tg.nyt;
   const int y0 = yt * TY;
   const int z0 = (int)((long long)zc * n / tg.nzc), z1 = (int)((long long)(zc + 1) * n / tg.nzc);
@@ -263,7 +270,7 @@ __global__ void __launch_bounds__(256, 2) cg_tiled_b(const __grid_constant__ CUt
   int issued = (kStagesB < L) ? kStagesB : L;
   const int xs = tx * SEG;
   const size_t line_off = (size_t)(y0 + ly) * n + xs;
-  // r and x of the first owned plane, prefetched into registers
+  // r and x of the first owned plane; later planes are fetched one plane ahead
   T rn[SEG], xn[SEG];
   load_seg<T, S, SEG>(r + (size_t)z0 * n * n + line_off, SEG, rn);
   if (!first) {
@@ -272,18 +279,17 @@ __global__ void __launch_bounds__(256, 2) cg_tiled_b(const __grid_constant__ CUt
 #pragma unroll
     for (int e = 0; e < SEG; ++e) xn[e] = T(0);
   }
-  double acc[2] = {0.0, 0.0};
+  T pprev[SEG], pcur[SEG];
+#pragma unroll
+  for (int e = 0; e < SEG; ++e) pprev[e] = pcur[e] = T(0);
+  T rz = T(0), rr = T(0);
   bool timed_out = false;
   for (int t = 0; t < L; ++t) {
-    const int s = t % kStagesB;
-    const bool ok = mbar_wait(&bar[s], (uint32_t)((t / kStagesB) & 1));
-    if (__syncthreads_or(!ok)) {
-      timed_out = true;
-      break;
-    }
+    // r and x of the plane this iteration outputs (z0+t-2) were fetched one
+    // plane earlier; fetch the next plane's before waiting for the tile
+    T rv[SEG], xv[SEG];
+    const int k = z0 + t - 2;
     if (t >= 2) {
-      const int k = z0 + t - 2;
-      T rv[SEG], xv[SEG];
 #pragma unroll
       for (int e = 0; e < SEG; ++e) {
         rv[e] = rn[e];
@@ -293,43 +299,49 @@ __global__ void __launch_bounds__(256, 2) cg_tiled_b(const __grid_constant__ CUt
         load_seg<T, S, SEG>(r + (size_t)(k + 1) * n * n + line_off, SEG, rn);
         if (!first) load_seg<T, X, SEG>(x + (size_t)(k + 1) * n * n + line_off, SEG, xn);
       }
-      const S* pm = st((t - 2) % kStagesB);
+    }
+    const int s = t % kStagesB;
+    const bool ok = mbar_wait(&bar[s], (uint32_t)((t / kStagesB) & 1));
+    T pn[SEG];
+    lds_seg<T, S, SEG>(st(s) + (size_t)l * n + xs, pn);
+    if (t >= 2) {
       const S* pc = st((t - 1) % kStagesB);
-      const S* pp = st(t % kStagesB);
-      const int l = ly + 1;
-      T c[SEG], a[SEG], b[SEG], zm[SEG], zp[SEG];
-      lds_seg<T, S, SEG>(pc + (size_t)l * n + xs, c);
+      T a[SEG], b[SEG];
       lds_seg<T, S, SEG>(pc + (size_t)(l - 1) * n + xs, a);
       lds_seg<T, S, SEG>(pc + (size_t)(l + 1) * n + xs, b);
-      lds_seg<T, S, SEG>(pm + (size_t)l * n + xs, zm);
-      lds_seg<T, S, SEG>(pp + (size_t)l * n + xs, zp);
       const T left = (xs > 0) ? wid<T>(pc[(size_t)l * n + xs - 1]) : T(0);
       const T right = (xs + SEG < n) ? wid<T>(pc[(size_t)l * n + xs + SEG]) : T(0);
 #pragma unroll
       for (int e = 0; e < SEG; ++e) {
-        const T xl = (e > 0) ? c[e - 1] : left;
-        const T xr = (e + 1 < SEG) ? c[e + 1] : right;
-        const T nb = ((xl + xr) + (a[e] + b[e])) + (zm[e] + zp[e]);
-        const T w = fma(d, c[e], o * nb);
+        const T xl = (e > 0) ? pcur[e - 1] : left;
+        const T xr = (e + 1 < SEG) ? pcur[e + 1] : right;
+        const T nb = ((xl + xr) + (a[e] + b[e])) + (pprev[e] + pn[e]);
+        const T w = fma(d, pcur[e], o * nb);
         rv[e] = rnd<S, T>(fma(-alpha, w, rv[e]));
-        xv[e] = fma(alpha, c[e], xv[e]);
+        xv[e] = fma(alpha, pcur[e], xv[e]);
       }
       T zv[SEG];
       bj_apply<T, BS, SEG>(sM, n, xs, rv, zv);
-      T rz = T(0), rr = T(0);
 #pragma unroll
       for (int e = 0; e < SEG; ++e) {
         zv[e] = rnd<S, T>(zv[e]);
         rz = fma(rv[e], zv[e], rz);
         rr = fma(rv[e], rv[e], rr);
       }
-      acc[0] += (double)rz;
-      acc[1] += (double)rr;
       store_seg<S, T, SEG>(r + (size_t)k * n * n + line_off, SEG, rv);
       store_seg<X, T, SEG>(x + (size_t)k * n * n + line_off, SEG, xv);
     }
-    __syncthreads();
-    if (tid == 0 && t >= 2 && issued < L) {
+#pragma unroll
+    for (int e = 0; e < SEG; ++e) {
+      pprev[e] = pcur[e];
+      pcur[e] = pn[e];
+    }
+    if (__syncthreads_or(!ok)) {
+      timed_out = true;
+      break;
+    }
+    // stage (t-1) % kStagesB is no longer read (its centre-plane role ends here)
+    if (tid == 0 && t >= 1 && issued < L) {
       fence_proxy_async();
       issue(issued);
       ++issued;
@@ -344,6 +356,7 @@ __global__ void __launch_bounds__(256, 2) cg_tiled_b(const __grid_constant__ CUt
     }
     __syncthreads();
   }
+  double acc[2] = {(double)rz, (double)rr};
   double tot[2];
   if (grid_reduce<2, 0u>(acc, partials, &sc->ticket, tot)) {
     if (sc->status == 6) return;
