@@ -331,6 +331,8 @@ def main():
     ap.add_argument("--workload", default="heat256", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
+    ap.add_argument("--bs", type=int, default=0, help="override the block-Jacobi block size")
+    ap.add_argument("--tol", type=float, default=0.0, help="override the solver tolerance")
     ap.add_argument("--batch", action="store_true", help="run the 512-problem batched workload instead")
     ap.add_argument("--batch-steps", type=int, default=50)
     ap.add_argument("--serve", type=int, default=0, help="run the serving workload with this many jobs instead")
@@ -340,7 +342,11 @@ def main():
         return run_batch(args)
     if args.serve:
         return run_serve(args)
-    cfg = WORKLOADS[args.workload]
+    cfg = dict(WORKLOADS[args.workload])
+    if args.bs:
+        cfg["bs"] = args.bs
+    if args.tol:
+        cfg["tol"] = args.tol
     if args.impl == "reference":
         return run_reference(args, cfg)
 

@@ -24,20 +24,29 @@ struct CombineArgs {
   long long N;
 };
 
+// The term loops run to the actual counts (not unrolled to kMaxStages): on
+// this part a predicated-off FP64 instruction still costs an FP64 issue slot.
 template <typename S>
 __global__ void __launch_bounds__(kThreads) combine_f64(CombineArgs a) {
-  double ce[kMaxStages];
-#pragma unroll
-  for (int j = 0; j < kMaxStages; ++j) ce[j] = (j < a.ne) ? a.ce[j] / a.rs[j]->sigma : 0.0;
+  __shared__ const double* s_kh[kMaxStages];
+  __shared__ const S* s_ke[kMaxStages];
+  __shared__ double s_ch[kMaxStages], s_ce[kMaxStages];
+  if (threadIdx.x < kMaxStages) {
+    const int j = threadIdx.x;
+    s_kh[j] = a.kh[j];
+    s_ch[j] = a.ch[j];
+    s_ke[j] = static_cast<const S*>(a.ke[j]);
+    s_ce[j] = (j < a.ne) ? a.ce[j] / a.rs[j]->sigma : 0.0;
+  }
+  __syncthreads();
+  const int nh = a.nh, ne = a.ne;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.N;
        i += (long long)gridDim.x * blockDim.x) {
     double v = a.u ? a.u[i] : 0.0;
-#pragma unroll
-    for (int j = 0; j < kMaxStages; ++j)
-      if (j < a.nh) v = fma(a.ch[j], a.kh[j][i], v);
-#pragma unroll
-    for (int j = 0; j < kMaxStages; ++j)
-      if (j < a.ne) v = fma(ce[j], wid<double>(static_cast<const S*>(a.ke[j])[i]), v);
+#pragma unroll 1
+    for (int j = 0; j < nh; ++j) v = fma(s_ch[j], s_kh[j][i], v);
+#pragma unroll 1
+    for (int j = 0; j < ne; ++j) v = fma(s_ce[j], wid<double>(s_ke[j][i]), v);
     a.out[i] = v;
   }
 }
