@@ -247,11 +247,18 @@ static bool tiled_setup(rk_problem* p) {
   }
   auto ka = cg_tiled_a<S, T, BS, SEG>;
   auto kb = cg_tiled_b<S, T, BS, SEG>;
-  if (cudaFuncSetAttribute((const void*)ka, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa) != cudaSuccess ||
-      cudaFuncSetAttribute((const void*)kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb) != cudaSuccess) {
+  // The limit is a property of the kernel, shared by every problem: set it
+  // once to the largest size any problem may use (never lower it).
+  static std::once_flag once;
+  static bool attr_ok = false;
+  std::call_once(once, [&] {
+    attr_ok = cudaFuncSetAttribute((const void*)ka, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) ==
+                  cudaSuccess &&
+              cudaFuncSetAttribute((const void*)kb, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) ==
+                  cudaSuccess;
     cudaGetLastError();
-    return false;
-  }
+  });
+  if (!attr_ok) return false;
   int occa = 0, occb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occa, ka, (ty + 2) * tpl, sa) != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occb, kb, ty * tpl, sb) != cudaSuccess || occa < 1 || occb < 1) {
