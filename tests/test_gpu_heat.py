@@ -216,3 +216,20 @@ def test_tiled_sweeps_match_segment_sweeps(rk, n, storage, bs, monkeypatch):
     if M is not None:
         ref = krylov.pcg(lambda v: M @ v, krylov.BlockJacobi(M, n, bs).apply, g, tol_rel=1e-12).x
         assert rel_l2(out["tiled"][0], ref) < bound
+
+
+def test_tiled_problems_of_different_sizes_interleaved(rk):
+    """Problems of different n share the tiled kernels; solving them in turn
+    (large, small, large) must keep working (per-kernel launch limits)."""
+    shift = 2.5e-4
+    probs = {n: make(rk, n, storage="f32", bs=8, tol=1e-6, max_iter=2000) for n in (96, 64)}
+    try:
+        for n in (96, 64, 96):
+            g = operators.heat_apply(synth.heat_modes(seed=n, n_random=4).evaluate(n), n, 1.0)
+            k = np.empty_like(g)
+            rk.rk_solve(probs[n].h, shift, g, k)
+            M = krylov.shifted(operators.heat_csr(n, 1.0), shift)
+            assert np.linalg.norm(g - M @ k) / np.linalg.norm(g) < 1e-4
+    finally:
+        for p in probs.values():
+            p.close()
