@@ -130,10 +130,23 @@ static rk_status heat_minv(rk_problem* p, double shift, const void** out) {
     RK_CUDA(cudaMemcpyAsync(e.dev, f.data(), f.size() * 4, cudaMemcpyHostToDevice, p->st));
     RK_CUDA(cudaStreamSynchronize(p->st));
   }
+  e.host = inv;
   e.shift = shift;
   e.valid = true;
   *out = e.dev;
   return RK_OK;
+}
+
+rk_status get_minv_entry(rk_problem* p, double shift, const MinvEntry** out) {
+  const void* d = nullptr;
+  RK_TRY(heat_minv(p, shift, &d));
+  for (auto& e : p->minv)
+    if (e.valid && e.dev == d) {
+      *out = &e;
+      return RK_OK;
+    }
+  set_error("block-Jacobi cache lookup failed");
+  return RK_ERR_ARG;
 }
 
 rk_status get_minv(rk_problem* p, double shift, const void** out) {
@@ -261,10 +274,14 @@ static bool tiled_setup(rk_problem* p) {
   if (!attr_ok) return false;
   int occa = 0, occb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occa, ka, (ty + 2) * tpl, sa) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occb, kb, ty * tpl, sb) != cudaSuccess || occa < 1 || occb < 1) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occb, kb, ty * tpl, sb) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
+  // with a single resident CTA per SM the plane pipeline cannot hide its
+  // latency (measured: FP64 at 256^3 ran 1.5x slower tiled); keep the
+  // per-segment sweeps then
+  if (occa < 2 || occb < 2) return false;
   const int nyt = n / ty;
   const int slots = device_sms() * std::min(occa, occb);
   tm.tg = TileGeo{n, tpl, ty, nyt, std::max(1, std::min(n, slots / nyt))};
@@ -278,8 +295,8 @@ static bool tiled_setup(rk_problem* p) {
 // the iteration count of the previous solve of the same stage slot.
 static rk_status heat_cg_solve(rk_problem* p, double shift, const double* g64, RhsScalars* rs, void* x,
                                int slot, int* iters, int* status) {
-  const void* minv = nullptr;
-  RK_TRY(get_minv(p, shift, &minv));
+  const MinvEntry* me = nullptr;
+  RK_TRY(get_minv_entry(p, shift, &me));
   CgScalars init{};
   init.tol_rel = p->sol.tol_rel;
   init.tol_abs = p->sol.tol_abs;
@@ -300,7 +317,7 @@ static rk_status heat_cg_solve(rk_problem* p, double shift, const double* g64, R
       S* z = static_cast<S*>(p->wz);
       using X = typename XOf<S>::type;
       X* xs = static_cast<X*>(x);
-      const T* M = static_cast<const T*>(minv);
+      const BjInv<T, BS> M = bj_param<T, BS>(me->host);
       auto ki = cg_init<S, T, BS, SEG>;
       auto ka = cg_sweep_a<S, T, SEG>;
       auto kb = cg_sweep_b<S, T, BS, SEG>;
@@ -942,8 +959,8 @@ rk_status rk_apply_precond(rk_problem* p, double shift, const double* r, double*
   if (p->desc.op != RK_OP_HEAT7) {
     RK_TRY(csr_precond_f64(p, shift, rin, zout));
   } else {
-    const void* minv = nullptr;
-    RK_TRY(get_minv(p, shift, &minv));
+    const MinvEntry* me = nullptr;
+    RK_TRY(get_minv_entry(p, shift, &me));
     rk_status lst = RK_OK;
     dispatch_st(p->sol.storage, [&](auto ts, auto tt) {
       using S = typename decltype(ts)::type;
@@ -953,9 +970,9 @@ rk_status rk_apply_precond(rk_problem* p, double shift, const double* r, double*
         constexpr int SEG = seg_of<S, BS>();
         HeatGeo g = heat_geo(p, SEG);
         auto kern = bj_apply_f64io<S, T, BS, SEG>;
+        const BjInv<T, BS> M = bj_param<T, BS>(me->host);
         launch(p, K_BJ, 16.0 * p->N, [&] {
-          kern<<<grid_for((const void*)kern, g.n2 * g.nseg), kThreads, 0, p->st>>>(
-              g, rin, static_cast<const T*>(minv), zout);
+          kern<<<grid_for((const void*)kern, g.n2 * g.nseg), kThreads, 0, p->st>>>(g, rin, M, zout);
         });
         if (cudaGetLastError() != cudaSuccess) lst = RK_ERR_CUDA;
       });

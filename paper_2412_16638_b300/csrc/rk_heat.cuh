@@ -169,13 +169,15 @@ __global__ void __launch_bounds__(kThreads) heat_correct_f64(HeatGeo g, const do
 }
 
 // ------------------------------------------------------------- CG sweeps
-// Block-Jacobi inverse in shared memory: [0] full BS-block, [1] the tail
-// block of a line (n mod BS nodes, zero padded).
+// Block-Jacobi inverse passed by value as a __grid_constant__ kernel
+// parameter: [0] the full BS-block, [1] the tail block of a line (n mod BS
+// nodes, zero padded).  Indexed with compile-time offsets inside the unrolled
+// GEMV, its entries are read from the constant bank as FMA operands, so the
+// preconditioner costs no load instructions.
 template <typename T, int BS>
-__device__ __forceinline__ void load_minv(const T* __restrict__ minv, T* sM) {
-  for (int i = threadIdx.x; i < 2 * BS * BS; i += blockDim.x) sM[i] = minv[i];
-  __syncthreads();
-}
+struct BjInv {
+  T m[2 * BS * BS];
+};
 
 // z = D^{-1} r on every block of the segment.
 template <typename T, int BS, int SEG>
@@ -198,13 +200,12 @@ __device__ __forceinline__ void bj_apply(const T* sM, int n, int i0, const T (&r
 // reductions r.z, r.r.  g is the FP64 right-hand side.
 template <typename S, typename T, int BS, int SEG>
 __global__ void __launch_bounds__(kThreads) cg_init(HeatGeo g, const double* __restrict__ gv,
-                                                    const RhsScalars* rs, const T* __restrict__ minv,
+                                                    const RhsScalars* rs, const __grid_constant__ BjInv<T, BS> inv,
                                                     S* __restrict__ r, S* __restrict__ z,
                                                     typename XOf<S>::type* __restrict__ x, CgScalars* sc,
                                                     double* partials) {
   using X = typename XOf<S>::type;
-  __shared__ T sM[2 * BS * BS];
-  load_minv<T, BS>(minv, sM);
+  const T* sM = inv.m;
   const double sigma = rs->sigma;
   double acc[2] = {0.0, 0.0};
   RK_SEG_LOOP(g, SEG)
@@ -311,12 +312,11 @@ __global__ void __launch_bounds__(kThreads, 4) cg_sweep_a(HeatGeo g, T d, T o, c
 template <typename S, typename T, int BS, int SEG>
 __global__ void __launch_bounds__(kThreads, 4) cg_sweep_b(HeatGeo g, T d, T o, const S* __restrict__ p,
                                                        typename XOf<S>::type* __restrict__ x, S* __restrict__ r,
-                                                       S* __restrict__ z, const T* __restrict__ minv,
+                                                       S* __restrict__ z, const __grid_constant__ BjInv<T, BS> inv,
                                                        CgScalars* sc, double* partials) {
   using X = typename XOf<S>::type;
   if (sc->done) return;
-  __shared__ T sM[2 * BS * BS];
-  load_minv<T, BS>(minv, sM);
+  const T* sM = inv.m;
   const T alpha = (T)sc->alpha;
   const bool first = (sc->iter == 0);
   T rz = T(0), rr = T(0);  // per-thread partials in the arithmetic type
@@ -378,9 +378,9 @@ __global__ void __launch_bounds__(kThreads, 4) cg_sweep_b(HeatGeo g, T d, T o, c
 // returned widened to FP64 (for testing the preconditioner).
 template <typename S, typename T, int BS, int SEG>
 __global__ void __launch_bounds__(kThreads) bj_apply_f64io(HeatGeo g, const double* __restrict__ r,
-                                                           const T* __restrict__ minv, double* __restrict__ z) {
-  __shared__ T sM[2 * BS * BS];
-  load_minv<T, BS>(minv, sM);
+                                                           const __grid_constant__ BjInv<T, BS> inv,
+                                                           double* __restrict__ z) {
+  const T* sM = inv.m;
   RK_SEG_LOOP(g, SEG)
     double rd[SEG];
     load_seg<double, double, SEG>(r + base, m, rd);

@@ -81,8 +81,17 @@ struct MinvEntry {
   double shift = 0.0;
   void* dev = nullptr;  // heat: 2*BS*BS values of the arithmetic type;
                         // CSR: per-block inverses in the storage type
+  std::vector<double> host;  // heat: the same 2*BS*BS values in FP64
   bool valid = false;
 };
+
+// Kernel-parameter copy of a heat block-Jacobi inverse.
+template <typename T, int BS>
+inline BjInv<T, BS> bj_param(const std::vector<double>& h) {
+  BjInv<T, BS> v;
+  for (int i = 0; i < 2 * BS * BS; ++i) v.m[i] = (T)h[i];
+  return v;
+}
 
 // CSR operator data (advection-diffusion)
 struct Csr {
@@ -178,6 +187,8 @@ struct rk_problem {
 namespace rk {
 rk_status alloc_dev(rk_problem* p, void** ptr, size_t bytes);
 rk_status get_minv(rk_problem* p, double shift, const void** out);
+// Heat path: the cache entry (host and device copies) for this shift.
+rk_status get_minv_entry(rk_problem* p, double shift, const MinvEntry** out);
 // Solve (I - shift L) x = sigma*g with RHS stats in *rs (device).  Result in x
 // (storage precision, scaled by sigma).  Returns iterations in *iters.
 rk_status krylov_solve(rk_problem* p, double shift, const double* g64, RhsScalars* rs, void* x,

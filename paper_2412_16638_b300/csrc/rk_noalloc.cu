@@ -6,8 +6,9 @@
 // whose allocator policy forbids it, and sections that must not synchronise
 // the device (cudaMalloc/cudaFree can).  This entry point runs the same CG
 // kernels as rk_solve, but its workspace (Krylov vectors, reduction partials,
-// solver scalars, block-Jacobi inverse) lives in one file-scope device array
-// of fixed size, so the call allocates nothing.
+// solver scalars) lives in one file-scope device array of fixed size, and the
+// block-Jacobi inverse travels as a kernel parameter, so the call allocates
+// nothing.
 //
 // Properties a caller must know:
 //  - The array g_noalloc_scratch (RK_NOALLOC_BYTES, about 5.3 MB) exists on
@@ -37,8 +38,7 @@ constexpr size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 constexpr size_t kOffCg = 0;
 constexpr size_t kOffRhs = align256(kOffCg + sizeof(rk::CgScalars));
 constexpr size_t kOffPart = align256(kOffRhs + sizeof(rk::RhsScalars));
-constexpr size_t kOffMinv = align256(kOffPart + sizeof(double) * 2 * kMaxCtas);
-constexpr size_t kOffVec = align256(kOffMinv + sizeof(float) * 2 * kMaxBs * kMaxBs);
+constexpr size_t kOffVec = align256(kOffPart + sizeof(double) * 2 * kMaxCtas);
 constexpr size_t kVecBytes = align256(sizeof(float) * kMaxDof);
 constexpr size_t RK_NOALLOC_BYTES = kOffVec + 5 * kVecBytes;  // r, z, p0, p1, x
 
@@ -130,14 +130,14 @@ rk_status solve_bs(int n, double c, double shift, double tol_rel, double tol_abs
   auto* sc = reinterpret_cast<rk::CgScalars*>(base + kOffCg);
   auto* rs = reinterpret_cast<rk::RhsScalars*>(base + kOffRhs);
   auto* partials = reinterpret_cast<double*>(base + kOffPart);
-  auto* minv = reinterpret_cast<T*>(base + kOffMinv);
+  rk::BjInv<T, BS> minv;  // block-Jacobi inverse, passed by value as a kernel parameter
   S* r = reinterpret_cast<S*>(base + kOffVec);
   S* z = reinterpret_cast<S*>(base + kOffVec + kVecBytes);
   S* p[2] = {reinterpret_cast<S*>(base + kOffVec + 2 * kVecBytes), reinterpret_cast<S*>(base + kOffVec + 3 * kVecBytes)};
   float* x = reinterpret_cast<float*>(base + kOffVec + 4 * kVecBytes);
 
   // everything that must start from a known value: solver scalars (ticket 0,
-  // done 0), right-hand-side scalars (sigma 1, ticket 0), preconditioner
+  // done 0) and right-hand-side scalars (sigma 1, ticket 0)
   float inv[2 * BS * BS];
   const double dd = 1.0 + 6.0 * shift * c, off = -shift * c;
   block_inverse(BS < n ? BS : n, dd, off, BS, inv);
@@ -149,10 +149,10 @@ rk_status solve_bs(int n, double c, double shift, double tol_rel, double tol_abs
   sc0.max_iter = max_iter;
   rk::RhsScalars rs0{};
   rs0.sigma = 1.0;
-  RK_CUDA(cudaMemcpyAsync(minv, inv, sizeof(inv), cudaMemcpyHostToDevice, st));
   RK_CUDA(cudaMemcpyAsync(sc, &sc0, sizeof(sc0), cudaMemcpyHostToDevice, st));
   RK_CUDA(cudaMemcpyAsync(rs, &rs0, sizeof(rs0), cudaMemcpyHostToDevice, st));
 
+  for (int i = 0; i < 2 * BS * BS; ++i) minv.m[i] = inv[i];
   const T d = (T)dd, o = (T)off;
   auto ki = rk::cg_init<S, T, BS, SEG>;
   auto ka = rk::cg_sweep_a<S, T, SEG>;

@@ -99,8 +99,8 @@ __device__ __forceinline__ void lds_seg(const S* p, T (&v)[SEG]) {
 template <typename S, typename T, int BS, int SEG>
 __global__ void __launch_bounds__(320, 2) cg_tiled_a(const __grid_constant__ CUtensorMap tm_r,
                                                   const __grid_constant__ CUtensorMap tm_po, TileGeo tg, T d, T o,
-                                                  const T* __restrict__ minv, S* __restrict__ pnew, CgScalars* sc,
-                                                  double* partials) {
+                                                  const __grid_constant__ BjInv<T, BS> inv, S* __restrict__ pnew,
+                                                  CgScalars* sc, double* partials) {
   if (sc->done) return;
   extern __shared__ __align__(128) unsigned char smem[];
   const int n = tg.n, TY = tg.ty, R = TY + 2;
@@ -109,9 +109,8 @@ __global__ void __launch_bounds__(320, 2) cg_tiled_a(const __grid_constant__ CUt
   auto st_r = [&](int s) { return reinterpret_cast<S*>(base + (size_t)s * 2 * tile); };
   auto st_p = [&](int s) { return reinterpret_cast<S*>(base + (size_t)s * 2 * tile + tile); };
   auto ring = [&](int s) { return reinterpret_cast<S*>(base + (size_t)kStagesA * 2 * tile + (size_t)s * tile); };
-  T* sM = reinterpret_cast<T*>(base + (size_t)(kStagesA * 2 + 3) * tile);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(base + (size_t)(kStagesA * 2 + 3) * tile +
-                                              align128(2 * BS * BS * sizeof(T)));
+  const T* sM = inv.m;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(base + (size_t)(kStagesA * 2 + 3) * tile);
   const int tid = threadIdx.x;
   const int tx = tid % tg.tpl, row = tid / tg.tpl;  // row in 0..TY+1
   const bool owner = row >= 1 && row <= TY;
@@ -122,7 +121,6 @@ __global__ void __launch_bounds__(320, 2) cg_tiled_a(const __grid_constant__ CUt
   const T beta = (T)sc->beta;
   const bool first = (sc->iter == 0);
   const uint32_t tx_bytes = (first ? 1u : 2u) * (uint32_t)(R * n * sizeof(S));
-  for (int i = tid; i < 2 * BS * BS; i += blockDim.x) sM[i] = minv[i];
   if (tid == 0) {
     for (int s = 0; s < kStagesA; ++s) mbar_init(&bar[s], 1);
     mbar_fence_init();
@@ -234,16 +232,17 @@ __global__ void __launch_bounds__(320, 2) cg_tiled_a(const __grid_constant__ CUt
 // convergence test.
 template <typename S, typename T, int BS, int SEG>
 __global__ void __launch_bounds__(256, 2) cg_tiled_b(const __grid_constant__ CUtensorMap tm_p, TileGeo tg, T d, T o,
-                                                  const T* __restrict__ minv, typename XOf<S>::type* __restrict__ x,
-                                                  S* __restrict__ r, CgScalars* sc, double* partials) {
+                                                  const __grid_constant__ BjInv<T, BS> inv,
+                                                  typename XOf<S>::type* __restrict__ x, S* __restrict__ r,
+                                                  CgScalars* sc, double* partials) {
   using X = typename XOf<S>::type;
   if (sc->done) return;
   extern __shared__ __align__(128) unsigned char smem[];
   const int n = tg.n, TY = tg.ty, R = TY + 2;
   const size_t tile = align128((size_t)R * n * sizeof(S));
   auto st = [&](int s) { return reinterpret_cast<S*>(smem + (size_t)s * tile); };
-  T* sM = reinterpret_cast<T*>(smem + (size_t)kStagesB * tile);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + (size_t)kStagesB * tile + align128(2 * BS * BS * sizeof(T)));
+  const T* sM = inv.m;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + (size_t)kStagesB * tile);
   const int tid = threadIdx.x;
   const int tx = tid % tg.tpl, ly = tid / tg.tpl;
   const int l = ly + 1;  // row of the own line in the tile
@@ -254,7 +253,6 @@ __global__ void __launch_bounds__(256, 2) cg_tiled_b(const __grid_constant__ CUt
   const T alpha = (T)sc->alpha;
   const bool first = (sc->iter == 0);
   const uint32_t tx_bytes = (uint32_t)(R * n * sizeof(S));
-  for (int i = tid; i < 2 * BS * BS; i += blockDim.x) sM[i] = minv[i];
   if (tid == 0) {
     for (int s = 0; s < kStagesB; ++s) mbar_init(&bar[s], 1);
     mbar_fence_init();
@@ -381,13 +379,11 @@ __global__ void __launch_bounds__(256, 2) cg_tiled_b(const __grid_constant__ CUt
 // Shared-memory bytes of the two sweeps.
 template <typename S, typename T, int BS>
 __host__ constexpr size_t tiled_smem_a(int n, int ty) {
-  return (size_t)(kStagesA * 2 + 3) * align128((size_t)(ty + 2) * n * sizeof(S)) +
-         align128(2 * BS * BS * sizeof(T)) + 8 * kStagesA;
+  return (size_t)(kStagesA * 2 + 3) * align128((size_t)(ty + 2) * n * sizeof(S)) + 8 * kStagesA;
 }
 template <typename S, typename T, int BS>
 __host__ constexpr size_t tiled_smem_b(int n, int ty) {
-  return (size_t)kStagesB * align128((size_t)(ty + 2) * n * sizeof(S)) + align128(2 * BS * BS * sizeof(T)) +
-         8 * kStagesB;
+  return (size_t)kStagesB * align128((size_t)(ty + 2) * n * sizeof(S)) + 8 * kStagesB;
 }
 
 }  // namespace rk
