@@ -139,6 +139,40 @@ __global__ void __launch_bounds__(kThreads) heat_apply_f64(HeatGeo g, const doub
 // c_s = shift * kappa/h^2.  This is k_i = L y_i with y_i = r_i + shift k^eps_i
 // (g = L r_i precomputed), and k - v is the true residual of the stage solve;
 // its squared norm is reduced into rs->res2.
+// Error-free transformations on the FP32 pipe: a + b = s + e exactly (Knuth's
+// TwoSum), and c*a = p + e exactly (product error through one FMA).
+// (The _rn intrinsics keep the compiler from contracting these into FMAs,
+// which would break the exactness.)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Laplacian numerator (sum of the six neighbours - 6 * centre) of FP32 values
+// as an unevaluated float pair hi + lo: every rounding error of the sum is
+// captured exactly and accumulated in lo, so hi + lo carries the sum to about
+// 2^-48 of the terms' magnitude (the FP64 stencil carries about 2^-53); one
+// conversion to FP64 then replaces seven.
+__device__ __forceinline__ double lap_pair(float c, float xl, float xr, float ym, float yp, float zm, float zp) {
+  float s, e, t;
+  const float p6 = __fmul_rn(-6.0f, c);
+  float lo = fmaf(-6.0f, c, -p6);  // exact error of the product
+  two_sum(p6, xl, s, e);
+  lo = __fadd_rn(lo, e);
+  two_sum(s, xr, t, e);
+  lo = __fadd_rn(lo, e);
+  two_sum(t, ym, s, e);
+  lo = __fadd_rn(lo, e);
+  two_sum(s, yp, t, e);
+  lo = __fadd_rn(lo, e);
+  two_sum(t, zm, s, e);
+  lo = __fadd_rn(lo, e);
+  two_sum(s, zp, t, e);
+  lo = __fadd_rn(lo, e);
+  return (double)t + (double)lo;
+}
+
 template <typename S, int SEG>
 __global__ void __launch_bounds__(kThreads) heat_correct_f64(HeatGeo g, const double* __restrict__ gv,
                                                              const S* __restrict__ ke, double cs,
@@ -146,6 +180,45 @@ __global__ void __launch_bounds__(kThreads) heat_correct_f64(HeatGeo g, const do
                                                              double* partials) {
   const double inv_sigma = 1.0 / rs->sigma;
   double acc[1] = {0.0};
+  if constexpr (sizeof(S) == 4) {
+    // FP32 k^eps: exact-pair Laplacian on the FP32 pipe (see lap_pair)
+    const double c2 = cs * inv_sigma;
+    RK_SEG_LOOP(g, SEG)
+      float v[SEG], nb_unused[SEG];
+      (void)nb_unused;
+      load_seg<float, S, SEG>(ke + base, m, v);
+      const float left = (i0 > 0) ? wid<float>(ke[base - 1]) : 0.f;
+      const float right = (i0 + SEG < g.n) ? wid<float>(ke[base + SEG]) : 0.f;
+      float ym[SEG], yp[SEG], zm[SEG], zp[SEG];
+      auto seg_or_zero = [&](bool in, long long off, float (&w)[SEG]) {
+        if (in) {
+          load_seg<float, S, SEG>(ke + off, m, w);
+        } else {
+#pragma unroll
+          for (int e = 0; e < SEG; ++e) w[e] = 0.f;
+        }
+      };
+      seg_or_zero(j > 0, base - g.n, ym);
+      seg_or_zero(j < g.n - 1, base + g.n, yp);
+      seg_or_zero(k > 0, base - g.n2, zm);
+      seg_or_zero(k < g.n - 1, base + g.n2, zp);
+      double gs[SEG], kv[SEG];
+      load_seg<double, double, SEG>(gv + base, m, gs);
+#pragma unroll
+      for (int e = 0; e < SEG; ++e) {
+        const float xl = (e > 0) ? v[e - 1] : left;
+        const float xr = (e + 1 < SEG) ? v[e + 1] : right;
+        const double lap = lap_pair(v[e], xl, xr, ym[e], yp[e], zm[e], zp[e]);
+        kv[e] = fma(c2, lap, gs[e]);
+        const double res = fma(-(double)v[e], inv_sigma, kv[e]);
+        if (e < m) acc[0] = fma(res, res, acc[0]);
+      }
+      store_seg<double, double, SEG>(kout + base, m, kv);
+    RK_SEG_LOOP_END
+    double tot[1];
+    if (grid_reduce<1, 0u>(acc, partials, &rs->ticket, tot)) rs->res2 = tot[0];
+    return;
+  }
   RK_SEG_LOOP(g, SEG)
     double v[SEG], nb[SEG], gs[SEG];
     load_seg<double, S, SEG>(ke + base, m, v);
@@ -207,7 +280,7 @@ __global__ void __launch_bounds__(kThreads) cg_init(HeatGeo g, const double* __r
   using X = typename XOf<S>::type;
   const T* sM = inv.m;
   const double sigma = rs->sigma;
-  double acc[2] = {0.0, 0.0};
+  T rz = T(0), rr = T(0);  // per-thread partials in the arithmetic type
   RK_SEG_LOOP(g, SEG)
     double gd[SEG];
     load_seg<double, double, SEG>(gv + base, m, gd);
@@ -222,14 +295,15 @@ __global__ void __launch_bounds__(kThreads) cg_init(HeatGeo g, const double* __r
     for (int e = 0; e < SEG; ++e) {
       zv[e] = rnd<S, T>(zv[e]);
       if (e < m) {
-        acc[0] += (double)(rv[e] * zv[e]);
-        acc[1] += (double)(rv[e] * rv[e]);
+        rz = fma(rv[e], zv[e], rz);
+        rr = fma(rv[e], rv[e], rr);
       }
     }
     store_seg<S, T, SEG>(r + base, m, rv);
     store_seg<S, T, SEG>(z + base, m, zv);
     store_seg<X, T, SEG>(x + base, m, zero);
   RK_SEG_LOOP_END
+  double acc[2] = {(double)rz, (double)rr};
   double tot[2];
   if (grid_reduce<2, 0u>(acc, partials, &sc->ticket, tot)) {
     sc->rz = tot[0];

@@ -83,10 +83,42 @@ __device__ __forceinline__ void tma_load3(void* dst, const CUtensorMap* map, uin
       : "memory");
 }
 
+// Shared-memory segment load/store.  A 32-byte segment is moved as two
+// 16-byte halves; lanes with bit 2 set take the halves in the opposite order,
+// so each 8-lane phase touches all 32 banks once (no 2-way conflict between
+// lanes 32 bytes apart).  Other segment sizes use the plain vector access.
 template <typename T, typename S, int SEG>
 __device__ __forceinline__ void lds_seg(const S* p, T (&v)[SEG]) {
-  // p is 16-byte aligned when SEG*sizeof(S) is a multiple of 16
-  load_seg<T, S, SEG>(p, SEG, v);
+  if constexpr (SEG * sizeof(S) == 32) {
+    const bool sw = (threadIdx.x & 4) != 0;
+    const uint4* q = reinterpret_cast<const uint4*>(p);
+    const uint4 a = q[sw ? 1 : 0];
+    const uint4 b = q[sw ? 0 : 1];
+    alignas(16) S tmp[SEG];
+    reinterpret_cast<uint4*>(tmp)[0] = sw ? b : a;
+    reinterpret_cast<uint4*>(tmp)[1] = sw ? a : b;
+#pragma unroll
+    for (int e = 0; e < SEG; ++e) v[e] = wid<T>(tmp[e]);
+  } else {
+    load_seg<T, S, SEG>(p, SEG, v);
+  }
+}
+
+template <typename S, typename T, int SEG>
+__device__ __forceinline__ void sts_seg(S* p, const T (&v)[SEG]) {
+  if constexpr (SEG * sizeof(S) == 32) {
+    alignas(16) S tmp[SEG];
+#pragma unroll
+    for (int e = 0; e < SEG; ++e) tmp[e] = nar<S>(v[e]);
+    const bool sw = (threadIdx.x & 4) != 0;
+    const uint4 a = reinterpret_cast<const uint4*>(tmp)[0];
+    const uint4 b = reinterpret_cast<const uint4*>(tmp)[1];
+    uint4* q = reinterpret_cast<uint4*>(p);
+    q[sw ? 1 : 0] = sw ? b : a;
+    q[sw ? 0 : 1] = sw ? a : b;
+  } else {
+    store_seg<S, T, SEG>(p, SEG, v);
+  }
 }
 
 // ----------------------------------------------------------------- sweep A
@@ -158,7 +190,7 @@ __global__ void __launch_bounds__(320, 2) cg_tiled_a(const __grid_constant__ CUt
       }
 #pragma unroll
       for (int e = 0; e < SEG; ++e) pn[e] = rnd<S, T>(pn[e]);
-      store_seg<S, T, SEG>(ring(t % 3) + (size_t)row * n + xs, SEG, pn);
+      sts_seg<S, T, SEG>(ring(t % 3) + (size_t)row * n + xs, pn);
     }
     if (__syncthreads_or(!ok)) {
       timed_out = true;

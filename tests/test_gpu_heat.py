@@ -233,3 +233,18 @@ def test_tiled_problems_of_different_sizes_interleaved(rk):
     finally:
         for p in probs.values():
             p.close()
+
+
+def test_fp32_correction_matches_fp64_stencil(rk):
+    """With FP32 k^eps the FP64 correction k = g + shift * L k^eps forms the
+    Laplacian as an exact FP32 pair; a ragged-size DIRK3 run must stay within
+    the FP32 bound of the oracle and report a small true residual."""
+    n, dt = 37, 1e-3
+    u0 = synth.heat_modes(seed=2, n_random=6).evaluate(n)
+    with make(rk, n, storage="f32", bs=8, tol=1e-7, correct=1, tab="dirk3", u0=u0, max_iter=500) as p:
+        st = rk.rk_integrate(p.h, dt, 3)
+        u = p.state()
+    ref = dirk.integrate(u0, dt, 3, tableau.dirk3(), operators.HeatOperator(n, 1.0),
+                         dirk.Solver("cg", bs=8, tol_rel=1e-13))
+    assert rel_l2(u, ref) < 1e-6
+    assert 0.0 <= st.true_res < 1e-4
