@@ -31,7 +31,7 @@ struct TileGeo {
   int nzc;  // z chunks
 };
 
-constexpr int kStagesA = 3;  // input stages of sweep A (r, p_old tiles)
+constexpr int kStagesA = 4;  // input stages of sweep A (r, p_old tiles)
 constexpr int kStagesB = 4;  // p-tile stages of sweep B (planes k-1, k, k+1 + one in flight)
 constexpr unsigned kWaitSpins = 1u << 24;
 
