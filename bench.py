@@ -42,12 +42,19 @@ import numpy as np  # noqa: E402
 import synth  # noqa: E402
 
 METRIC = "DOF*steps/s"
+# tol: solver tolerance of the mixed path; tol64: of the plain FP64 path.  Each
+# is the loosest tolerance (of 1e-2, 3e-3, 1e-3, 3e-4, 1e-4, 1e-5) whose error
+# against the exact solution after 23 steps stays within 1.05x that of an
+# exact solve (profiles/heat256_tolerance_sweep.md); 1e-3 is also the
+# tolerance of the paper's accuracy study (Sec. 5.4).
 WORKLOADS = {
-    "heat256": dict(n=256, kappa=1.0, tableau="sdirk2", dt=1e-3, bs=8, tol=1e-6, storage="f32"),
-    "heat256-4s3pB": dict(n=256, kappa=1.0, tableau="4s3pB", dt=1e-3, bs=8, tol=1e-6, storage="f32"),
-    "heat256-f16": dict(n=256, kappa=1.0, tableau="sdirk2", dt=1e-3, bs=8, tol=1e-3, storage="f16"),
-    "heat128": dict(n=128, kappa=1.0, tableau="sdirk2", dt=1e-3, bs=8, tol=1e-6, storage="f32"),
+    "heat256": dict(n=256, kappa=1.0, tableau="sdirk2", dt=1e-3, bs=8, tol=1e-3, tol64=1e-4, storage="f32"),
+    "heat256-tight": dict(n=256, kappa=1.0, tableau="sdirk2", dt=1e-3, bs=8, tol=1e-6, tol64=1e-6, storage="f32"),
+    "heat256-4s3pB": dict(n=256, kappa=1.0, tableau="4s3pB", dt=1e-3, bs=8, tol=1e-6, tol64=1e-6, storage="f32"),
+    "heat256-f16": dict(n=256, kappa=1.0, tableau="sdirk2", dt=1e-3, bs=8, tol=1e-3, tol64=1e-4, storage="f16"),
+    "heat128": dict(n=128, kappa=1.0, tableau="sdirk2", dt=1e-3, bs=8, tol=1e-3, tol64=1e-4, storage="f32"),
 }
+MATCH = 1.05  # matched error: within 5 % of the exact solve's error
 HBM_FALLBACK_GBS = 6400.0
 
 
@@ -225,7 +232,7 @@ def run_reference(args, cfg):
 def workload_config(name, cfg):
     return {"workload": name, "grid": "%d^3" % cfg["n"], "dof": cfg["n"] ** 3, "kappa": cfg["kappa"],
             "tableau": cfg["tableau"], "dt": cfg["dt"], "krylov": "cg", "bj_block": cfg["bs"],
-            "tol_rel": cfg["tol"], "storage": cfg["storage"], "arith": "f32",
+            "tol_rel": cfg["tol"], "tol_rel_fp64": cfg["tol64"], "storage": cfg["storage"], "arith": "f32",
             "solution": "f32", "high_precision": "f64",
             "u0": "sine mode + 32 random modes (seed 0)", "l2": "working set > L2 (no flush needed)"}
 
@@ -451,7 +458,7 @@ def main():
     # ---------------- plain FP64 DIRK step of the same problem
     fp64 = None
     if not args.no_fp64:
-        q = make("f64", cfg["tol"], 0)
+        q = make("f64", cfg["tol64"], 0)
         rk.rk_integrate(q.h, dt, args.warmup)
         k64 = args.steps
         torch.cuda.synchronize()
@@ -465,8 +472,15 @@ def main():
         q.close()
         d64, c64 = closed_form(n, cfg["kappa"], dt, args.warmup + k64, tab, modes)
         fp64 = {"value": N * k64 / sec64, "ms_per_step": 1e3 * sec64 / k64, "steps": k64,
-                "iters_per_step": s64.iters_total / k64, "err_vs_discrete": rel(u64, d64),
+                "iters_per_step": s64.iters_total / k64, "tol_rel": cfg["tol64"], "err_vs_discrete": rel(u64, d64),
                 "err_vs_continuous": rel(u64, c64)}
+
+    # ---------------- matched error: both paths within MATCH x the error of an
+    # exact solve (the fully discrete solution) against the exact solution
+    e_exact = rel(disc, cont)
+    matched = {"exact_solve_err": e_exact, "mixed_ratio": err_cont / e_exact,
+               "fp64_ratio": (fp64["err_vs_continuous"] / e_exact) if fp64 else None, "bound": MATCH}
+    matched["ok"] = bool(matched["mixed_ratio"] <= MATCH and (fp64 is None or matched["fp64_ratio"] <= MATCH))
 
     # ---------------- oracle on the host cores
     cpu = None
@@ -490,6 +504,7 @@ def main():
             "true_res_max": st.true_res,
             "err_vs_discrete": err_disc,
             "err_vs_continuous": err_cont,
+            "matched_error": matched,
             "fp64_plain": fp64,
             "speedup_vs_fp64": (value / world / fp64["value"]) if fp64 else None,
             "kernels": kernels,
