@@ -75,10 +75,12 @@ def ncu_traffic(kernel, workload):
     try:
         with open(path) as f:
             d = json.load(f)[workload]
-        src = os.path.join(ROOT, "paper_2412_16638_b300", "csrc", "rk_heat.cuh")
-        with open(src, "rb") as f:
-            sha = hashlib.sha256(f.read()).hexdigest()[:16]
-        if d.get("heat_src_sha256_16") != sha:
+        h = hashlib.sha256()
+        for name in ("rk_heat.cuh", "rk_tiled.cuh"):
+            with open(os.path.join(ROOT, "paper_2412_16638_b300", "csrc", name), "rb") as f:
+                h.update(f.read())
+        sha = h.hexdigest()[:16]
+        if d.get("kernel_src_sha256_16") != sha:
             return None
         return float(d[kernel]["dram_bytes_per_launch"])
     except Exception:
@@ -207,12 +209,11 @@ def run_reference(args, cfg):
     if rank != 0:
         return 0
     ipath = os.path.join(ROOT, "profiles", "traffic.json")
-    iters = None
     try:
         with open(ipath) as f:
             iters = float(json.load(f)[args.workload]["iters_per_step"])
     except Exception:
-        iters = 240.0
+        iters = 60.0
     t_step, sample = oracle_step_seconds(cfg, iters)
     N = cfg["n"] ** 3
     value = N / t_step
