@@ -16,6 +16,9 @@ the paper:
 * ``krylov``    -- block-Jacobi, preconditioned CG and restarted GMRES for the
                    stage systems (Sec. 3, Eq. corelinear; stopping rule of
                    Sec. 5.3).
+* ``fdm``       -- the fast-diagonalization preconditioner (Sec. 3, Eqs.
+                   preconbasic, Pinvform, TensorDecomp) for the heat stage
+                   matrix.
 * ``dirk``      -- the perturbed stage loop (Sec. 2.2.1, Eqs. mpAstep1-5;
                    Sec. 4.2 precision policy), all in float64.
 
@@ -25,4 +28,4 @@ solves, observed order).  The variable-coefficient advection-diffusion
 operator at full size has no closed form: beyond the tiny-grid brute-force and
 dense pins it is "parity unpinned beyond the oracle".
 """
-from . import tableau, operators, krylov, dirk  # noqa: F401
+from . import tableau, operators, krylov, fdm, dirk  # noqa: F401

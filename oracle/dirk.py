@@ -23,14 +23,16 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import krylov
+from . import fdm, krylov
 
 
 class Solver:
-    """Stage solver settings: 'cg' (heat) or 'gmres' (advection-diffusion)."""
+    """Stage solver settings: 'cg' (heat) or 'gmres' (advection-diffusion);
+    precond 'bj' (x-line block-Jacobi of size bs) or 'fdm' (fast
+    diagonalization, constant-coefficient heat operators only)."""
 
-    def __init__(self, method="cg", bs=8, tol_rel=1e-12, tol_abs=0.0, max_iter=2000, restart=30):
-        self.method, self.bs = method, bs
+    def __init__(self, method="cg", bs=8, tol_rel=1e-12, tol_abs=0.0, max_iter=2000, restart=30, precond="bj"):
+        self.method, self.bs, self.precond = method, bs, precond
         self.tol_rel, self.tol_abs = tol_rel, tol_abs
         self.max_iter, self.restart = max_iter, restart
         self._cache = {}
@@ -39,13 +41,16 @@ class Solver:
         """Solve (I - s L) k = g."""
         key = (id(op), float(s))
         if key not in self._cache:
-            M = krylov.shifted(op.csr(), s)
-            self._cache[key] = (M, krylov.BlockJacobi(M, op.n, self.bs))
-        M, bj = self._cache[key]
+            if self.precond == "fdm":
+                self._cache[key] = fdm.FastDiagonalization(op.n, op.kappa, s).apply
+            else:
+                M = krylov.shifted(op.csr(), s)
+                self._cache[key] = krylov.BlockJacobi(M, op.n, self.bs).apply
+        apply_M = self._cache[key]
         apply_A = lambda v: v - s * op.apply(v)
         if self.method == "cg":
-            return krylov.pcg(apply_A, bj.apply, g, self.tol_rel, self.tol_abs, self.max_iter)
-        return krylov.gmres(apply_A, bj.apply, g, self.restart, self.tol_rel, self.tol_abs, self.max_iter)
+            return krylov.pcg(apply_A, apply_M, g, self.tol_rel, self.tol_abs, self.max_iter)
+        return krylov.gmres(apply_A, apply_M, g, self.restart, self.tol_rel, self.tol_abs, self.max_iter)
 
 
 def rk_step(u, dt, tableau, op, solver: Solver, corrected=True, stats=None):

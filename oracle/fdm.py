@@ -1,0 +1,82 @@
+"""Fast-diagonalization preconditioner (Sec. 3, Eqs. preconbasic, Pinvform,
+TensorDecomp), float64.  TEST INFRASTRUCTURE ONLY.
+
+On the unit cube with a uniform Cartesian grid the preconditioner has the
+Kronecker-sum form
+
+    P = I (x) I (x) A + I (x) B (x) I + C (x) I (x) I           (Eq. preconbasic)
+
+with n x n one-dimensional operators A (x), B (y), C (z).  With the spectral
+decompositions A = Q_A Lambda_A Q_A^-1 (and likewise B, C),
+
+    P^-1 = (Q_C (x) Q_B (x) Q_A) P_D^-1 (Q_C^-1 (x) Q_B^-1 (x) Q_A^-1)  (Eq. Pinvform)
+
+where P_D is diagonal, and the Kronecker factor splits into the three
+tensor operations T_L T_M T_R of Eq. TensorDecomp.  The tensor operations act
+on the lexicographic vector x_{i + j n + k n^2} (Sec. 4):
+
+    (T_R x)_{ijk} = sum_q Q_{iq} x_{qjk},   (T_M x)_{ijk} = sum_q Q_{jq} x_{iqk},
+    (T_L x)_{ijk} = sum_q Q_{kq} x_{ijq}.
+
+For the constant-coefficient heat stage system (I - s L) k = g with
+L = kappa/h^2 (7-point Laplacian) the splitting is exact: A = B = C =
+I/3 + (s kappa/h^2) K1D with K1D = tridiag(-1, 2, -1) (Sec. 5.2.1), so P is
+the system matrix itself and preconditioned CG converges in one iteration
+in exact arithmetic.  The one-dimensional decomposition is taken from LAPACK
+(numpy.linalg.eigh); the tests pin it to the closed-form sine eigenpairs.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .operators import grid_h
+
+
+def line_operator(n: int, kappa: float, s: float) -> np.ndarray:
+    """The one-dimensional factor I/3 + (s kappa / h^2) tridiag(-1, 2, -1)."""
+    c = s * kappa / grid_h(n) ** 2
+    K = 2.0 * np.eye(n) - np.eye(n, k=1) - np.eye(n, k=-1)
+    return np.eye(n) / 3.0 + c * K
+
+
+def _t_r(Q, x3):
+    """T_R: contract the x index (fastest; x3 is indexed [k, j, i])."""
+    return np.einsum("iq,kjq->kji", Q, x3)
+
+
+def _t_m(Q, x3):
+    """T_M: contract the y index."""
+    return np.einsum("jq,kqi->kji", Q, x3)
+
+
+def _t_l(Q, x3):
+    """T_L: contract the z index."""
+    return np.einsum("kq,qji->kji", Q, x3)
+
+
+class FastDiagonalization:
+    """z = P^-1 r for the heat stage matrix I - s L (Eq. Pinvform)."""
+
+    def __init__(self, n: int, kappa: float, s: float):
+        self.n = n
+        A = line_operator(n, kappa, s)
+        lam, Q = np.linalg.eigh(A)  # A = Q diag(lam) Q^T, Q orthogonal
+        self.Q = Q
+        self.lam = lam
+        # P_D = I (x) I (x) Lambda_A + I (x) Lambda_B (x) I + Lambda_C (x) I (x) I,
+        # indexed [k, j, i]
+        self.pd = lam[:, None, None] + lam[None, :, None] + lam[None, None, :]
+
+    def apply(self, r):
+        n, Q = self.n, self.Q
+        Qi = Q.T  # Q^-1 of an orthogonal matrix
+        x = np.asarray(r, dtype=np.float64).reshape(n, n, n)
+        # (Q_C^-1 (x) Q_B^-1 (x) Q_A^-1) = T_L^-1 T_M^-1 T_R^-1 applied right to left
+        x = _t_r(Qi, x)
+        x = _t_m(Qi, x)
+        x = _t_l(Qi, x)
+        x = x / self.pd
+        x = _t_r(Q, x)
+        x = _t_m(Q, x)
+        x = _t_l(Q, x)
+        return x.reshape(-1)
