@@ -59,6 +59,15 @@ typedef enum {
 
 typedef enum { RK_KRYLOV_CG = 0, RK_KRYLOV_GMRES = 1 } rk_krylov;
 
+/* Preconditioner of the stage solves.  RK_PREC_BLOCK_JACOBI: x-line blocks of
+ * bj_block nodes.  RK_PREC_FDM: the fast-diagonalization preconditioner of
+ * Sec. 3 (Eqs. preconbasic, Pinvform, TensorDecomp), exact for the
+ * constant-coefficient heat stage matrix; applied as six tensor-core mode
+ * products in the storage precision (TF32 for FP32 storage, FP16/BF16 for
+ * 16-bit storage, FP32 accumulation).  Needs CG, RK_OP_HEAT7, storage F32,
+ * F16 or BF16, n <= 256 and n * (storage bytes) a multiple of 16. */
+typedef enum { RK_PREC_BLOCK_JACOBI = 0, RK_PREC_FDM = 1 } rk_precond;
+
 typedef struct {
   int op;                    /* rk_op                                             */
   int n;                     /* interior nodes per direction, 1 <= n <= 1024      */
@@ -85,6 +94,7 @@ typedef struct {
                       ||L r_i - (I - tau a_ii L) k^eps_i|| / ||L r_i|| exceeds
                       tol_true (0 disables)                                         */
   double tol_true; /* true-residual acceptance bound (<= 0: report only)            */
+  int precond;     /* rk_precond (0 = block-Jacobi)                                 */
 } rk_solver_desc;
 
 typedef struct {
@@ -143,8 +153,11 @@ rk_status rk_apply_op(rk_problem* p, const double* x, double* y, int is_device_p
 rk_status rk_solve(rk_problem* p, double shift, const double* g, double* k,
                    int is_device_ptr, rk_stats* stats);
 
-/* z = D^{-1} r with D the x-line block-Jacobi diagonal of (I - shift L), in
- * the problem's storage/arithmetic precision.  r, z: n^3 float64. */
+/* z = M^{-1} r with M the problem's preconditioner of (I - shift L): the
+ * x-line block-Jacobi diagonal, or the fast-diagonalization operator P, in
+ * the problem's storage/arithmetic precision (r is rounded to the storage
+ * type unscaled, so with FP16 storage |r| must stay below 65504).  r, z: n^3
+ * float64. */
 rk_status rk_apply_precond(rk_problem* p, double shift, const double* r, double* z,
                            int is_device_ptr);
 

@@ -196,11 +196,7 @@ rk_status op_correct_f64(rk_problem* p, double shift, const double* gv, const vo
 }
 
 // ------------------------------------------------------------ tiled sweeps
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-static EncodeTiledFn encode_fn() {
+EncodeTiledFn encode_fn() {
   static EncodeTiledFn fn = nullptr;
   static bool tried = false;
   static std::mutex mu;
@@ -215,13 +211,6 @@ static EncodeTiledFn encode_fn() {
     cudaGetLastError();
   }
   return fn;
-}
-
-template <typename S>
-static CUtensorMapDataType tma_dtype() {
-  if (sizeof(S) == 8) return CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
-  if (sizeof(S) == 4) return CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-  return std::is_same<S, __half>::value ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
 }
 
 // Decide once per problem whether the tiled sweeps apply (n <= 256, n a
@@ -250,9 +239,9 @@ static bool tiled_setup(rk_problem* p) {
   const cuuint64_t strides[2] = {(cuuint64_t)n * sizeof(S), (cuuint64_t)n * n * sizeof(S)};
   const cuuint32_t box[3] = {(cuuint32_t)n, (cuuint32_t)(ty + 2), 1};
   const cuuint32_t estr[3] = {1, 1, 1};
-  void* bufs[3] = {p->wr, p->wp[0], p->wp[1]};
-  CUtensorMap* maps[3] = {&tm.r, &tm.p[0], &tm.p[1]};
-  for (int i = 0; i < 3; ++i) {
+  void* bufs[4] = {p->wr, p->wp[0], p->wp[1], p->wz};
+  CUtensorMap* maps[4] = {&tm.r, &tm.p[0], &tm.p[1], &tm.z};
+  for (int i = 0; i < 4; ++i) {
     if (enc(maps[i], tma_dtype<S>(), 3, bufs[i], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
@@ -295,8 +284,15 @@ static bool tiled_setup(rk_problem* p) {
 // the iteration count of the previous solve of the same stage slot.
 static rk_status heat_cg_solve(rk_problem* p, double shift, const double* g64, RhsScalars* rs, void* x,
                                int slot, int* iters, int* status) {
+  // With the fast-diagonalization preconditioner the sweeps run with the
+  // identity block (z = r) and z = P^-1 r is formed after cg_init and after
+  // every sweep B by the tensor-core passes, which also update r.z and beta.
+  const bool fdm = p->sol.precond == RK_PREC_FDM;
   const MinvEntry* me = nullptr;
-  RK_TRY(get_minv_entry(p, shift, &me));
+  if (fdm)
+    RK_TRY(fdm_setup(p));
+  else
+    RK_TRY(get_minv_entry(p, shift, &me));
   CgScalars init{};
   init.tol_rel = p->sol.tol_rel;
   init.tol_abs = p->sol.tol_abs;
@@ -307,7 +303,7 @@ static rk_status heat_cg_solve(rk_problem* p, double shift, const double* g64, R
   dispatch_st(p->sol.storage, [&](auto ts, auto tt) {
     using S = typename decltype(ts)::type;
     using T = typename decltype(tt)::type;
-    dispatch_bs(p->sol.bj_block, [&](auto bsc) {
+    dispatch_bs(fdm ? 1 : p->sol.bj_block, [&](auto bsc) {
       constexpr int BS = decltype(bsc)::value;
       constexpr int SEG = seg_of<S, BS>();
       HeatGeo g = heat_geo(p, SEG);
@@ -317,7 +313,13 @@ static rk_status heat_cg_solve(rk_problem* p, double shift, const double* g64, R
       S* z = static_cast<S*>(p->wz);
       using X = typename XOf<S>::type;
       X* xs = static_cast<X*>(x);
-      const BjInv<T, BS> M = bj_param<T, BS>(me->host);
+      BjInv<T, BS> M;
+      if (fdm) {
+        for (auto& v : M.m) v = T(0);
+        for (int i = 0; i < BS; ++i) M.m[i * BS + i] = M.m[BS * BS + i * BS + i] = T(1);
+      } else {
+        M = bj_param<T, BS>(me->host);
+      }
       auto ki = cg_init<S, T, BS, SEG>;
       auto ka = cg_sweep_a<S, T, SEG>;
       auto kb = cg_sweep_b<S, T, BS, SEG>;
@@ -328,6 +330,7 @@ static rk_status heat_cg_solve(rk_problem* p, double shift, const double* g64, R
       const double Nx = (double)p->N * sizeof(X);
       launch(p, K_CG_INIT, 8.0 * p->N + 2.0 * Ns + Nx,
              [&] { ki<<<gi, kThreads, 0, p->st>>>(g, g64, rs, M, r, z, xs, p->sc, p->partials); });
+      if (fdm && (st = fdm_apply(p, shift, true, solve, 0)) != RK_OK) return;
       const bool tiled = tiled_setup<S, T, BS, SEG>(p);
       const TileGeo tg = tiled ? p->tiled->tg : TileGeo{};
       const int tgrid = tg.nyt * tg.nzc, tthreads = tg.tpl * tg.ty, athreads = tg.tpl * (tg.ty + 2);
@@ -344,8 +347,9 @@ static rk_status heat_cg_solve(rk_problem* p, double shift, const double* g64, R
           if (tiled) {
             // 8 vectors per iteration: A reads r, p_old, writes p; B reads p, r, x, writes r, x
             prof_begin(p, K_CG_A, (idx == 0 ? 2.0 : 3.0) * Ns, solve, idx);
-            cg_tiled_a<S, T, BS, SEG><<<tgrid, athreads, sma, p->st>>>(p->tiled->r, p->tiled->p[cur ^ 1], tg, d, o, M,
-                                                                       pn, p->sc, p->partials);
+            cg_tiled_a<S, T, BS, SEG><<<tgrid, athreads, sma, p->st>>>(fdm ? p->tiled->z : p->tiled->r,
+                                                                       p->tiled->p[cur ^ 1], tg, d, o, M, pn, p->sc,
+                                                                       p->partials);
             prof_end(p);
             prof_begin(p, K_CG_B, (idx == 0 ? 3.0 * Ns + Nx : 3.0 * Ns + 2.0 * Nx), solve, idx);
             cg_tiled_b<S, T, BS, SEG><<<tgrid, tthreads, smb, p->st>>>(p->tiled->p[cur], tg, d, o, M, xs, r, p->sc,
@@ -359,6 +363,7 @@ static rk_status heat_cg_solve(rk_problem* p, double shift, const double* g64, R
             kb<<<gb, kThreads, 0, p->st>>>(g, d, o, pn, xs, r, z, M, p->sc, p->partials);
             prof_end(p);
           }
+          if (fdm && (st = fdm_apply(p, shift, true, solve, idx + 1)) != RK_OK) return;
           cur ^= 1;
         }
         launched += chunk;
@@ -617,6 +622,25 @@ static rk_status check_solver(const rk_solver_desc* s, const rk_problem_desc* d)
     set_error("max_refine must be in 0..10");
     return RK_ERR_ARG;
   }
+  if (s->precond != RK_PREC_BLOCK_JACOBI && s->precond != RK_PREC_FDM) {
+    set_error("unknown preconditioner %d", s->precond);
+    return RK_ERR_ARG;
+  }
+  if (s->precond == RK_PREC_FDM) {
+    if (s->krylov != RK_KRYLOV_CG || (d && d->op != RK_OP_HEAT7)) {
+      set_error("the fast-diagonalization preconditioner is built for CG on the heat operator");
+      return RK_ERR_ARG;
+    }
+    if (s->storage == RK_F64) {
+      set_error("the fast-diagonalization preconditioner runs on the tensor cores: FP32, FP16 or BF16 storage");
+      return RK_ERR_ARG;
+    }
+    const size_t es = s->storage == RK_F32 ? 4 : 2;
+    if (d && (d->n > 256 || ((size_t)d->n * es) % 16 != 0)) {
+      set_error("the fast-diagonalization preconditioner needs n <= 256 and 16-byte rows (n = %d)", d->n);
+      return RK_ERR_ARG;
+    }
+  }
   return RK_OK;
 }
 
@@ -645,6 +669,7 @@ static void free_problem(rk_problem* p) {
   if (p->h_sc) cudaFreeHost(p->h_sc);
   if (p->h_rs) cudaFreeHost(p->h_rs);
   csr_free(p);
+  fdm_free(p);
   prof_free(p);
   delete p->tiled;
   delete p;
@@ -958,6 +983,8 @@ rk_status rk_apply_precond(rk_problem* p, double shift, const double* r, double*
   }
   if (p->desc.op != RK_OP_HEAT7) {
     RK_TRY(csr_precond_f64(p, shift, rin, zout));
+  } else if (p->sol.precond == RK_PREC_FDM) {
+    RK_TRY(fdm_precond_f64(p, shift, rin, zout));
   } else {
     const MinvEntry* me = nullptr;
     RK_TRY(get_minv_entry(p, shift, &me));

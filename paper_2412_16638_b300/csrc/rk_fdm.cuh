@@ -1,0 +1,325 @@
+// Fast-diagonalization preconditioner of the heat stage matrix on the
+// 5th-generation tensor cores (Sec. 3, Eqs. preconbasic, Pinvform,
+// TensorDecomp; the tensor operations T_R, T_M, T_L of Sec. 4).
+//
+// For the constant-coefficient system I - s L with L = kappa/h^2 times the
+// 7-point Laplacian, the one-dimensional factors share the orthonormal sine
+// basis Q_jk = sqrt(2/(n+1)) sin((j+1)(k+1) pi/(n+1)) (Q = Q^T = Q^-1) and
+// P_D = 1 + c (mu_i + mu_j + mu_k), c = s kappa/h^2, mu_k = 4 sin^2((k+1) pi /
+// (2(n+1))).  P^-1 = (Q (x) Q (x) Q) P_D^-1 (Q (x) Q (x) Q) is exact.
+//
+// Each tensor operation is one pass of a persistent GEMM over the vector
+// viewed as an (n^2 x n) row-major matrix X (rows = the two slow indices,
+// columns = the fastest index):  Y = X Q^T, a K-major x K-major product.
+// The epilogue stores Y transposed, out[j n^2 + m] = Y[m][j], which moves the
+// contracted index to the slowest position.  Three passes therefore contract
+// x, then y, then z, and return the vector to its lexicographic layout:
+//   [z][y][x] -> [x'][z][y] -> [y'][x'][z] -> [z'][y'][x'].
+// Unlike the paper's three strided kernels (one per T), every pass reads and
+// writes with unit stride and contracts on the tensor cores.
+//
+// Per CTA (one per SM, persistent over 128-row tiles): warp 0 issues TMA
+// loads (the CTA's N tile of Q once, then 128 x 128-byte K blocks of X into a
+// ring of stages); warp 1 owns the tensor memory and issues tcgen05.mma with
+// the accumulator in TMEM (two accumulators, so the epilogue of one tile
+// overlaps the MMAs of the next); warps 2-5 read the accumulator with
+// tcgen05.ld and store.  Every mbarrier wait is bounded; a wait that runs out
+// sets a shared flag that stops the other roles, the CTA lets its copies and
+// MMAs land, frees its tensor memory and reports status 6.
+//
+// Storage float runs kind::tf32, __half and __nv_bfloat16 run kind::f16 with
+// the same type for both operands; accumulation is FP32 in TMEM.
+#pragma once
+#include <cuda.h>
+
+#include <type_traits>
+
+#include "rk_device.cuh"
+#include "rk_heat.cuh"
+#include "rk_tiled.cuh"
+
+namespace rk {
+
+constexpr int kFdmStages = 4;      // K-block stages of X
+constexpr int kFdmThreads = 192;   // 6 warps
+constexpr int kFdmRows = 128;      // rows per tile (TMEM lanes)
+constexpr int kFdmTmemCols = 256;  // two FP32 accumulators of up to 128 columns
+constexpr uint32_t kFdmStageBytes = kFdmRows * 128;
+
+struct FdmGeo {
+  int n;        // nodes per direction
+  int rows;     // n*n
+  int nt;       // columns per N tile: multiple of 16, <= 128
+  int ntiles;   // N tiles (1 or 2); the grid is a multiple of ntiles
+  int kblocks;  // 128-byte K blocks: ceil(n * sizeof(S) / 128)
+  int mtiles;   // ceil(rows / 128)
+};
+
+enum FdmMode { kFdmPlain = 0, kFdmScale = 1, kFdmDot = 2 };
+
+// Dynamic shared memory: 1 KB alignment slack, Q tile, X stages, barriers.
+__host__ __device__ constexpr size_t fdm_smem_bytes(int nt, int kblocks) {
+  return 1024 + (size_t)kblocks * nt * 128 + (size_t)kFdmStages * kFdmStageBytes + 256;
+}
+
+// ---------------------------------------------------------------- PTX wrappers
+__device__ __forceinline__ void tma_load2(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_addr(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// Bounded wait that also gives up once another role has failed.
+__device__ __forceinline__ bool fdm_wait(uint64_t* bar, uint32_t parity, volatile int* fail) {
+  for (unsigned i = 0; i < kWaitSpins; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 63u) == 63u && *fail) return false;
+  }
+  *fail = 1;
+  return false;
+}
+
+// Shared-memory matrix descriptor of a K-major tile with 128-byte swizzle:
+// rows of 128 bytes, 8-row groups 1024 bytes apart (stride byte offset),
+// descriptor version 1, swizzle mode 2 (128 B).  The tile base is 1024-aligned.
+__device__ __forceinline__ uint64_t fdm_desc(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor: FP32 accumulator, A/B format, both K-major, N, M=128.
+template <typename S>
+__host__ __device__ constexpr uint32_t fdm_idesc(int nt) {
+  constexpr uint32_t fmt = std::is_same<S, float>::value ? 2u : (std::is_same<S, __half>::value ? 0u : 1u);
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(nt >> 3) << 17) | ((uint32_t)(kFdmRows >> 4) << 24);
+}
+
+template <typename S>
+__device__ __forceinline__ void fdm_mma(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  if constexpr (std::is_same<S, float>::value) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+  }
+}
+
+__device__ __forceinline__ void fdm_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 16 consecutive FP32 accumulator columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// ---------------------------------------------------------------- the pass
+// out[j*rows + m] = sum_k in[m*n + k] Q[j*n + k]     (j < n, m < rows)
+// mode kFdmScale: divided by P_D = 1 + c (mu[m / n] + mu[m % n] + mu[j]).
+// mode kFdmDot:   also r.z over the output (z = out, r = rdot, same layout);
+//                 the last CTA turns it into the CG scalars: beta is rescaled
+//                 from the unpreconditioned r.r the sweep left behind, rz set.
+// cg != 0: the pass belongs to a CG solve and returns at once when sc->done.
+// A timed-out wait sets sc->status = 6 and sc->done = 1 in either case.
+template <typename S>
+__global__ void __launch_bounds__(kFdmThreads, 1)
+    fdm_pass(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CUtensorMap tm_q, FdmGeo fg, int mode,
+             float c, const float* __restrict__ mu, S* __restrict__ out, const S* __restrict__ rdot, int cg,
+             CgScalars* sc, double* partials) {
+  if (cg && sc->done) return;
+  extern __shared__ unsigned char fdm_smem_raw[];
+  // 1024-byte alignment of the shared-window offset (128-byte swizzle atoms)
+  unsigned char* sm = fdm_smem_raw + ((1024u - (smem_addr(fdm_smem_raw) & 1023u)) & 1023u);
+  const uint32_t qbytes = (uint32_t)fg.kblocks * fg.nt * 128;
+  unsigned char* sQ = sm;
+  unsigned char* sX = sm + qbytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sX + (size_t)kFdmStages * kFdmStageBytes);
+  uint64_t* full = bars;                    // [kFdmStages] X stage landed
+  uint64_t* empty = bars + kFdmStages;      // [kFdmStages] X stage consumed by the MMAs
+  uint64_t* qfull = bars + 2 * kFdmStages;  // Q tile landed
+  uint64_t* accfull = qfull + 1;            // [2] accumulator ready
+  uint64_t* accempty = qfull + 3;           // [2] accumulator drained
+  uint64_t* mmadone = qfull + 5;            // every MMA of the CTA finished
+  uint32_t* tholder = reinterpret_cast<uint32_t*>(qfull + 6);
+  volatile int* fail = reinterpret_cast<volatile int*>(qfull + 7);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ntile = blockIdx.x % fg.ntiles;
+  const int total = fg.mtiles * fg.ntiles;
+  constexpr int KB = 128 / (int)sizeof(S);  // elements per 128-byte K block
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kFdmStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(qfull, 1);
+    mbar_init(&accfull[0], 1);
+    mbar_init(&accfull[1], 1);
+    mbar_init(&accempty[0], 4 * 32);
+    mbar_init(&accempty[1], 4 * 32);
+    mbar_init(mmadone, 1);
+    *fail = 0;
+    mbar_fence_init();
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tholder)),
+                 "r"(kFdmTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    tc_fence_before();
+  }
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = *tholder;
+
+  float dot = 0.f;
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---- TMA producer
+      mbar_expect_tx(qfull, qbytes);
+      for (int kb = 0; kb < fg.kblocks; ++kb)
+        tma_load2(sQ + (size_t)kb * fg.nt * 128, &tm_q, qfull, kb * KB, ntile * fg.nt);
+      uint32_t it = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+        const int mt = t / fg.ntiles;
+        for (int kb = 0; kb < fg.kblocks; ++kb, ++it) {
+          const int s = (int)(it % kFdmStages);
+          if (!fdm_wait(&empty[s], ((it / kFdmStages) & 1u) ^ 1u, fail)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&full[s], kFdmStageBytes);
+          tma_load2(sX + (size_t)s * kFdmStageBytes, &tm_in, &full[s], kb * KB, mt * kFdmRows);
+        }
+      }
+      // every copy issued must land before the CTA exits
+      (void)mbar_wait(qfull, 0);
+      const uint32_t first = it > (uint32_t)kFdmStages ? it - kFdmStages : 0u;
+      for (uint32_t j = first; j < it; ++j) (void)mbar_wait(&full[j % kFdmStages], (j / kFdmStages) & 1u);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---- MMA issuer
+      const uint32_t idesc = fdm_idesc<S>(fg.nt);
+      bool ok = fdm_wait(qfull, 0, fail);
+      tc_fence_after();
+      const uint32_t q0 = smem_addr(sQ), x0 = smem_addr(sX);
+      uint32_t it = 0, lt = 0;
+      for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++lt) {
+        const uint32_t acc = lt & 1u;
+        if (!fdm_wait(&accempty[acc], ((lt >> 1) & 1u) ^ 1u, fail)) break;
+        tc_fence_after();
+        const uint32_t d = tbase + acc * 128u;
+        for (int kb = 0; kb < fg.kblocks; ++kb, ++it) {
+          const int s = (int)(it % kFdmStages);
+          if (!fdm_wait(&full[s], (it / kFdmStages) & 1u, fail)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint64_t ad = fdm_desc(x0 + (uint32_t)s * kFdmStageBytes);
+          const uint64_t bd = fdm_desc(q0 + (uint32_t)kb * fg.nt * 128u);
+#pragma unroll
+          for (int k = 0; k < 4; ++k)  // 32 bytes of K per instruction
+            fdm_mma<S>(d, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), idesc, (kb | k) != 0);
+          fdm_commit(&empty[s]);
+        }
+        if (ok) fdm_commit(&accfull[acc]);
+      }
+      // all MMAs issued by this thread complete before the commit below arrives
+      fdm_commit(mmadone);
+      (void)mbar_wait(mmadone, 0);
+    }
+  } else {
+    // ---- epilogue: warps 2..5 own TMEM lane quadrants (warp % 4)
+    const int quad = warp & 3;
+    const int row = quad * 32 + lane;
+    uint32_t lt = 0;
+    for (int t = blockIdx.x; t < total; t += gridDim.x, ++lt) {
+      const uint32_t acc = lt & 1u;
+      // warp-uniform: tcgen05.ld below is a warp-collective instruction
+      if (!__all_sync(0xffffffffu, fdm_wait(&accfull[acc], (lt >> 1) & 1u, fail))) break;
+      tc_fence_after();
+      const int m = (t / fg.ntiles) * kFdmRows + row;
+      const bool mrow = m < fg.rows;
+      float mab = 0.f;
+      if (mode == kFdmScale && mrow) mab = mu[m / fg.n] + mu[m % fg.n];
+      const int j0 = ntile * fg.nt;
+      for (int c0 = 0; c0 < fg.nt; c0 += 16) {
+        float v[16];
+        tmem_ld16(tbase + ((uint32_t)(quad * 32) << 16) + acc * 128u + (uint32_t)c0, v);
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) {
+          const int j = j0 + c0 + jj;
+          if (mrow && j < fg.n) {
+            float y = v[jj];
+            if (mode == kFdmScale) y = y / fmaf(c, mab + mu[j], 1.0f);
+            const S ys = nar<S>(y);
+            const size_t o = (size_t)j * fg.rows + m;
+            out[o] = ys;
+            if (mode == kFdmDot) dot = fmaf(wid<float>(rdot[o]), wid<float>(ys), dot);
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&accempty[acc]);
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(kFdmTmemCols) : "memory");
+  }
+  const bool failed = *fail != 0;
+  if (failed && threadIdx.x == 0) {
+    sc->status = 6;
+    sc->done = 1;
+  }
+  if (mode != kFdmDot) return;
+  double a[1] = {(double)dot};
+  double tot[1];
+  if (grid_reduce<1, 0u>(a, partials, &sc->ticket, tot)) {
+    if (sc->status == 6) return;
+    const double rz = tot[0];
+    if (sc->iter > 0) sc->beta = sc->beta * (rz / sc->rz);
+    sc->rz = rz;
+    if (!isfinite(rz)) {
+      sc->done = 1;
+      sc->status = 5;
+    } else if (!(rz > 0.0)) {
+      sc->done = 1;
+      sc->status = 4;
+    }
+  }
+}
+
+}  // namespace rk

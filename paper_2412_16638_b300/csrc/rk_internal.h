@@ -16,6 +16,7 @@
 #include "rk_heat.cuh"
 #include "rk_vec.cuh"
 #include "rk_tiled.cuh"
+#include "rk_fdm.cuh"
 
 namespace rk {
 
@@ -75,6 +76,18 @@ constexpr int seg_of() {
 }
 
 int device_sms();
+// cuTensorMapEncodeTiled through the runtime's driver entry point (null if
+// the driver does not provide it).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_fn();
+template <typename S>
+inline CUtensorMapDataType tma_dtype() {
+  if (sizeof(S) == 8) return CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+  if (sizeof(S) == 4) return CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  return std::is_same<S, __half>::value ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+}
 int grid_for(const void* kernel, long long work_items, int threads = kThreads);
 
 struct MinvEntry {
@@ -111,13 +124,29 @@ struct TiledMaps {
   bool tried = false;    // eligibility already decided
   TileGeo tg{};
   CUtensorMap r, p[2];   // r and the two p buffers, box (n, ty+2, 1)
+  CUtensorMap z;         // z (the fast-diagonalization output), same box
+};
+
+// Fast-diagonalization preconditioner state of a heat problem (storage
+// float/half/bf16, n <= 256): the sine basis Q and the eigenvalues mu of
+// tridiag(-1, 2, -1), one temporary vector, and the 2-D tensor maps of the
+// (n^2 x n) views of r, z and the temporary plus the one of Q.
+struct FdmState {
+  bool ok = false;
+  FdmGeo geo{};
+  void* q = nullptr;
+  float* mu = nullptr;
+  void* t = nullptr;
+  CUtensorMap in_r, in_z, in_t, qmap;
+  int grid = 0;
+  size_t smem = 0;
 };
 
 // Kernel ids for the launch profiler.
 enum Kid {
   K_CG_INIT, K_CG_A, K_CG_B, K_OP, K_CORRECT, K_COMBINE, K_NORMS, K_WIDEN, K_TRUERES, K_ADDSCALED, K_BJ,
   K_CSR_SPMV, K_CSR_CORRECT, K_CSR_BJ_SETUP, K_GM_INIT, K_GM_ARNOLDI, K_GM_ORTH, K_GM_NORM, K_GM_UPDATE,
-  K_GM_PREC, K_BATCH, K_COUNT
+  K_GM_PREC, K_BATCH, K_FDM, K_COUNT
 };
 extern const char* const kKernelNames[K_COUNT];
 
@@ -177,6 +206,7 @@ struct rk_problem {
   rk::Csr csr;
   rk::GmresWork* gw = nullptr;
   rk::TiledMaps* tiled = nullptr;
+  rk::FdmState* fdm = nullptr;
   size_t bytes = 0;  // device footprint
   // launch accounting / profiler
   long long launches = 0;
@@ -214,6 +244,14 @@ inline void launch(rk_problem* p, int kid, double bytes, F&& f) {
   prof_end(p);
 }
 // CSR path
+// Fast-diagonalization preconditioner (heat, CG): set up once per problem;
+// z = P^-1 r on the problem's wr -> wz (6 tensor-core passes).  With cg the
+// last pass also forms r.z and updates the CG scalars; solve/idx tag the
+// launches for the profiler.
+rk_status fdm_setup(rk_problem* p);
+rk_status fdm_apply(rk_problem* p, double shift, bool cg, int solve, int idx);
+rk_status fdm_precond_f64(rk_problem* p, double shift, const double* r, double* z);
+void fdm_free(rk_problem* p);
 rk_status csr_setup(rk_problem* p);
 rk_status csr_free(rk_problem* p);
 rk_status gmres_solve(rk_problem* p, double shift, const double* g64, RhsScalars* rs, void* x, int slot,

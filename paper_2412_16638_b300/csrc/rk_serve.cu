@@ -173,8 +173,8 @@ extern "C" rk_status rk_integrate_batch(rk_problem** ps, int count, double dt, i
       set_error("rk_integrate_batch: problem %d is NULL", i);
       return RK_ERR_ARG;
     }
-    if (p->desc.op != RK_OP_HEAT7 || p->sol.krylov != RK_KRYLOV_CG) {
-      set_error("rk_integrate_batch: problem %d is not a heat/CG problem", i);
+    if (p->desc.op != RK_OP_HEAT7 || p->sol.krylov != RK_KRYLOV_CG || p->sol.precond != RK_PREC_BLOCK_JACOBI) {
+      set_error("rk_integrate_batch: problem %d is not a heat/CG/block-Jacobi problem", i);
       return RK_ERR_ARG;
     }
     if (p->q == 0) {
@@ -352,6 +352,7 @@ static size_t job_footprint(const rk_problem_desc& d, const rk_solver_desc& s, i
     const size_t nnz = N * 7;
     bytes += nnz * (4 + 8 + sb) + (N + 1) * 4 + (size_t)(s.restart + 2) * N * sb + N * s.bj_block * sb * 4;
   }
+  if (s.precond == RK_PREC_FDM) bytes += N * sb + (size_t)d.n * d.n * sb;
   return bytes;
 }
 
@@ -522,7 +523,8 @@ static void worker_loop(rk_server* s) {
     std::vector<rk_stats> stepstats(act.size());
     for (size_t i = 0; i < act.size(); ++i) {
       Job* j = act[i].get();
-      if (j->desc.op == RK_OP_HEAT7 && j->sol.krylov == RK_KRYLOV_CG && j->desc.n <= kBatchMaxN) {
+      if (j->desc.op == RK_OP_HEAT7 && j->sol.krylov == RK_KRYLOV_CG && j->sol.precond == RK_PREC_BLOCK_JACOBI &&
+          j->desc.n <= kBatchMaxN) {
         small[j->dt].push_back(act[i]);
       } else {
         tasks.push_back([&, i, j] {

@@ -53,6 +53,27 @@ def test_argument_checks_without_gpu(rk):
     assert rk._lib.rk_destroy_problem(None) == rk.RK_ERR_ARG
 
 
+def test_fdm_argument_checks_without_gpu(rk):
+    """The fast-diagonalization preconditioner is accepted only where it is
+    built: CG on the heat operator, low-precision storage, n <= 256 and
+    16-byte rows."""
+    h = ctypes.c_void_p()
+
+    def create(d, s):
+        return rk._lib.rk_create_problem(ctypes.byref(d), ctypes.byref(s), None, ctypes.byref(h))
+
+    heat = rk.problem_desc(n=64)
+    assert create(heat, rk.solver_desc(precond=7)) == rk.RK_ERR_ARG
+    assert "preconditioner" in rk.rk_last_error()
+    assert create(heat, rk.solver_desc(precond="fdm", storage="f64")) == rk.RK_ERR_ARG
+    assert "tensor cores" in rk.rk_last_error()
+    assert create(rk.problem_desc(n=300), rk.solver_desc(precond="fdm")) == rk.RK_ERR_ARG
+    assert create(rk.problem_desc(n=10), rk.solver_desc(precond="fdm")) == rk.RK_ERR_ARG  # 40-byte rows
+    assert create(rk.problem_desc(n=12), rk.solver_desc(precond="fdm", storage="f16")) == rk.RK_ERR_ARG
+    assert "16-byte rows" in rk.rk_last_error()
+    assert create(heat, rk.solver_desc(precond="fdm", krylov=rk.RK_KRYLOV_GMRES)) == rk.RK_ERR_ARG
+
+
 def test_package_tableaux_match_oracle(rk):
     """The library's tableau table and the oracle's are typed independently
     from the paper; they must agree."""
