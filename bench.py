@@ -53,6 +53,9 @@ WORKLOADS = {
     "heat256-4s3pB": dict(n=256, kappa=1.0, tableau="4s3pB", dt=1e-3, bs=8, tol=1e-6, tol64=1e-6, storage="f32"),
     "heat256-f16": dict(n=256, kappa=1.0, tableau="sdirk2", dt=1e-3, bs=8, tol=1e-3, tol64=1e-4, storage="f16"),
     "heat128": dict(n=128, kappa=1.0, tableau="sdirk2", dt=1e-3, bs=8, tol=1e-3, tol64=1e-4, storage="f32"),
+    # the fast-diagonalization preconditioner (tensor-core mode products) in place of block-Jacobi
+    "heat256-fdm": dict(n=256, kappa=1.0, tableau="sdirk2", dt=1e-3, bs=8, tol=1e-3, tol64=1e-4, storage="f32",
+                        precond="fdm"),
 }
 MATCH = 1.05  # matched error: within 5 % of the exact solve's error
 HBM_FALLBACK_GBS = 6400.0
@@ -185,7 +188,7 @@ def oracle_step_seconds(cfg, iters_per_step):
         op = operators.HeatOperator(n, cfg["kappa"])
         tab = tableau.get(cfg["tableau"])
         u0 = synth.heat_modes(seed=0).evaluate(n)
-        solver = dirk.Solver("cg", bs=cfg["bs"], tol_rel=cfg["tol"], max_iter=1)
+        solver = dirk.Solver("cg", bs=cfg["bs"], tol_rel=cfg["tol"], max_iter=1, precond=cfg.get("precond", "bj"))
         shifts = sorted({cfg["dt"] * a for a in np.diag(tab[1]) if a != 0.0})
         for s in shifts:  # preconditioner setup, untimed
             solver.solve(op, s, np.zeros(n ** 3))
@@ -233,6 +236,7 @@ def run_reference(args, cfg):
 def workload_config(name, cfg):
     return {"workload": name, "grid": "%d^3" % cfg["n"], "dof": cfg["n"] ** 3, "kappa": cfg["kappa"],
             "tableau": cfg["tableau"], "dt": cfg["dt"], "krylov": "cg", "bj_block": cfg["bs"],
+            "precond": cfg.get("precond", "bj"), "precond_fp64": "bj",
             "tol_rel": cfg["tol"], "tol_rel_fp64": cfg["tol64"], "storage": cfg["storage"], "arith": "f32",
             "solution": "f32", "high_precision": "f64",
             "u0": "sine mode + 32 random modes (seed 0)", "l2": "working set > L2 (no flush needed)"}
@@ -387,14 +391,14 @@ def main():
     stream = torch.cuda.current_stream()
     sptr = stream.cuda_stream
 
-    def make(storage, tol, correct):
+    def make(storage, tol, correct, precond="bj"):
         return rk.Problem(rk.problem_desc(n=n, kappa=cfg["kappa"]),
                           rk.solver_desc(bj_block=cfg["bs"], tol_rel=tol, storage=storage, correct=correct,
-                                         max_iter=2000),
+                                         max_iter=2000, precond=precond),
                           tableau=tab, u0=u0, stream=sptr)
 
     # ---------------- mixed-precision path, device-resident inputs
-    p = make(cfg["storage"], cfg["tol"], 1)
+    p = make(cfg["storage"], cfg["tol"], 1, cfg.get("precond", "bj"))
     rk.rk_integrate(p.h, dt, args.warmup)
     rk.rk_profile(p.h, True)
     clocks = ClockSampler(local)

@@ -41,17 +41,17 @@ def line_operator(n: int, kappa: float, s: float) -> np.ndarray:
 
 def _t_r(Q, x3):
     """T_R: contract the x index (fastest; x3 is indexed [k, j, i])."""
-    return np.einsum("iq,kjq->kji", Q, x3)
+    return np.einsum("iq,kjq->kji", Q, x3, optimize=True)
 
 
 def _t_m(Q, x3):
     """T_M: contract the y index."""
-    return np.einsum("jq,kqi->kji", Q, x3)
+    return np.einsum("jq,kqi->kji", Q, x3, optimize=True)
 
 
 def _t_l(Q, x3):
     """T_L: contract the z index."""
-    return np.einsum("kq,qji->kji", Q, x3)
+    return np.einsum("kq,qji->kji", Q, x3, optimize=True)
 
 
 class FastDiagonalization:
