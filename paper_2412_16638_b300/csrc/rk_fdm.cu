@@ -4,6 +4,7 @@
 #include <cmath>
 #include <mutex>
 
+#include "rk_fdm.cuh"
 #include "rk_internal.h"
 
 namespace rk {
@@ -150,7 +151,8 @@ rk_status apply_typed(rk_problem* p, double shift, bool cg, int solve, int idx) 
   } const passes[6] = {{&f.in_r, t, kFdmPlain}, {&f.in_t, z, kFdmPlain}, {&f.in_z, t, kFdmScale},
                        {&f.in_t, z, kFdmPlain}, {&f.in_z, t, kFdmPlain}, {&f.in_t, z, cg ? kFdmDot : kFdmPlain}};
   for (const Pass& ps : passes) {
-    prof_begin(p, K_FDM, (ps.mode == kFdmDot ? 3.0 : 2.0) * Ns, cg ? solve : -1, cg ? idx : -1);
+    const int kid = ps.mode == kFdmDot ? K_FDM_DOT : (ps.mode == kFdmScale ? K_FDM_SCALE : K_FDM);
+    prof_begin(p, kid, (ps.mode == kFdmDot ? 3.0 : 2.0) * Ns, cg ? solve : -1, cg ? idx : -1);
     fdm_pass<S><<<f.grid, kFdmThreads, f.smem, p->st>>>(*ps.in, f.qmap, g, ps.mode, c, f.mu, ps.out, r, cg ? 1 : 0,
                                                          p->sc, p->partials);
     prof_end(p);

@@ -22,8 +22,9 @@
 // loads (the CTA's N tile of Q once, then 128 x 128-byte K blocks of X into a
 // ring of stages); warp 1 owns the tensor memory and issues tcgen05.mma with
 // the accumulator in TMEM (two accumulators, so the epilogue of one tile
-// overlaps the MMAs of the next); warps 2-5 read the accumulator with
-// tcgen05.ld and store.  Every mbarrier wait is bounded; a wait that runs out
+// overlaps the MMAs of the next); warps 2-9 read the accumulator with
+// tcgen05.ld and store (two warps per TMEM lane quadrant, alternating
+// 16-column chunks, so the stores of one hide the latency of the other).  Every mbarrier wait is bounded; a wait that runs out
 // sets a shared flag that stops the other roles, the CTA lets its copies and
 // MMAs land, frees its tensor memory and reports status 6.
 //
@@ -35,25 +36,18 @@
 #include <type_traits>
 
 #include "rk_device.cuh"
+#include "rk_fdm_geo.h"
 #include "rk_heat.cuh"
 #include "rk_tiled.cuh"
 
 namespace rk {
 
 constexpr int kFdmStages = 4;      // K-block stages of X
-constexpr int kFdmThreads = 192;   // 6 warps
+constexpr int kFdmEpiWarps = 8;    // epilogue warps: two per TMEM lane quadrant
+constexpr int kFdmThreads = 32 * (2 + kFdmEpiWarps);
 constexpr int kFdmRows = 128;      // rows per tile (TMEM lanes)
 constexpr int kFdmTmemCols = 256;  // two FP32 accumulators of up to 128 columns
 constexpr uint32_t kFdmStageBytes = kFdmRows * 128;
-
-struct FdmGeo {
-  int n;        // nodes per direction
-  int rows;     // n*n
-  int nt;       // columns per N tile: multiple of 16, <= 128
-  int ntiles;   // N tiles (1 or 2); the grid is a multiple of ntiles
-  int kblocks;  // 128-byte K blocks: ceil(n * sizeof(S) / 128)
-  int mtiles;   // ceil(rows / 128)
-};
 
 enum FdmMode { kFdmPlain = 0, kFdmScale = 1, kFdmDot = 2 };
 
@@ -183,8 +177,8 @@ __global__ void __launch_bounds__(kFdmThreads, 1)
     mbar_init(qfull, 1);
     mbar_init(&accfull[0], 1);
     mbar_init(&accfull[1], 1);
-    mbar_init(&accempty[0], 4 * 32);
-    mbar_init(&accempty[1], 4 * 32);
+    mbar_init(&accempty[0], kFdmEpiWarps * 32);
+    mbar_init(&accempty[1], kFdmEpiWarps * 32);
     mbar_init(mmadone, 1);
     *fail = 0;
     mbar_fence_init();
@@ -260,9 +254,12 @@ __global__ void __launch_bounds__(kFdmThreads, 1)
       (void)mbar_wait(mmadone, 0);
     }
   } else {
-    // ---- epilogue: warps 2..5 own TMEM lane quadrants (warp % 4)
+    // ---- epilogue: warp w owns TMEM lane quadrant w % 4 (the hardware
+    // restriction) and every second 16-column chunk, starting at (w - 2) / 4
     const int quad = warp & 3;
+    const int half = (warp - 2) >> 2;
     const int row = quad * 32 + lane;
+    float dacc[4] = {0.f, 0.f, 0.f, 0.f};
     uint32_t lt = 0;
     for (int t = blockIdx.x; t < total; t += gridDim.x, ++lt) {
       const uint32_t acc = lt & 1u;
@@ -271,10 +268,18 @@ __global__ void __launch_bounds__(kFdmThreads, 1)
       tc_fence_after();
       const int m = (t / fg.ntiles) * kFdmRows + row;
       const bool mrow = m < fg.rows;
-      float mab = 0.f;
-      if (mode == kFdmScale && mrow) mab = mu[m / fg.n] + mu[m % fg.n];
+      float cab = 0.f;
+      if (mode == kFdmScale && mrow) cab = fmaf(c, mu[m / fg.n] + mu[m % fg.n], 1.0f);
       const int j0 = ntile * fg.nt;
-      for (int c0 = 0; c0 < fg.nt; c0 += 16) {
+      for (int c0 = 16 * half; c0 < fg.nt; c0 += 32) {
+        float rv[16];
+        if (mode == kFdmDot) {  // r loads in flight during the TMEM read
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj) {
+            const int j = j0 + c0 + jj;
+            rv[jj] = (mrow && j < fg.n) ? wid<float>(rdot[(size_t)j * fg.rows + m]) : 0.f;
+          }
+        }
         float v[16];
         tmem_ld16(tbase + ((uint32_t)(quad * 32) << 16) + acc * 128u + (uint32_t)c0, v);
 #pragma unroll
@@ -282,17 +287,18 @@ __global__ void __launch_bounds__(kFdmThreads, 1)
           const int j = j0 + c0 + jj;
           if (mrow && j < fg.n) {
             float y = v[jj];
-            if (mode == kFdmScale) y = y / fmaf(c, mab + mu[j], 1.0f);
+            // P_D >= 1: the fast division's 2-ulp error is far below TF32/FP16 rounding
+            if (mode == kFdmScale) y = __fdividef(y, fmaf(c, mu[j], cab));
             const S ys = nar<S>(y);
-            const size_t o = (size_t)j * fg.rows + m;
-            out[o] = ys;
-            if (mode == kFdmDot) dot = fmaf(wid<float>(rdot[o]), wid<float>(ys), dot);
+            out[(size_t)j * fg.rows + m] = ys;
+            if (mode == kFdmDot) dacc[jj & 3] = fmaf(rv[jj], wid<float>(ys), dacc[jj & 3]);
           }
         }
       }
       tc_fence_before();
       mbar_arrive(&accempty[acc]);
     }
+    dot = (dacc[0] + dacc[1]) + (dacc[2] + dacc[3]);
   }
   __syncthreads();
   if (warp == 1) {

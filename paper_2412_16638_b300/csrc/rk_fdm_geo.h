@@ -1,0 +1,16 @@
+// Launch geometry of the fast-diagonalization passes (shared by the kernel
+// and the host code that sets it up).
+#pragma once
+
+namespace rk {
+
+struct FdmGeo {
+  int n;        // nodes per direction
+  int rows;     // n*n
+  int nt;       // columns per N tile: multiple of 16, <= 128
+  int ntiles;   // N tiles (1 or 2); the grid is a multiple of ntiles
+  int kblocks;  // 128-byte K blocks: ceil(n * sizeof(S) / 128)
+  int mtiles;   // ceil(rows / 128)
+};
+
+}  // namespace rk
