@@ -19,11 +19,12 @@ on the lexicographic vector x_{i + j n + k n^2} (Sec. 4):
     (T_L x)_{ijk} = sum_q Q_{kq} x_{ijq}.
 
 For the constant-coefficient heat stage system (I - s L) k = g with
-L = kappa/h^2 (7-point Laplacian) the splitting is exact: A = B = C =
-I/3 + (s kappa/h^2) K1D with K1D = tridiag(-1, 2, -1) (Sec. 5.2.1), so P is
-the system matrix itself and preconditioned CG converges in one iteration
-in exact arithmetic.  The one-dimensional decomposition is taken from LAPACK
-(numpy.linalg.eigh); the tests pin it to the closed-form sine eigenpairs.
+L = kappa/h^2 (7-point Laplacian) the splitting is exact with the settings of
+Sec. 5.2.1: A = I + (s kappa/h^2) K1D and B = C = (s kappa/h^2) K1D,
+K1D = tridiag(-1, 2, -1), so P is the system matrix itself and
+preconditioned CG converges in one iteration in exact arithmetic.  The
+one-dimensional decompositions are taken from LAPACK (numpy.linalg.eigh);
+the tests pin them to the closed-form sine eigenpairs.
 """
 from __future__ import annotations
 
@@ -32,11 +33,12 @@ import numpy as np
 from .operators import grid_h
 
 
-def line_operator(n: int, kappa: float, s: float) -> np.ndarray:
-    """The one-dimensional factor I/3 + (s kappa / h^2) tridiag(-1, 2, -1)."""
+def line_operators(n: int, kappa: float, s: float):
+    """The one-dimensional factors (A, B = C) of Sec. 5.2.1:
+    A = I + (s kappa / h^2) K1D (x), B = C = (s kappa / h^2) K1D (y, z)."""
     c = s * kappa / grid_h(n) ** 2
     K = 2.0 * np.eye(n) - np.eye(n, k=1) - np.eye(n, k=-1)
-    return np.eye(n) / 3.0 + c * K
+    return np.eye(n) + c * K, c * K
 
 
 def _t_r(Q, x3):
@@ -59,24 +61,23 @@ class FastDiagonalization:
 
     def __init__(self, n: int, kappa: float, s: float):
         self.n = n
-        A = line_operator(n, kappa, s)
-        lam, Q = np.linalg.eigh(A)  # A = Q diag(lam) Q^T, Q orthogonal
-        self.Q = Q
-        self.lam = lam
+        A, B = line_operators(n, kappa, s)
+        self.lam_a, self.Qa = np.linalg.eigh(A)  # A = Q_A diag(lam_a) Q_A^T, Q_A orthogonal
+        self.lam_b, self.Qb = np.linalg.eigh(B)  # B = C
         # P_D = I (x) I (x) Lambda_A + I (x) Lambda_B (x) I + Lambda_C (x) I (x) I,
         # indexed [k, j, i]
-        self.pd = lam[:, None, None] + lam[None, :, None] + lam[None, None, :]
+        self.pd = self.lam_b[:, None, None] + self.lam_b[None, :, None] + self.lam_a[None, None, :]
 
     def apply(self, r):
-        n, Q = self.n, self.Q
-        Qi = Q.T  # Q^-1 of an orthogonal matrix
+        n, Qa, Qb = self.n, self.Qa, self.Qb
         x = np.asarray(r, dtype=np.float64).reshape(n, n, n)
-        # (Q_C^-1 (x) Q_B^-1 (x) Q_A^-1) = T_L^-1 T_M^-1 T_R^-1 applied right to left
-        x = _t_r(Qi, x)
-        x = _t_m(Qi, x)
-        x = _t_l(Qi, x)
+        # (Q_C^-1 (x) Q_B^-1 (x) Q_A^-1) = T_L^-1 T_M^-1 T_R^-1, applied right to
+        # left; Q^-1 = Q^T for the orthogonal eigenvector matrices
+        x = _t_r(Qa.T, x)
+        x = _t_m(Qb.T, x)
+        x = _t_l(Qb.T, x)
         x = x / self.pd
-        x = _t_r(Q, x)
-        x = _t_m(Q, x)
-        x = _t_l(Q, x)
+        x = _t_r(Qa, x)
+        x = _t_m(Qb, x)
+        x = _t_l(Qb, x)
         return x.reshape(-1)

@@ -25,12 +25,14 @@ def test_line_eigenpairs_are_the_sine_basis():
     P = fdm.FastDiagonalization(n, kappa, s)
     c = s * kappa * (n + 1) ** 2
     mu = np.array([4.0 * math.sin(k * math.pi / (2 * (n + 1))) ** 2 for k in range(1, n + 1)])
-    assert np.allclose(P.lam, 1.0 / 3.0 + c * mu, rtol=1e-13, atol=0)
+    assert np.allclose(P.lam_a, 1.0 + c * mu, rtol=1e-13, atol=0)
+    assert np.allclose(P.lam_b, c * mu, rtol=1e-12, atol=0)
     j = np.arange(1, n + 1)
     S = math.sqrt(2.0 / (n + 1)) * np.sin(np.outer(j, j) * math.pi / (n + 1))
     # eigenvectors agree up to sign
-    dots = np.abs(np.sum(S * P.Q, axis=0))
-    assert np.allclose(dots, 1.0, atol=1e-12)
+    for Q in (P.Qa, P.Qb):
+        dots = np.abs(np.sum(S * Q, axis=0))
+        assert np.allclose(dots, 1.0, atol=1e-12)
 
 
 def test_pd_holds_the_3d_eigenvalues():
@@ -102,7 +104,7 @@ def test_planted_mistake_in_pd_is_caught():
     # a dropped direction in P_D breaks the inverse
     n, kappa, s = 6, 1.0, 1e-2
     P = fdm.FastDiagonalization(n, kappa, s)
-    P.pd = P.lam[None, :, None] + P.lam[None, None, :] + 1.0 / 3.0
+    P.pd = P.lam_b[None, :, None] + P.lam_a[None, None, :]  # the z direction dropped
     v = rand_vec(n ** 3, 5)
     w = P.apply(v)
     back = w - s * operators.heat_apply(w, n, kappa)
