@@ -58,6 +58,13 @@ WORKLOADS = {
                         precond="fdm"),
 }
 MATCH = 1.05  # matched error: within 5 % of the exact solve's error
+# FP64-pipe instructions per DOF of the heat FP64 kernels (counted from the
+# source: heat_apply_f64 = 5 DADD neighbour sum + DMUL + DFMA + DFMA and DMNMX
+# for the norms) and the FP64 peak in lane-operations per second: the nominal
+# 1.25 TFLOP/s of the part is 2 FP64 FMA lanes per SM per clock, x 148 SMs x
+# 2.032 GHz (maximum SM clock).
+FP64_ALU = {"op_apply_f64": 9, "correct_f64": 7}
+FP64_PEAK_GINSTR = 2 * 148 * 2.032
 HBM_FALLBACK_GBS = 6400.0
 
 
@@ -72,14 +79,14 @@ def measured_peaks():
 
 def ncu_traffic(kernel, workload):
     """Per-launch DRAM bytes of `kernel` from the committed ncu summary, or None
-    when there is none or the kernel source changed since it was taken."""
+    when there is none or the kernel sources changed since it was taken."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)[workload]
         h = hashlib.sha256()
-        for name in ("rk_heat.cuh", "rk_tiled.cuh"):
+        for name in d.get("sources", ("rk_heat.cuh", "rk_tiled.cuh")):
             with open(os.path.join(ROOT, "paper_2412_16638_b300", "csrc", name), "rb") as f:
                 h.update(f.read())
         sha = h.hexdigest()[:16]
@@ -343,6 +350,8 @@ def main():
     ap.add_argument("--workload", default="heat256", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
+    ap.add_argument("--no-fdm", action="store_true",
+                    help="skip the fast-diagonalization variant of a block-Jacobi workload")
     ap.add_argument("--bs", type=int, default=0, help="override the block-Jacobi block size")
     ap.add_argument("--tol", type=float, default=0.0, help="override the solver tolerance")
     ap.add_argument("--batch", action="store_true", help="run the 512-problem batched workload instead")
@@ -442,9 +451,10 @@ def main():
     e2e_value = world * N * k_e2e / e2e_secs
     p.close()
 
-    # ---------------- roofline of the dominant kernel
+    # ---------------- roofline of the dominant HBM-bound kernel; the FP64
+    # stencil kernels are bound by the FP64 pipe and reported apart
     peak, peak_kind = measured_peaks()
-    dom = max(prof.items(), key=lambda kv: kv[1]["ms_total"])
+    dom = max(((k, v) for k, v in prof.items() if k not in FP64_ALU), key=lambda kv: kv[1]["ms_total"])
     dname, d = dom
     achieved = d["bytes_total"] / (d["ms_total"] / 1e3) / 1e9
     kernels = {k: {"launches": v["launches"], "noop_launches": v["noop_launches"],
@@ -459,6 +469,14 @@ def main():
                 "traffic": traffic,
                 "bytes_per_launch": d["bytes_total"] / max(d["launches"], 1),
                 "avg_launch_us": 1e3 * d["ms_total"] / max(d["launches"], 1)}
+    fp64_alu = None
+    if "op_apply_f64" in prof:
+        a = prof["op_apply_f64"]
+        rate = FP64_ALU["op_apply_f64"] * N * a["launches"] / (a["ms_total"] / 1e3) / 1e9
+        fp64_alu = {"bound": "alu", "kernel": "op_apply_f64", "fp64_instr_per_dof": FP64_ALU["op_apply_f64"],
+                    "achieved": round(rate, 1), "peak": FP64_PEAK_GINSTR, "unit": "G FP64 instr/s",
+                    "frac": round(rate / FP64_PEAK_GINSTR, 4),
+                    "share": round(a["ms_total"] / sum(x["ms_total"] for x in prof.values()), 4)}
 
     # ---------------- plain FP64 DIRK step of the same problem
     fp64 = None
@@ -479,6 +497,35 @@ def main():
         fp64 = {"value": N * k64 / sec64, "ms_per_step": 1e3 * sec64 / k64, "steps": k64,
                 "iters_per_step": s64.iters_total / k64, "tol_rel": cfg["tol64"], "err_vs_discrete": rel(u64, d64),
                 "err_vs_continuous": rel(u64, c64)}
+
+    # ---------------- the same workload with the fast-diagonalization preconditioner
+    fdm_line = None
+    if cfg.get("precond", "bj") == "bj" and cfg["storage"] != "f64" and n <= 256 and not args.no_fdm:
+        f = make(cfg["storage"], cfg["tol"], 1, "fdm")
+        rk.rk_integrate(f.h, dt, args.warmup)
+        rk.rk_profile(f.h, True)
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        sf = rk.rk_integrate(f.h, dt, args.steps)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        fprof, flaunch = rk.rk_profile_read(f.h)
+        secf = g0.elapsed_time(g1) / 1e3
+        uf = f.state()
+        f.close()
+        fk = {k: v for k, v in fprof.items() if k.startswith("fdm_pass")}
+        fms = sum(v["ms_total"] for v in fk.values())
+        fbytes = sum(v["bytes_total"] for v in fk.values())
+        fn = sum(v["launches"] for v in fk.values())
+        fdm_line = {"value": world * N * args.steps / secf, "ms_per_step": 1e3 * secf / args.steps,
+                    "iters_per_step": sf.iters_total / args.steps, "tol_rel": cfg["tol"],
+                    "err_vs_discrete": rel(uf, disc), "err_vs_continuous": rel(uf, cont),
+                    "matched_ratio": rel(uf, cont) / rel(disc, cont), "gpu_launches": flaunch,
+                    "fdm_pass": {"launches": fn, "avg_us": 1e3 * fms / max(fn, 1),
+                                 "GBps": fbytes / max(fms, 1e-9) / 1e6,
+                                 "frac_hbm": fbytes / max(fms, 1e-9) / 1e6 / peak},
+                    "share_fdm_pass": fms / sum(v["ms_total"] for v in fprof.values())}
 
     # ---------------- matched error: both paths within MATCH x the error of an
     # exact solve (the fully discrete solution) against the exact solution
@@ -503,6 +550,7 @@ def main():
                     "d2h_bytes_per_step": 8 * N, "steps": k_e2e},
             "gpu_launches": launches,
             "roofline": roofline,
+            "fp64_alu": fp64_alu,
             "cpu_baseline": cpu,
             "clocks": clk,
             "iters_per_step": iters_per_step,
@@ -512,6 +560,8 @@ def main():
             "matched_error": matched,
             "fp64_plain": fp64,
             "speedup_vs_fp64": (value / world / fp64["value"]) if fp64 else None,
+            "fdm": (dict(fdm_line, speedup_vs_fp64=(fdm_line["value"] / world / fp64["value"]) if fp64 else None)
+                    if fdm_line else None),
             "kernels": kernels,
         }
         print(json.dumps(line))

@@ -37,10 +37,22 @@ S host_round(double v) {
     return __double2bfloat16(v);
 }
 
+// Largest dynamic shared memory a block of fdm_pass<S> may use on this
+// device: the opt-in limit minus the kernel's static shared memory.
 template <typename S>
-constexpr size_t fdm_smem_max() {
-  // n = 256: two N tiles of 128 columns, 256 * sizeof(S) / 128 K blocks
-  return fdm_smem_bytes(128, 256 * (int)sizeof(S) / 128);
+int smem_dynamic_max() {
+  static int v = 0;
+  if (v == 0) {
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa{};
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || optin <= 0)
+      optin = 227 * 1024;
+    if (cudaFuncGetAttributes(&fa, (const void*)fdm_pass<S>) != cudaSuccess) fa.sharedSizeBytes = 4096;
+    cudaGetLastError();
+    v = optin - (int)fa.sharedSizeBytes;
+  }
+  return v;
 }
 
 template <typename S>
@@ -63,8 +75,15 @@ rk_status setup_typed(rk_problem* p) {
   g.nt = ((n + g.ntiles - 1) / g.ntiles + 15) / 16 * 16;
   g.kblocks = (int)((n * sizeof(S) + 127) / 128);
   g.mtiles = (g.rows + kFdmRows - 1) / kFdmRows;
+  const size_t budget = (size_t)smem_dynamic_max<S>();
+  const size_t fixed = fdm_smem_bytes(g.nt, g.kblocks, 0);
+  g.stages = budget > fixed ? (int)std::min<size_t>(kFdmMaxStages, (budget - fixed) / kFdmStageBytes) : 0;
+  if (g.stages < 2) {
+    set_error("fast diagonalization: shared memory too small for n = %d", n);
+    return RK_ERR_ARG;
+  }
   f.geo = g;
-  f.smem = fdm_smem_bytes(g.nt, g.kblocks);
+  f.smem = fdm_smem_bytes(g.nt, g.kblocks, g.stages);
 
   // Q_jk = sqrt(2/(n+1)) sin((j+1)(k+1) pi/(n+1)); mu_k = 4 sin^2((k+1) pi/(2(n+1)))
   std::vector<S> qh((size_t)n * n);
@@ -119,7 +138,7 @@ rk_status setup_typed(rk_problem* p) {
   static cudaError_t attr = cudaSuccess;
   std::call_once(once, [] {
     attr = cudaFuncSetAttribute((const void*)fdm_pass<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)fdm_smem_max<S>());
+                                smem_dynamic_max<S>());
     cudaGetLastError();
   });
   if (attr != cudaSuccess) {

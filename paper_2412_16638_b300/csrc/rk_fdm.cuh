@@ -24,7 +24,11 @@
 // the accumulator in TMEM (two accumulators, so the epilogue of one tile
 // overlaps the MMAs of the next); warps 2-9 read the accumulator with
 // tcgen05.ld and store (two warps per TMEM lane quadrant, alternating
-// 16-column chunks, so the stores of one hide the latency of the other).  Every mbarrier wait is bounded; a wait that runs out
+// 16-column chunks, so the stores of one hide the latency of the other).
+// The ring holds as many 16 KB X stages as shared memory allows beside the
+// Q tile, up to 6 (measured: 4 and 6 stages give the same time at n = 256;
+// the two CTAs that share an X tile for the two N halves read it from L2
+// twice, and that L2 traffic, not the ring depth, bounds the pass).  Every mbarrier wait is bounded; a wait that runs out
 // sets a shared flag that stops the other roles, the CTA lets its copies and
 // MMAs land, frees its tensor memory and reports status 6.
 //
@@ -42,7 +46,7 @@
 
 namespace rk {
 
-constexpr int kFdmStages = 4;      // K-block stages of X
+constexpr int kFdmMaxStages = 6;  // K-block stages of X (ring depth set per problem)
 constexpr int kFdmEpiWarps = 8;    // epilogue warps: two per TMEM lane quadrant
 constexpr int kFdmThreads = 32 * (2 + kFdmEpiWarps);
 constexpr int kFdmRows = 128;      // rows per tile (TMEM lanes)
@@ -52,8 +56,8 @@ constexpr uint32_t kFdmStageBytes = kFdmRows * 128;
 enum FdmMode { kFdmPlain = 0, kFdmScale = 1, kFdmDot = 2 };
 
 // Dynamic shared memory: 1 KB alignment slack, Q tile, X stages, barriers.
-__host__ __device__ constexpr size_t fdm_smem_bytes(int nt, int kblocks) {
-  return 1024 + (size_t)kblocks * nt * 128 + (size_t)kFdmStages * kFdmStageBytes + 256;
+__host__ __device__ constexpr size_t fdm_smem_bytes(int nt, int kblocks, int stages) {
+  return 1024 + (size_t)kblocks * nt * 128 + (size_t)stages * kFdmStageBytes + 512;
 }
 
 // ---------------------------------------------------------------- PTX wrappers
@@ -154,10 +158,11 @@ __global__ void __launch_bounds__(kFdmThreads, 1)
   const uint32_t qbytes = (uint32_t)fg.kblocks * fg.nt * 128;
   unsigned char* sQ = sm;
   unsigned char* sX = sm + qbytes;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sX + (size_t)kFdmStages * kFdmStageBytes);
-  uint64_t* full = bars;                    // [kFdmStages] X stage landed
-  uint64_t* empty = bars + kFdmStages;      // [kFdmStages] X stage consumed by the MMAs
-  uint64_t* qfull = bars + 2 * kFdmStages;  // Q tile landed
+  const int NS = fg.stages;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sX + (size_t)NS * kFdmStageBytes);
+  uint64_t* full = bars;                       // [NS] X stage landed
+  uint64_t* empty = bars + kFdmMaxStages;      // [NS] X stage consumed by the MMAs
+  uint64_t* qfull = bars + 2 * kFdmMaxStages;  // Q tile landed
   uint64_t* accfull = qfull + 1;            // [2] accumulator ready
   uint64_t* accempty = qfull + 3;           // [2] accumulator drained
   uint64_t* mmadone = qfull + 5;            // every MMA of the CTA finished
@@ -170,7 +175,7 @@ __global__ void __launch_bounds__(kFdmThreads, 1)
   constexpr int KB = 128 / (int)sizeof(S);  // elements per 128-byte K block
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kFdmStages; ++s) {
+    for (int s = 0; s < NS; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
@@ -206,8 +211,8 @@ __global__ void __launch_bounds__(kFdmThreads, 1)
       for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
         const int mt = t / fg.ntiles;
         for (int kb = 0; kb < fg.kblocks; ++kb, ++it) {
-          const int s = (int)(it % kFdmStages);
-          if (!fdm_wait(&empty[s], ((it / kFdmStages) & 1u) ^ 1u, fail)) {
+          const int s = (int)(it % NS);
+          if (!fdm_wait(&empty[s], ((it / NS) & 1u) ^ 1u, fail)) {
             ok = false;
             break;
           }
@@ -217,8 +222,8 @@ __global__ void __launch_bounds__(kFdmThreads, 1)
       }
       // every copy issued must land before the CTA exits
       (void)mbar_wait(qfull, 0);
-      const uint32_t first = it > (uint32_t)kFdmStages ? it - kFdmStages : 0u;
-      for (uint32_t j = first; j < it; ++j) (void)mbar_wait(&full[j % kFdmStages], (j / kFdmStages) & 1u);
+      const uint32_t first = it > (uint32_t)NS ? it - NS : 0u;
+      for (uint32_t j = first; j < it; ++j) (void)mbar_wait(&full[j % NS], (j / NS) & 1u);
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -234,8 +239,8 @@ __global__ void __launch_bounds__(kFdmThreads, 1)
         tc_fence_after();
         const uint32_t d = tbase + acc * 128u;
         for (int kb = 0; kb < fg.kblocks; ++kb, ++it) {
-          const int s = (int)(it % kFdmStages);
-          if (!fdm_wait(&full[s], (it / kFdmStages) & 1u, fail)) {
+          const int s = (int)(it % NS);
+          if (!fdm_wait(&full[s], (it / NS) & 1u, fail)) {
             ok = false;
             break;
           }

@@ -11,6 +11,7 @@ struct FdmGeo {
   int ntiles;   // N tiles (1 or 2); the grid is a multiple of ntiles
   int kblocks;  // 128-byte K blocks: ceil(n * sizeof(S) / 128)
   int mtiles;   // ceil(rows / 128)
+  int stages;   // X stages in the TMA ring (as many as shared memory holds, <= 6)
 };
 
 }  // namespace rk
