@@ -1,6 +1,7 @@
 """The perturbed (mixed-precision) DIRK step, evaluated entirely in float64.
 
-For du/dt = L u and a tableau split A = A_hi + A_lo (Sec. 2.2), stage i is
+For du/dt = f(u) = L u (+ a fixed forcing vector, the heat test of Sec. 5.2.1)
+and a tableau split A = A_hi + A_lo (Sec. 2.2), stage i is
 
     y_i = u_n + tau sum_{j<i} (a^h_ij f(y_j) + a^eps_ij f^eps(y_j))
               + tau a^eps_ii f^eps(y_i)                      (Eqs. mpAstep1-4)
@@ -53,8 +54,9 @@ class Solver:
         return krylov.gmres(apply_A, apply_M, g, self.restart, self.tol_rel, self.tol_abs, self.max_iter)
 
 
-def rk_step(u, dt, tableau, op, solver: Solver, corrected=True, stats=None):
-    """One step u_n -> u_{n+1} of the split tableau (A_hi, A_lo, b)."""
+def rk_step(u, dt, tableau, op, solver: Solver, corrected=True, stats=None, source=None):
+    """One step u_n -> u_{n+1} of the split tableau (A_hi, A_lo, b) for
+    du/dt = L u + source (source: a fixed forcing vector or None)."""
     A_hi, A_lo, b = tableau
     q = len(b)
     u = np.asarray(u, dtype=np.float64)
@@ -68,18 +70,20 @@ def rk_step(u, dt, tableau, op, solver: Solver, corrected=True, stats=None):
             if A_lo[i, j] != 0.0:
                 r += dt * A_lo[i, j] * ke[j]
         a = A_lo[i, i]
+        f = (lambda y: op.apply(y)) if source is None else (lambda y: op.apply(y) + source)
         if a != 0.0:
-            g = op.apply(r)
+            # stage derivative k = f(y), y = r + dt a k:  (I - dt a L) k = f(r)
+            g = f(r)
             res = solver.solve(op, dt * a, g)
             if stats is not None:
                 stats.append((res.iters, res.converged))
             ke[i] = res.x
             if corrected:
-                k[i] = op.apply(r + dt * a * ke[i])
+                k[i] = f(r + dt * a * ke[i])
             else:
                 k[i] = ke[i]
         else:
-            k[i] = op.apply(r)
+            k[i] = f(r)
             ke[i] = k[i]
     out = u.copy()
     for j in range(q):
@@ -88,8 +92,8 @@ def rk_step(u, dt, tableau, op, solver: Solver, corrected=True, stats=None):
     return out
 
 
-def integrate(u0, dt, nsteps, tableau, op, solver: Solver, corrected=True, stats=None):
+def integrate(u0, dt, nsteps, tableau, op, solver: Solver, corrected=True, stats=None, source=None):
     u = np.asarray(u0, dtype=np.float64).copy()
     for _ in range(nsteps):
-        u = rk_step(u, dt, tableau, op, solver, corrected, stats)
+        u = rk_step(u, dt, tableau, op, solver, corrected, stats, source)
     return u

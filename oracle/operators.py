@@ -1,9 +1,10 @@
 """Semi-discrete operators L of du/dt = L u on the unit cube (Sec. 3; Sec. 5.2).
 
 Unknowns live on the n^3 interior nodes x_i = (i+1) h, h = 1/(n+1), with
-homogeneous Dirichlet values on the boundary, numbered lexicographically
-u[i + j n + k n^2] (the numbering of Sec. 4.2).  In numpy a field is viewed
-as an (n, n, n) array indexed [k, j, i].
+homogeneous Dirichlet values on the boundary (heat, advection-diffusion), or
+on the periodic grid x_i = i h, h = 1/n (periodic advection), numbered
+lexicographically u[i + j n + k n^2] (the numbering of Sec. 4.2).  In numpy a
+field is viewed as an (n, n, n) array indexed [k, j, i].
 """
 from __future__ import annotations
 
@@ -83,6 +84,25 @@ def advdiff_csr(n: int, kappa: np.ndarray, vel=(1.0, 0.5, 0.25)) -> sp.csr_matri
     A.sum_duplicates()
     A.sort_indices()
     return A
+
+
+def adv_periodic_csr(n: int, beta=(1.0, 1.0, 1.0)) -> sp.csr_matrix:
+    """CSR matrix of L u = -div(beta u) = -sum_d beta_d D_d u for constant beta
+    on the periodic grid x_i = i h, h = 1/n (the advection test of Sec. 5.2.2):
+    D_d is the second-order central difference (u(x + h e_d) - u(x - h e_d)) /
+    (2h), i.e. the 1-D matrix Tridiag(-1, 0, 1) + K^(B) / (2h) with the periodic
+    corner entries K^(B).  Written as a sum of Kronecker products."""
+    h = 1.0 / n
+    K = np.zeros((n, n))
+    for i in range(n):
+        K[i, (i + 1) % n] += 1.0
+        K[i, (i - 1) % n] -= 1.0
+    D = sp.csr_matrix(K / (2.0 * h))
+    I = sp.identity(n, format="csr")
+    Dx = sp.kron(I, sp.kron(I, D))
+    Dy = sp.kron(I, sp.kron(D, I))
+    Dz = sp.kron(D, sp.kron(I, I))
+    return (-(beta[0] * Dx + beta[1] * Dy + beta[2] * Dz)).tocsr()
 
 
 def heat_csr(n: int, kappa: float) -> sp.csr_matrix:

@@ -139,6 +139,26 @@ def gaussian_bump(n: int, width: float = 100.0) -> np.ndarray:
     return np.exp(-width * ((x - 0.5) ** 2 + (y - 0.5) ** 2 + (z - 0.5) ** 2)).ravel()
 
 
+def periodic_coords(n: int):
+    """Node coordinates x_i = i h, h = 1/n, of the periodic grid (the
+    advection test), as (n,n,n) arrays indexed [k, j, i]."""
+    t = np.arange(n, dtype=np.float64) / n
+    z, y, x = np.meshgrid(t, t, t, indexing="ij")
+    return x, y, z
+
+
+def gaussian_bump_periodic(n: int, width: float = 100.0) -> np.ndarray:
+    """exp(-width |x - 1/2|^2) on the periodic grid (flat)."""
+    x, y, z = periodic_coords(n)
+    return np.exp(-width * ((x - 0.5) ** 2 + (y - 0.5) ** 2 + (z - 0.5) ** 2)).ravel()
+
+
+def plane_wave_periodic(n: int, k=(1, 1, 1)) -> np.ndarray:
+    """cos(2 pi (k . x)) on the periodic grid (flat)."""
+    x, y, z = periodic_coords(n)
+    return np.cos(2.0 * math.pi * (k[0] * x + k[1] * y + k[2] * z)).ravel()
+
+
 @dataclass
 class BatchProblem:
     n: int

@@ -56,3 +56,38 @@ def rel_l2(a, b):
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def forced_sine_after(n, kappa, dt, nsteps, A, b, u0_amp=0.0):
+    """du/dt = L u + phi with phi the (1,1,1) sine mode and u0 = u0_amp phi:
+    the RK step maps the deviation from the fixed point u* = -phi / lambda_1
+    by R(dt lambda_1), so u_N = u* + R^N (u0 - u*) exactly (fully discrete).
+    Returns (u_N, semi-discrete exact solution at t = N dt)."""
+    from synth import sine_mode
+    lam = sine_eigenvalue(n, kappa, 1, 1, 1)
+    R = complex(R_scalar(A, b, dt * lam)).real
+    ustar = -1.0 / lam
+    phi = sine_mode(n)
+    disc = (ustar + R ** nsteps * (u0_amp - ustar)) * phi
+    cont = (ustar + math.exp(lam * dt * nsteps) * (u0_amp - ustar)) * phi
+    return disc, cont
+
+
+def periodic_wave_eigenvalue(n, beta, k):
+    """Eigenvalue of L = -sum_d beta_d D_d (central, periodic, h = 1/n) for the
+    Fourier mode exp(2 pi i k . x): -i sum_d beta_d sin(2 pi k_d h) / h."""
+    h = 1.0 / n
+    return -1j * sum(bd * math.sin(2.0 * math.pi * kd * h) / h for bd, kd in zip(beta, k))
+
+
+def plane_wave_after(n, beta, k, dt, nsteps, A, b):
+    """u0 = cos(2 pi k . x) on the periodic grid: u_N = Re(R(dt lam)^N e^{i theta})
+    (fully discrete), and Re(e^{lam t} e^{i theta}) (semi-discrete)."""
+    from synth import periodic_coords
+    x, y, z = periodic_coords(n)
+    theta = (2.0 * math.pi * (k[0] * x + k[1] * y + k[2] * z)).ravel()
+    lam = periodic_wave_eigenvalue(n, beta, k)
+    R = complex(R_scalar(A, b, dt * lam))
+    disc = np.real(R ** nsteps * np.exp(1j * theta))
+    cont = np.real(np.exp(lam * dt * nsteps) * np.exp(1j * theta))
+    return disc, cont
