@@ -52,9 +52,13 @@ typedef enum { RK_F64 = 0, RK_F32 = 1, RK_F16 = 2, RK_BF16 = 3 } rk_dtype;
 typedef enum {
   RK_OP_HEAT7 = 0,      /* L u = kappa/h^2 * (7-point Laplacian), constant kappa,
                            applied matrix-free (Sec. 5.2.1)                     */
-  RK_OP_ADVDIFF_CSR = 1 /* L u = div(kappa(x) grad u) - v.grad u, face kappa =
+  RK_OP_ADVDIFF_CSR = 1, /* L u = div(kappa(x) grad u) - v.grad u, face kappa =
                            mean of the two nodes, first-order upwind, assembled
                            in CSR (variable-coefficient stand-in for Sec. 5.2.2) */
+  RK_OP_ADV_PERIODIC = 2 /* L u = -div(beta u) = -sum_d beta_d D_d u with the
+                           second-order central difference D_d, periodic in every
+                           direction, nodes x_i = i h, h = 1/n, n >= 3; beta = vel;
+                           assembled in CSR (the advection problem of Sec. 5.2.2) */
 } rk_op;
 
 typedef enum { RK_KRYLOV_CG = 0, RK_KRYLOV_GMRES = 1 } rk_krylov;
@@ -70,11 +74,16 @@ typedef enum { RK_PREC_BLOCK_JACOBI = 0, RK_PREC_FDM = 1 } rk_precond;
 
 typedef struct {
   int op;                    /* rk_op                                             */
-  int n;                     /* interior nodes per direction, 1 <= n <= 1024      */
+  int n;                     /* nodes per direction, 1 <= n <= 1024 (interior nodes
+                                for the Dirichlet operators)                      */
   double kappa;              /* constant diffusivity (RK_OP_HEAT7), > 0           */
   const double* kappa_field; /* RK_OP_ADVDIFF_CSR: n^3 host values at the nodes,
                                 lexicographic; copied at creation                 */
-  double vel[3];             /* RK_OP_ADVDIFF_CSR: constant velocity (vx,vy,vz)   */
+  double vel[3];             /* RK_OP_ADVDIFF_CSR, RK_OP_ADV_PERIODIC: constant
+                                velocity (vx,vy,vz)                               */
+  const double* source;      /* optional forcing f: n^3 host values; the problem is
+                                then du/dt = L u + f (Sec. 5.2.1 heat problem);
+                                NULL = none; copied at creation                   */
 } rk_problem_desc;
 
 typedef struct {
@@ -143,8 +152,9 @@ rk_status rk_destroy_problem(rk_problem* p);
 
 /* ---- single operations of the step (for testing the kernels) ------------- */
 
-/* y = L x in FP64 (the explicit evaluation k = f(y) of Sec. 4.2).  x, y: n^3
- * float64, host or device per is_device_ptr. */
+/* y = L x in FP64 (the explicit evaluation k = f(y) of Sec. 4.2, without the
+ * forcing term of a problem that has one).  x, y: n^3 float64, host or device
+ * per is_device_ptr. */
 rk_status rk_apply_op(rk_problem* p, const double* x, double* y, int is_device_ptr);
 
 /* Solve (I - shift L) k = g (Eq. corelinear in stage-derivative form) with the

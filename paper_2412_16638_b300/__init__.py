@@ -26,7 +26,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 RK_OK, RK_ERR_ARG, RK_ERR_OOM, RK_ERR_CUDA, RK_ERR_NOT_CONVERGED, RK_ERR_NONFINITE, RK_ERR_TIMEOUT, \
     RK_ERR_BUSY, RK_ERR_NOT_FOUND = range(9)
 RK_F64, RK_F32, RK_F16, RK_BF16 = range(4)
-RK_OP_HEAT7, RK_OP_ADVDIFF_CSR = 0, 1
+RK_OP_HEAT7, RK_OP_ADVDIFF_CSR, RK_OP_ADV_PERIODIC = 0, 1, 2
 RK_KRYLOV_CG, RK_KRYLOV_GMRES = 0, 1
 DTYPES = {"f64": RK_F64, "f32": RK_F32, "f16": RK_F16, "bf16": RK_BF16}
 RK_PREC_BLOCK_JACOBI, RK_PREC_FDM = 0, 1
@@ -35,7 +35,8 @@ PRECONDS = {"bj": RK_PREC_BLOCK_JACOBI, "fdm": RK_PREC_FDM}
 
 class rk_problem_desc(ctypes.Structure):
     _fields_ = [("op", ctypes.c_int), ("n", ctypes.c_int), ("kappa", ctypes.c_double),
-                ("kappa_field", ctypes.POINTER(ctypes.c_double)), ("vel", ctypes.c_double * 3)]
+                ("kappa_field", ctypes.POINTER(ctypes.c_double)), ("vel", ctypes.c_double * 3),
+                ("source", ctypes.POINTER(ctypes.c_double))]
 
 
 class rk_solver_desc(ctypes.Structure):
@@ -132,13 +133,17 @@ def _dvec(values):
     return (ctypes.c_double * len(values))(*values)
 
 
-def problem_desc(op=RK_OP_HEAT7, n=32, kappa=1.0, kappa_field=None, vel=(0.0, 0.0, 0.0)):
+def problem_desc(op=RK_OP_HEAT7, n=32, kappa=1.0, kappa_field=None, vel=(0.0, 0.0, 0.0), source=None):
     d = rk_problem_desc()
     d.op, d.n, d.kappa = op, n, kappa
     if kappa_field is not None:
         kf = np.ascontiguousarray(kappa_field, dtype=np.float64)
         d._kf = kf  # keeps the array alive as long as the descriptor
         d.kappa_field = kf.ctypes.data_as(_DP)
+    if source is not None:
+        sf = np.ascontiguousarray(source, dtype=np.float64)
+        d._sf = sf
+        d.source = sf.ctypes.data_as(_DP)
     d.vel = (ctypes.c_double * 3)(*vel)
     return d
 

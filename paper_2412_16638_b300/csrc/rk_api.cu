@@ -164,14 +164,14 @@ static HeatGeo heat_geo(const rk_problem* p, int seg) {
   return g;
 }
 
-rk_status op_apply_f64(rk_problem* p, const double* x, double* y, RhsScalars* rs) {
-  if (p->desc.op != RK_OP_HEAT7) return csr_apply_f64(p, x, y, rs);
+rk_status op_apply_f64(rk_problem* p, const double* x, double* y, RhsScalars* rs, const double* f) {
+  if (p->desc.op != RK_OP_HEAT7) return csr_apply_f64(p, x, y, rs, f);
   constexpr int SEG = 4;
   HeatGeo g = heat_geo(p, SEG);
   auto kern = heat_apply_f64<SEG>;
   int grid = grid_for((const void*)kern, g.n2 * g.nseg);
-  launch(p, K_OP, 16.0 * p->N,
-         [&] { kern<<<grid, kThreads, 0, p->st>>>(g, x, y, -6.0 * p->c, p->c, rs, p->partials); });
+  launch(p, K_OP, (f ? 24.0 : 16.0) * p->N,
+         [&] { kern<<<grid, kThreads, 0, p->st>>>(g, x, f, y, -6.0 * p->c, p->c, rs, p->partials); });
   RK_CUDA(cudaGetLastError());
   return RK_OK;
 }
@@ -475,12 +475,12 @@ rk_status step_impl(rk_problem* p, double dt, rk_stats* acc) {
       rp = p->r;
     }
     if (!implicit[i]) {
-      RK_TRY(op_apply_f64(p, rp, p->k[i], nullptr));
+      RK_TRY(op_apply_f64(p, rp, p->k[i], nullptr, p->src));  // k_i = L r_i + f
       continue;
     }
     const double shift = dt * p->Al[i * q + i];
     RhsScalars* rs = p->rs + i;
-    RK_TRY(op_apply_f64(p, rp, p->g64, rs));  // g = L r_i (FP64) + norms + scale
+    RK_TRY(op_apply_f64(p, rp, p->g64, rs, p->src));  // g = L r_i + f (FP64) + norms + scale
     int iters = 0, status = 0;
     RK_TRY(krylov_solve(p, shift, p->g64, rs, p->ke[i], i, &iters, &status));
     if (acc) {
@@ -614,8 +614,8 @@ static rk_status check_solver(const rk_solver_desc* s, const rk_problem_desc* d)
     set_error("CG needs the symmetric heat operator");
     return RK_ERR_ARG;
   }
-  if (s->krylov == RK_KRYLOV_GMRES && d && d->op != RK_OP_ADVDIFF_CSR) {
-    set_error("GMRES is implemented for the CSR advection-diffusion operator");
+  if (s->krylov == RK_KRYLOV_GMRES && d && d->op == RK_OP_HEAT7) {
+    set_error("GMRES is implemented for the CSR operators (advection-diffusion, periodic advection)");
     return RK_ERR_ARG;
   }
   if (s->max_refine < 0 || s->max_refine > 10) {
@@ -652,6 +652,7 @@ static void free_problem(rk_problem* p) {
   f(p->u);
   f(p->r);
   f(p->g64);
+  f(p->src);
   f(p->res64);
   for (int i = 0; i < 8; ++i) {
     f(p->k[i]);
@@ -692,7 +693,7 @@ rk_status rk_create_problem(const rk_problem_desc* desc, const rk_solver_desc* s
     set_error("problem descriptor is NULL");
     return RK_ERR_ARG;
   }
-  if (desc->op != RK_OP_HEAT7 && desc->op != RK_OP_ADVDIFF_CSR) {
+  if (desc->op != RK_OP_HEAT7 && desc->op != RK_OP_ADVDIFF_CSR && desc->op != RK_OP_ADV_PERIODIC) {
     set_error("unknown operator %d", desc->op);
     return RK_ERR_ARG;
   }
@@ -714,15 +715,31 @@ rk_status rk_create_problem(const rk_problem_desc* desc, const rk_solver_desc* s
       return RK_ERR_ARG;
     }
   }
+  if (desc->op == RK_OP_ADV_PERIODIC) {
+    if (desc->n < 3) {
+      set_error("RK_OP_ADV_PERIODIC needs n >= 3 (distinct neighbours on the periodic grid)");
+      return RK_ERR_ARG;
+    }
+    if ((long long)desc->n * desc->n * desc->n * 6 > 2000000000LL) {
+      set_error("CSR with int32 indices supports n^3*6 < 2e9");
+      return RK_ERR_ARG;
+    }
+    for (int d = 0; d < 3; ++d)
+      if (!std::isfinite(desc->vel[d])) {
+        set_error("vel must be finite");
+        return RK_ERR_ARG;
+      }
+  }
   RK_TRY(check_solver(solver, desc));
   rk_problem* p = new rk_problem();
   p->desc = *desc;
   p->desc.kappa_field = nullptr;
+  p->desc.source = nullptr;
   p->sol = *solver;
   p->st = static_cast<cudaStream_t>(cuda_stream);
   p->n = desc->n;
   p->N = (long long)desc->n * desc->n * desc->n;
-  p->h = 1.0 / (desc->n + 1);
+  p->h = desc->op == RK_OP_ADV_PERIODIC ? 1.0 / desc->n : 1.0 / (desc->n + 1);
   p->c = desc->kappa / (p->h * p->h);
   const size_t N = (size_t)p->N, s = dtype_size(solver->storage);
   rk_status st = RK_OK;
@@ -754,11 +771,18 @@ rk_status rk_create_problem(const rk_problem_desc* desc, const rk_solver_desc* s
       st = RK_ERR_CUDA;
     }
   }
-  if (st == RK_OK && desc->op == RK_OP_ADVDIFF_CSR) {
+  if (st == RK_OK && desc->op != RK_OP_HEAT7) {
     // csr_setup reads the kappa field from the caller's descriptor
     p->desc.kappa_field = desc->kappa_field;
     st = csr_setup(p);
     p->desc.kappa_field = nullptr;
+  }
+  if (st == RK_OK && desc->source) {
+    A((void**)&p->src, N * 8);
+    if (st == RK_OK && cudaMemcpy(p->src, desc->source, N * 8, cudaMemcpyHostToDevice) != cudaSuccess) {
+      set_error("copy of the forcing term failed");
+      st = RK_ERR_CUDA;
+    }
   }
   if (st != RK_OK) {
     free_problem(p);

@@ -1,6 +1,8 @@
 // Advection-diffusion path: CSR assembly, FP64 operator and correction,
 // block-Jacobi with per-block inverses, and the GMRES(m) driver.
+#include <algorithm>
 #include <cmath>
+#include <utility>
 
 #include "rk_csr.cuh"
 #include "rk_internal.h"
@@ -9,12 +11,13 @@ namespace rk {
 
 __global__ void __launch_bounds__(kThreads) csr_apply_f64_kernel(CsrView A, const double* __restrict__ vals,
                                                                  long long N, const double* __restrict__ x,
+                                                                 const double* __restrict__ f,
                                                                  double* __restrict__ y, RhsScalars* rs,
                                                                  double* partials) {
   double acc[2] = {0.0, 0.0};
   for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < N;
        r += (long long)gridDim.x * blockDim.x) {
-    double s = 0.0;
+    double s = f ? f[r] : 0.0;
     for (int e = A.rowptr[r]; e < A.rowptr[r + 1]; ++e) s = fma(vals[e], x[A.cols[e]], s);
     y[r] = s;
     acc[0] = fma(s, s, acc[0]);
@@ -121,16 +124,58 @@ static int gm_seg(int storage, int bs) {
   return bs > v ? bs : v;
 }
 
+// L u = -sum_d beta_d (u(x + h e_d) - u(x - h e_d)) / (2h) on the periodic
+// grid x_i = i h, h = 1/n (second-order central differences of Sec. 5.2.2,
+// the 1-D matrix Tridiag(-1, 0, 1) + K^(B) per direction).  n >= 3, so the two
+// neighbours of a node differ; columns of a row ascending, the diagonal (zero)
+// is not stored.
+static void assemble_periodic(int n, const double beta[3], std::vector<int>& rowptr, std::vector<int>& cols,
+                              std::vector<double>& vals) {
+  const long long N = (long long)n * n * n;
+  const double ih2 = 0.5 * n;  // 1 / (2h)
+  rowptr.assign(N + 1, 0);
+  cols.clear();
+  vals.clear();
+  cols.reserve(N * 6);
+  vals.reserve(N * 6);
+  const long long stride[3] = {1, n, (long long)n * n};
+  std::vector<std::pair<long long, double>> row;
+  for (int k = 0; k < n; ++k)
+    for (int j = 0; j < n; ++j)
+      for (int i = 0; i < n; ++i) {
+        const long long P = i + (long long)j * n + (long long)k * n * n;
+        const int idx[3] = {i, j, k};
+        row.clear();
+        for (int d = 0; d < 3; ++d) {
+          if (beta[d] == 0.0) continue;
+          const long long base = P - idx[d] * stride[d];
+          const long long plus = base + ((idx[d] + 1) % n) * stride[d];
+          const long long minus = base + ((idx[d] + n - 1) % n) * stride[d];
+          row.emplace_back(plus, -beta[d] * ih2);
+          row.emplace_back(minus, beta[d] * ih2);
+        }
+        std::sort(row.begin(), row.end());
+        for (const auto& e : row) {
+          cols.push_back((int)e.first);
+          vals.push_back(e.second);
+        }
+        rowptr[P + 1] = (int)cols.size();
+      }
+}
+
 rk_status csr_setup(rk_problem* p) {
   std::vector<int> rowptr, cols;
   std::vector<double> vals;
-  assemble(p->n, p->desc.kappa_field, p->desc.vel, rowptr, cols, vals);
+  if (p->desc.op == RK_OP_ADV_PERIODIC)
+    assemble_periodic(p->n, p->desc.vel, rowptr, cols, vals);
+  else
+    assemble(p->n, p->desc.kappa_field, p->desc.vel, rowptr, cols, vals);
   Csr& c = p->csr;
   c.nnz = (long long)vals.size();
   double vmax = 0.0;
   for (double v : vals) vmax = std::max(vmax, std::fabs(v));
   if (!(vmax > 0.0) || !std::isfinite(vmax)) {
-    set_error("CSR operator has no finite nonzero entries (check kappa_field)");
+    set_error("CSR operator has no finite nonzero entries (check kappa_field / vel)");
     return RK_ERR_ARG;
   }
   c.lscale = 1.0 / vmax;
@@ -194,12 +239,12 @@ rk_status csr_free(rk_problem* p) {
 
 static CsrView view(const rk_problem* p) { return CsrView{p->csr.rowptr, p->csr.cols}; }
 
-rk_status csr_apply_f64(rk_problem* p, const double* x, double* y, RhsScalars* rs) {
+rk_status csr_apply_f64(rk_problem* p, const double* x, double* y, RhsScalars* rs, const double* f) {
   auto kern = csr_apply_f64_kernel;
   const int grid = grid_for((const void*)kern, p->N);
-  const double bytes = (double)p->csr.nnz * 12.0 + 4.0 * (p->N + 1) + 16.0 * p->N;
+  const double bytes = (double)p->csr.nnz * 12.0 + 4.0 * (p->N + 1) + (f ? 24.0 : 16.0) * p->N;
   launch(p, K_CSR_SPMV, bytes,
-         [&] { kern<<<grid, kThreads, 0, p->st>>>(view(p), p->csr.v64, p->N, x, y, rs, p->partials); });
+         [&] { kern<<<grid, kThreads, 0, p->st>>>(view(p), p->csr.v64, p->N, x, f, y, rs, p->partials); });
   RK_CUDA(cudaGetLastError());
   return RK_OK;
 }
@@ -293,8 +338,8 @@ rk_status csr_precond_f64(rk_problem* p, double shift, const double* r, double* 
 // and the restart.
 rk_status gmres_solve(rk_problem* p, double shift, const double* g64, RhsScalars* rs, void* x, int slot, int* iters,
                       int* status) {
-  if (p->desc.op != RK_OP_ADVDIFF_CSR || !p->gw || !p->gw->V) {
-    set_error("GMRES is implemented for the CSR advection-diffusion operator");
+  if (p->desc.op == RK_OP_HEAT7 || !p->gw || !p->gw->V) {
+    set_error("GMRES is implemented for the CSR operators");
     return RK_ERR_ARG;
   }
   GmresWork* w = p->gw;

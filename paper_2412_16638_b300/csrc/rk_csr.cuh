@@ -45,9 +45,11 @@ struct GmScalars {
 };
 
 // ------------------------------------------------------------- FP64 CSR ops
-// y = L x (FP64); with rs != null also ||y||^2, ||y||_inf and the storage scale.
+// y = L x + f (FP64; f the optional forcing, nullptr = none); with rs != null
+// also ||y||^2, ||y||_inf and the storage scale.
 __global__ void __launch_bounds__(kThreads) csr_apply_f64_kernel(CsrView A, const double* __restrict__ vals,
                                                                  long long N, const double* __restrict__ x,
+                                                                 const double* __restrict__ f,
                                                                  double* __restrict__ y, RhsScalars* rs,
                                                                  double* partials);
 

@@ -99,13 +99,14 @@ __device__ __forceinline__ void nb_sum(const HeatGeo& g, int i0, int m, int j, i
 #define RK_SEG_LOOP_END }
 
 // ------------------------------------------------------------- FP64 operator
-// y = d*x + o*(sum of neighbours of x) in FP64 (L: d = -6c, o = c with
-// c = kappa/h^2).  If rs != null, also ||y||^2, ||y||_inf and the storage
-// scale are reduced into *rs (the stage right-hand side g = L r_i).
+// y = d*x + o*(sum of neighbours of x) + f in FP64 (L: d = -6c, o = c with
+// c = kappa/h^2; f the optional forcing, nullptr = none, at no extra FP64
+// operation).  If rs != null, also ||y||^2, ||y||_inf and the storage scale
+// are reduced into *rs (the stage right-hand side g = L r_i + f).
 template <int SEG>
 __global__ void __launch_bounds__(kThreads) heat_apply_f64(HeatGeo g, const double* __restrict__ x,
-                                                           double* __restrict__ y, double d, double o,
-                                                           RhsScalars* rs, double* partials) {
+                                                           const double* __restrict__ f, double* __restrict__ y,
+                                                           double d, double o, RhsScalars* rs, double* partials) {
   double acc[2] = {0.0, 0.0};
   RK_SEG_LOOP(g, SEG)
     double xv[SEG], nb[SEG];
@@ -114,10 +115,16 @@ __global__ void __launch_bounds__(kThreads) heat_apply_f64(HeatGeo g, const doub
         g, i0, m, j, k, base, xv,
         [&](long long off, int mm, double (&v)[SEG]) { load_seg<double, double, SEG>(x + off, mm, v); },
         [&](long long idx) { return x[idx]; }, nb);
-    double yv[SEG];
+    double yv[SEG], fv[SEG];
+    if (f) {
+      load_seg<double, double, SEG>(f + base, m, fv);
+    } else {
+#pragma unroll
+      for (int e = 0; e < SEG; ++e) fv[e] = 0.0;
+    }
 #pragma unroll
     for (int e = 0; e < SEG; ++e) {
-      yv[e] = fma(d, xv[e], o * nb[e]);
+      yv[e] = fma(d, xv[e], fma(o, nb[e], fv[e]));
       if (e < m) {
         acc[0] = fma(yv[e], yv[e], acc[0]);
         acc[1] = fmax(acc[1], fabs(yv[e]));

@@ -182,6 +182,7 @@ struct rk_problem {
   double* u = nullptr;
   double* r = nullptr;
   double* g64 = nullptr;
+  double* src = nullptr;  // forcing f of du/dt = L u + f (FP64), nullptr = none
   double* res64 = nullptr;
   double* k[8]{};
   void* ke[8]{};
@@ -223,8 +224,9 @@ rk_status get_minv_entry(rk_problem* p, double shift, const MinvEntry** out);
 // (storage precision, scaled by sigma).  Returns iterations in *iters.
 rk_status krylov_solve(rk_problem* p, double shift, const double* g64, RhsScalars* rs, void* x,
                        int slot, int* iters, int* status);
-// FP64 operator: y = L x; if rs != null also the RHS statistics.
-rk_status op_apply_f64(rk_problem* p, const double* x, double* y, RhsScalars* rs);
+// FP64 operator: y = L x + f (f: forcing, nullptr = none); if rs != null also
+// the RHS statistics.
+rk_status op_apply_f64(rk_problem* p, const double* x, double* y, RhsScalars* rs, const double* f = nullptr);
 // FP64 correction k = g + shift * L(ke/sigma) and true-residual norm into rs->res2.
 rk_status op_correct_f64(rk_problem* p, double shift, const double* g, const void* ke, double* kout,
                          RhsScalars* rs);
@@ -257,7 +259,7 @@ rk_status csr_free(rk_problem* p);
 rk_status gmres_solve(rk_problem* p, double shift, const double* g64, RhsScalars* rs, void* x, int slot,
                       int* iters, int* status);
 rk_status csr_precond_f64(rk_problem* p, double shift, const double* r, double* z);
-rk_status csr_apply_f64(rk_problem* p, const double* x, double* y, RhsScalars* rs);
+rk_status csr_apply_f64(rk_problem* p, const double* x, double* y, RhsScalars* rs, const double* f = nullptr);
 rk_status csr_correct_f64(rk_problem* p, double shift, const double* g, const void* ke, double* kout,
                           RhsScalars* rs);
 }  // namespace rk

@@ -173,8 +173,9 @@ extern "C" rk_status rk_integrate_batch(rk_problem** ps, int count, double dt, i
       set_error("rk_integrate_batch: problem %d is NULL", i);
       return RK_ERR_ARG;
     }
-    if (p->desc.op != RK_OP_HEAT7 || p->sol.krylov != RK_KRYLOV_CG || p->sol.precond != RK_PREC_BLOCK_JACOBI) {
-      set_error("rk_integrate_batch: problem %d is not a heat/CG/block-Jacobi problem", i);
+    if (p->desc.op != RK_OP_HEAT7 || p->sol.krylov != RK_KRYLOV_CG || p->sol.precond != RK_PREC_BLOCK_JACOBI ||
+        p->src) {
+      set_error("rk_integrate_batch: problem %d is not a heat/CG/block-Jacobi problem without forcing", i);
       return RK_ERR_ARG;
     }
     if (p->q == 0) {
@@ -322,6 +323,7 @@ struct Job {
   uint64_t id = 0;
   rk_problem_desc desc{};
   std::vector<double> kappa;  // copy of kappa_field
+  std::vector<double> source;  // copy of the forcing term
   rk_solver_desc sol{};
   int q = 0;
   std::vector<double> Ah, Al, b, u0;
@@ -348,7 +350,8 @@ static size_t job_footprint(const rk_problem_desc& d, const rk_solver_desc& s, i
   for (int i = 0; i < q; ++i)
     if (Al[i * q + i] != 0.0) ++implicit;
   size_t bytes = N * 8 * 3 + N * sb * 4 + N * 8 * q + N * xb * implicit + N * xb + (1u << 20);
-  if (d.op == RK_OP_ADVDIFF_CSR) {
+  if (d.source) bytes += N * 8;
+  if (d.op != RK_OP_HEAT7) {
     const size_t nnz = N * 7;
     bytes += nnz * (4 + 8 + sb) + (N + 1) * 4 + (size_t)(s.restart + 2) * N * sb + N * s.bj_block * sb * 4;
   }
@@ -467,6 +470,7 @@ static rk_status start_job(Job& j) {
   }
   rk_problem_desc d = j.desc;
   d.kappa_field = j.kappa.empty() ? nullptr : j.kappa.data();
+  d.source = j.source.empty() ? nullptr : j.source.data();
   RK_TRY(rk_create_problem(&d, &j.sol, j.stream, &j.p));
   RK_TRY(rk_set_tableau(j.p, j.q, j.Ah.data(), j.Al.data(), j.b.data()));
   RK_TRY(rk_set_state(j.p, j.u0.data(), 0));
@@ -524,7 +528,7 @@ static void worker_loop(rk_server* s) {
     for (size_t i = 0; i < act.size(); ++i) {
       Job* j = act[i].get();
       if (j->desc.op == RK_OP_HEAT7 && j->sol.krylov == RK_KRYLOV_CG && j->sol.precond == RK_PREC_BLOCK_JACOBI &&
-          j->desc.n <= kBatchMaxN) {
+          j->source.empty() && j->desc.n <= kBatchMaxN) {
         small[j->dt].push_back(act[i]);
       } else {
         tasks.push_back([&, i, j] {
@@ -609,7 +613,8 @@ rk_status rk_submit_job(rk_server* s, const rk_problem_desc* desc, const rk_solv
     set_error("rk_submit_job: need 1 <= q <= 8, dt > 0 finite, nsteps >= 0");
     return RK_ERR_ARG;
   }
-  if (desc->n < 1 || desc->n > 1024 || (desc->op != RK_OP_HEAT7 && desc->op != RK_OP_ADVDIFF_CSR) ||
+  if (desc->n < 1 || desc->n > 1024 ||
+      (desc->op != RK_OP_HEAT7 && desc->op != RK_OP_ADVDIFF_CSR && desc->op != RK_OP_ADV_PERIODIC) ||
       (desc->op == RK_OP_ADVDIFF_CSR && !desc->kappa_field)) {
     set_error("rk_submit_job: invalid problem descriptor");
     return RK_ERR_ARG;
@@ -618,7 +623,9 @@ rk_status rk_submit_job(rk_server* s, const rk_problem_desc* desc, const rk_solv
   j->desc = *desc;
   const size_t N = (size_t)desc->n * desc->n * desc->n;
   if (desc->kappa_field) j->kappa.assign(desc->kappa_field, desc->kappa_field + N);
+  if (desc->source) j->source.assign(desc->source, desc->source + N);
   j->desc.kappa_field = nullptr;
+  j->desc.source = nullptr;
   j->sol = *solver;
   j->q = q;
   j->Ah.assign(A_hi, A_hi + q * q);

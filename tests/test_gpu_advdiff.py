@@ -128,3 +128,16 @@ def test_config3_full_size_sampled_rows_and_true_residual(rk):
     res = g - (k - shift * (L @ k))
     assert np.linalg.norm(res) / np.linalg.norm(g) < 5e-5
     assert st.iters_total < 600
+
+
+def test_nonfinite_state_reported(rk):
+    """GMRES path: an infinite value in the state is reported as
+    RK_ERR_NONFINITE."""
+    n = 16
+    u0 = synth.gaussian_bump(n)
+    bad = u0.copy()
+    bad[123] = np.inf
+    with make(rk, n, storage="f32", tol=1e-6, correct=1, tab="dirk3", u0=bad) as p:
+        with pytest.raises(rk.RKError) as e:
+            rk.rk_step(p.h, 5e-4)
+        assert e.value.status == rk.RK_ERR_NONFINITE

@@ -248,3 +248,22 @@ def test_fp32_correction_matches_fp64_stencil(rk):
                          dirk.Solver("cg", bs=8, tol_rel=1e-13))
     assert rel_l2(u, ref) < 1e-6
     assert 0.0 <= st.true_res < 1e-4
+
+
+@pytest.mark.parametrize("storage,precond", [("f64", "bj"), ("f32", "bj"), ("f16", "bj"), ("f32", "fdm")])
+def test_nonfinite_state_reported(rk, storage, precond):
+    """A NaN in the state is caught by the fused reductions of the stage solve
+    and reported as RK_ERR_NONFINITE (never a hang or a silent result); the
+    problem stays usable after a valid state is set again."""
+    n = 32
+    u0 = synth.sine_mode(n)
+    bad = u0.copy()
+    bad[n ** 3 // 2 + 5] = np.nan
+    with make(rk, n, storage=storage, bs=8, tol=1e-6, tab="sdirk2", u0=bad, precond=precond) as p:
+        with pytest.raises(rk.RKError) as e:
+            rk.rk_step(p.h, 1e-3)
+        assert e.value.status == rk.RK_ERR_NONFINITE
+        rk.rk_set_state(p.h, u0)
+        rk.rk_integrate(p.h, 1e-3, 2)
+        u = p.state()
+    assert np.all(np.isfinite(u)) and rel_l2(u, u0) < 0.1

@@ -74,6 +74,22 @@ def test_fdm_argument_checks_without_gpu(rk):
     assert create(heat, rk.solver_desc(precond="fdm", krylov=rk.RK_KRYLOV_GMRES)) == rk.RK_ERR_ARG
 
 
+def test_periodic_and_forcing_argument_checks_without_gpu(rk):
+    h = ctypes.c_void_p()
+
+    def create(d, s):
+        return rk._lib.rk_create_problem(ctypes.byref(d), ctypes.byref(s), None, ctypes.byref(h))
+
+    gm = rk.solver_desc(krylov=rk.RK_KRYLOV_GMRES)
+    assert create(rk.problem_desc(op=rk.RK_OP_ADV_PERIODIC, n=2, vel=(1, 1, 1)), gm) == rk.RK_ERR_ARG
+    assert "n >= 3" in rk.rk_last_error()
+    assert create(rk.problem_desc(op=rk.RK_OP_ADV_PERIODIC, n=8, vel=(1, float("nan"), 1)), gm) == rk.RK_ERR_ARG
+    assert create(rk.problem_desc(op=rk.RK_OP_ADV_PERIODIC, n=8, vel=(1, 1, 1)), rk.solver_desc()) == rk.RK_ERR_ARG
+    assert "CG" in rk.rk_last_error()
+    assert create(rk.problem_desc(n=8), gm) == rk.RK_ERR_ARG
+    assert create(rk.problem_desc(op=7, n=8), rk.solver_desc()) == rk.RK_ERR_ARG
+
+
 def test_package_tableaux_match_oracle(rk):
     """The library's tableau table and the oracle's are typed independently
     from the paper; they must agree."""
