@@ -287,6 +287,71 @@ def run_batch(args):
     return 0
 
 
+def run_paper_sweep(args):
+    """Error at T = 0.1 against the analytic solution for the paper's two test
+    problems (Sec. 5.2) over tau = 1/10 .. 1/1280 (Fig. CombinedErrors), FP32
+    mixed precision (perturbed step, FP64 corrections) vs plain FP64, solver
+    tolerance 1e-3.  Heat (Sec. 5.2.1): u_t = Lap u + g, g the sine mode,
+    u(0) = 0, u_a = g (1 - e^{-3 pi^2 t}) / (3 pi^2); FP32 CG with the
+    fast-diagonalization preconditioner, FP64 CG with block-Jacobi.  Advection
+    (Sec. 5.2.2): periodic, beta = (1,1,1), the Gaussian bump, exact solution
+    the bump translated by beta t; GMRES(30) + block-Jacobi in both precisions."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2412_16638_b300 as rk
+
+    torch.cuda.set_device(0)
+    T = 0.1
+    taus = [1.0 / m for m in (10, 20, 40, 80, 160, 320, 640, 1280)]
+    out = {}
+    for problem in args.paper_sweep.split(","):
+        heat = problem == "heat"
+        n = args.paper_n or (256 if heat else 200)
+        methods = ["midpoint1", "4s3pB", "4s3pC"] + ([] if heat else ["4s3pA"])
+        if heat:
+            g = synth.sine_mode(n)
+            exact = g * (1.0 - math.exp(-3.0 * math.pi ** 2 * T)) / (3.0 * math.pi ** 2)
+            u0 = np.zeros(n ** 3)
+            desc = rk.problem_desc(n=n, kappa=1.0, source=g)
+        else:
+            beta = (1.0, 1.0, 1.0)
+            x, y, z = synth.periodic_coords(n)
+            d2 = sum(((c - 0.5 - T * b + 0.5) % 1.0 - 0.5) ** 2 for c, b in zip((x, y, z), beta))
+            exact = np.exp(-100.0 * d2).ravel()
+            u0 = synth.gaussian_bump_periodic(n)
+            desc = rk.problem_desc(op=rk.RK_OP_ADV_PERIODIC, n=n, vel=beta)
+        rows = []
+        for name in methods:
+            tab = rk.tableaux.get(name)
+            for tau in taus:
+                steps = int(round(T / tau))
+                row = {"method": name, "tau": tau, "steps": steps}
+                for prec in ("f32", "f64"):
+                    if heat:
+                        sol = rk.solver_desc(tol_rel=1e-3, storage=prec, max_iter=5000, correct=1 if prec == "f32" else 0,
+                                             precond="fdm" if prec == "f32" else "bj", bj_block=8)
+                    else:
+                        sol = rk.solver_desc(krylov=rk.RK_KRYLOV_GMRES, restart=30, bj_block=8, tol_rel=1e-3,
+                                             storage=prec, max_iter=5000, correct=1 if prec == "f32" else 0)
+                    with rk.Problem(desc, sol, tableau=tab, u0=u0) as p:
+                        torch.cuda.synchronize()
+                        t0 = time.perf_counter()
+                        try:
+                            st = rk.rk_integrate(p.h, tau, steps, allow_not_converged=True)
+                            u = p.state()
+                            err = rel(u, exact) if np.all(np.isfinite(u)) else float("inf")
+                            row[prec] = {"err": err, "iters_per_solve": st.iters_total / max(st.solves, 1),
+                                         "ms_per_step": 1e3 * (time.perf_counter() - t0) / steps}
+                        except rk.RKError as e:
+                            row[prec] = {"err": None, "status": e.status}
+                rows.append(row)
+        out[problem] = {"n": n, "rows": rows}
+    print(json.dumps({"paper_sweep": out, "T": T, "tol_rel": 1e-3, "data": "synthetic",
+                      "note": "errors are relative L2 against the analytic solution at T"}))
+    return 0
+
+
 def run_serve(args):
     """Serving workload: Poisson arrivals (200 jobs/s) of --serve jobs, n in
     {32, 64, 96, 128, 192}, tableau in {midpoint + 1 correction, SDIRK2,
@@ -358,7 +423,11 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=50)
     ap.add_argument("--serve", type=int, default=0, help="run the serving workload with this many jobs instead")
     ap.add_argument("--serve-slots", type=int, default=64)
+    ap.add_argument("--paper-sweep", default="", help="heat,advection: error vs tau at T = 0.1 (Sec. 5.2)")
+    ap.add_argument("--paper-n", type=int, default=0, help="grid of the paper sweep (256 heat, 200 advection)")
     args = ap.parse_args()
+    if args.paper_sweep:
+        return run_paper_sweep(args)
     if args.batch:
         return run_batch(args)
     if args.serve:
