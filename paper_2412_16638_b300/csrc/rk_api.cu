@@ -314,11 +314,15 @@ static rk_status heat_cg_solve(rk_problem* p, double shift, const double* g64, R
       using X = typename XOf<S>::type;
       X* xs = static_cast<X*>(x);
       BjInv<T, BS> M;
+      BjTri<T, BS> tri;
       if (fdm) {
         for (auto& v : M.m) v = T(0);
         for (int i = 0; i < BS; ++i) M.m[i * BS + i] = M.m[BS * BS + i * BS + i] = T(1);
+        for (int i = 0; i < BS; ++i) tri.ip[i] = T(1), tri.nu[i] = T(0);
+        tri.mo = T(0);
       } else {
         M = bj_param<T, BS>(me->host);
+        tri = bj_tri<T, BS>(1.0 + 6.0 * shift * p->c, -shift * p->c);
       }
       auto ki = cg_init<S, T, BS, SEG>;
       auto ka = cg_sweep_a<S, T, SEG>;
@@ -348,11 +352,11 @@ static rk_status heat_cg_solve(rk_problem* p, double shift, const double* g64, R
             // 8 vectors per iteration: A reads r, p_old, writes p; B reads p, r, x, writes r, x
             prof_begin(p, K_CG_A, (idx == 0 ? 2.0 : 3.0) * Ns, solve, idx);
             cg_tiled_a<S, T, BS, SEG><<<tgrid, athreads, sma, p->st>>>(fdm ? p->tiled->z : p->tiled->r,
-                                                                       p->tiled->p[cur ^ 1], tg, d, o, M, pn, p->sc,
+                                                                       p->tiled->p[cur ^ 1], tg, d, o, tri, pn, p->sc,
                                                                        p->partials);
             prof_end(p);
             prof_begin(p, K_CG_B, (idx == 0 ? 3.0 * Ns + Nx : 3.0 * Ns + 2.0 * Nx), solve, idx);
-            cg_tiled_b<S, T, BS, SEG><<<tgrid, tthreads, smb, p->st>>>(p->tiled->p[cur], tg, d, o, M, xs, r, p->sc,
+            cg_tiled_b<S, T, BS, SEG><<<tgrid, tthreads, smb, p->st>>>(p->tiled->p[cur], tg, d, o, tri, xs, r, p->sc,
                                                                        p->partials);
             prof_end(p);
           } else {

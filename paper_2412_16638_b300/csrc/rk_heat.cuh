@@ -259,6 +259,38 @@ struct BjInv {
   T m[2 * BS * BS];
 };
 
+// The same block inverse in factored form: the x-line block of I - shift L is
+// the constant tridiagonal matrix tridiag(o, d, o) (d = 1 + 6 shift c,
+// o = -shift c), whose LU factors have pivots p_1 = d, p_i = d - o^2/p_{i-1}.
+// With ip_i = 1/p_i, mo = -o and nu_i = -o ip_i, the solve is
+//   y_1 = ip_1 r_1,  y_i = ip_i (r_i + mo y_{i-1}),  z_BS = y_BS,
+//   z_i = y_i + nu_i z_{i+1}
+// (3 FP32 operations per element instead of BS for the dense inverse); the
+// factors are formed in FP64 and rounded.  Full blocks only (the callers'
+// segments hold whole blocks).  The blocks are diagonally dominant, so the
+// recurrences are stable.
+template <typename T, int BS>
+struct BjTri {
+  T ip[BS];
+  T nu[BS];
+  T mo;
+};
+
+template <typename T, int BS, int SEG>
+__device__ __forceinline__ void bj_apply_tri(const BjTri<T, BS>& t, const T (&r)[SEG], T (&z)[SEG]) {
+  static_assert(SEG % BS == 0, "segments hold whole blocks");
+#pragma unroll
+  for (int cb = 0; cb < SEG / BS; ++cb) {
+    T y[BS];
+    y[0] = t.ip[0] * r[cb * BS];
+#pragma unroll
+    for (int i = 1; i < BS; ++i) y[i] = t.ip[i] * fma(t.mo, y[i - 1], r[cb * BS + i]);
+    z[cb * BS + BS - 1] = y[BS - 1];
+#pragma unroll
+    for (int i = BS - 2; i >= 0; --i) z[cb * BS + i] = fma(t.nu[i], z[cb * BS + i + 1], y[i]);
+  }
+}
+
 // z = D^{-1} r on every block of the segment.
 template <typename T, int BS, int SEG>
 __device__ __forceinline__ void bj_apply(const T* sM, int n, int i0, const T (&r)[SEG], T (&z)[SEG]) {

@@ -99,6 +99,21 @@ struct MinvEntry {
 };
 
 // Kernel-parameter copy of a heat block-Jacobi inverse.
+// LU factors of the constant tridiagonal block tridiag(off, dd, off) of BS
+// nodes, formed in FP64 (see BjTri).
+template <typename T, int BS>
+inline BjTri<T, BS> bj_tri(double dd, double off) {
+  BjTri<T, BS> t;
+  double piv = dd;
+  for (int i = 0; i < BS; ++i) {
+    if (i > 0) piv = dd - off * off / piv;
+    t.ip[i] = (T)(1.0 / piv);
+    t.nu[i] = (T)(-off / piv);
+  }
+  t.mo = (T)(-off);
+  return t;
+}
+
 template <typename T, int BS>
 inline BjInv<T, BS> bj_param(const std::vector<double>& h) {
   BjInv<T, BS> v;

@@ -131,7 +131,7 @@ __device__ __forceinline__ void sts_seg(S* p, const T (&v)[SEG]) {
 template <typename S, typename T, int BS, int SEG>
 __global__ void __launch_bounds__(320, 2) cg_tiled_a(const __grid_constant__ CUtensorMap tm_r,
                                                   const __grid_constant__ CUtensorMap tm_po, TileGeo tg, T d, T o,
-                                                  const __grid_constant__ BjInv<T, BS> inv, S* __restrict__ pnew,
+                                                  const __grid_constant__ BjTri<T, BS> tri, S* __restrict__ pnew,
                                                   CgScalars* sc, double* partials) {
   if (sc->done) return;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -141,7 +141,6 @@ __global__ void __launch_bounds__(320, 2) cg_tiled_a(const __grid_constant__ CUt
   auto st_r = [&](int s) { return reinterpret_cast<S*>(base + (size_t)s * 2 * tile); };
   auto st_p = [&](int s) { return reinterpret_cast<S*>(base + (size_t)s * 2 * tile + tile); };
   auto ring = [&](int s) { return reinterpret_cast<S*>(base + (size_t)kStagesA * 2 * tile + (size_t)s * tile); };
-  const T* sM = inv.m;
   uint64_t* bar = reinterpret_cast<uint64_t*>(base + (size_t)(kStagesA * 2 + 3) * tile);
   const int tid = threadIdx.x;
   const int tx = tid % tg.tpl, row = tid / tg.tpl;  // row in 0..TY+1
@@ -181,7 +180,7 @@ __global__ void __launch_bounds__(320, 2) cg_tiled_a(const __grid_constant__ CUt
     {
       T rv[SEG];
       lds_seg<T, S, SEG>(st_r(s) + (size_t)row * n + xs, rv);
-      bj_apply<T, BS, SEG>(sM, n, xs, rv, pn);
+      bj_apply_tri<T, BS, SEG>(tri, rv, pn);
       if (!first) {
         T pv[SEG];
         lds_seg<T, S, SEG>(st_p(s) + (size_t)row * n + xs, pv);
@@ -264,7 +263,7 @@ __global__ void __launch_bounds__(320, 2) cg_tiled_a(const __grid_constant__ CUt
 // convergence test.
 template <typename S, typename T, int BS, int SEG>
 __global__ void __launch_bounds__(256, 2) cg_tiled_b(const __grid_constant__ CUtensorMap tm_p, TileGeo tg, T d, T o,
-                                                  const __grid_constant__ BjInv<T, BS> inv,
+                                                  const __grid_constant__ BjTri<T, BS> tri,
                                                   typename XOf<S>::type* __restrict__ x, S* __restrict__ r,
                                                   CgScalars* sc, double* partials) {
   using X = typename XOf<S>::type;
@@ -273,7 +272,6 @@ __global__ void __launch_bounds__(256, 2) cg_tiled_b(const __grid_constant__ CUt
   const int n = tg.n, TY = tg.ty, R = TY + 2;
   const size_t tile = align128((size_t)R * n * sizeof(S));
   auto st = [&](int s) { return reinterpret_cast<S*>(smem + (size_t)s * tile); };
-  const T* sM = inv.m;
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + (size_t)kStagesB * tile);
   const int tid = threadIdx.x;
   const int tx = tid % tg.tpl, ly = tid / tg.tpl;
@@ -351,7 +349,7 @@ __global__ void __launch_bounds__(256, 2) cg_tiled_b(const __grid_constant__ CUt
         xv[e] = fma(alpha, pcur[e], xv[e]);
       }
       T zv[SEG];
-      bj_apply<T, BS, SEG>(sM, n, xs, rv, zv);
+      bj_apply_tri<T, BS, SEG>(tri, rv, zv);
 #pragma unroll
       for (int e = 0; e < SEG; ++e) {
         zv[e] = rnd<S, T>(zv[e]);
