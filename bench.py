@@ -287,6 +287,82 @@ def run_batch(args):
     return 0
 
 
+def run_advdiff(args):
+    """Advection-diffusion workload (variable kappa, CSR, GMRES(30) + block-
+    Jacobi 8, DIRK3, dt 5e-4, tol 1e-8): the mixed step (FP32 GMRES, FP64
+    corrections) against the plain FP64 step on the same problem, both timed
+    with CUDA events over --steps steps after --warmup; errors against an FP64
+    run solved to 1e-12 (no closed form for variable kappa)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2412_16638_b300 as rk
+
+    torch.cuda.set_device(0)
+    n, dt, vel = args.advdiff, 5e-4, (1.0, 0.5, 0.25)
+    N = n ** 3
+    kap = synth.kappa_field(n, seed=0)
+    u0 = synth.gaussian_bump(n)
+    tab = rk.tableaux.get("dirk3")
+    stream = torch.cuda.current_stream()
+
+    def make(storage, tol, correct, basis=None):
+        kw = {} if basis is None else {"basis": basis}
+        return rk.Problem(rk.problem_desc(op=rk.RK_OP_ADVDIFF_CSR, n=n, kappa_field=kap, vel=vel),
+                          rk.solver_desc(krylov=rk.RK_KRYLOV_GMRES, restart=30, bj_block=8, tol_rel=tol,
+                                         storage=storage, correct=correct, max_iter=3000, **kw),
+                          tableau=tab, u0=u0, stream=stream.cuda_stream)
+
+    def timed(p, prof=False):
+        rk.rk_integrate(p.h, dt, args.warmup)
+        if prof:
+            rk.rk_profile(p.h, True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = rk.rk_integrate(p.h, dt, args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out = (e0.elapsed_time(e1) / 1e3, st)
+        if prof:
+            out += rk.rk_profile_read(p.h)
+        return out
+
+    with make("f64", 1e-12, 0) as q:
+        rk.rk_integrate(q.h, dt, args.warmup + args.steps)
+        ref = q.state()
+    variants = {"mixed_f32": ("f32", 1e-8, 1, None), "fp64_plain": ("f64", 1e-8, 0, None)}
+    if args.advdiff_basis:
+        variants["mixed_f32_basis_" + args.advdiff_basis] = ("f32", 1e-8, 1, args.advdiff_basis)
+    res = {}
+    peak, peak_kind = measured_peaks()
+    for name, (storage, tol, corr, basis) in variants.items():
+        with make(storage, tol, corr, basis) as p:
+            secs, st, prof, launches = timed(p, prof=True)
+            u = p.state()
+        kern = {k: {"launches": v["launches"], "avg_us": round(1e3 * v["ms_total"] / max(v["launches"], 1), 2),
+                    "GBps": round(v["bytes_total"] / max(v["ms_total"], 1e-9) / 1e6, 1),
+                    "share": round(v["ms_total"] / sum(x["ms_total"] for x in prof.values()), 4)}
+                for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms_total"])}
+        dom, d = max(prof.items(), key=lambda kv: kv[1]["ms_total"])
+        achieved = d["bytes_total"] / (d["ms_total"] / 1e3) / 1e9
+        res[name] = {"value": N * args.steps / secs, "ms_per_step": 1e3 * secs / args.steps,
+                     "iters_per_solve": st.iters_total / max(st.solves, 1), "err_vs_fp64_tight": rel(u, ref),
+                     "gpu_launches": launches,
+                     "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
+                                  "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_kind": peak_kind},
+                     "kernels": kern}
+    line = {"metric": METRIC, "workload": "advdiff%d" % n, "unit": "DOF*steps/s", "steps": args.steps,
+            "warmup": args.warmup, "data": "synthetic",
+            "config": {"grid": "%d^3" % n, "kappa": "exp(Gaussian field, sigma 0.5, l 0.1), seed 0",
+                       "vel": vel, "tableau": "dirk3", "dt": dt, "krylov": "gmres(30)", "bj_block": 8,
+                       "tol_rel": 1e-8, "u0": "Gaussian bump"},
+            "variants": res,
+            "speedup_vs_fp64": res["mixed_f32"]["value"] / res["fp64_plain"]["value"]}
+    print(json.dumps(line))
+    return 0
+
+
 def run_paper_sweep(args):
     """Error at T = 0.1 against the analytic solution for the paper's two test
     problems (Sec. 5.2) over tau = 1/10 .. 1/1280 (Fig. CombinedErrors), FP32
@@ -432,9 +508,13 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=64)
     ap.add_argument("--paper-sweep", default="", help="heat,advection: error vs tau at T = 0.1 (Sec. 5.2)")
     ap.add_argument("--paper-n", type=int, default=0, help="grid of the paper sweep (256 heat, 200 advection)")
+    ap.add_argument("--advdiff", type=int, default=0, help="run the advection-diffusion GMRES workload at this n")
+    ap.add_argument("--advdiff-basis", default="", help="also run the mixed step with this GMRES basis dtype")
     args = ap.parse_args()
     if args.paper_sweep:
         return run_paper_sweep(args)
+    if args.advdiff:
+        return run_advdiff(args)
     if args.batch:
         return run_batch(args)
     if args.serve:
