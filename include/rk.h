@@ -104,6 +104,9 @@ typedef struct {
                       tol_true (0 disables)                                         */
   double tol_true; /* true-residual acceptance bound (<= 0: report only)            */
   int precond;     /* rk_precond (0 = block-Jacobi)                                 */
+  int basis;       /* GMRES Krylov basis dtype: 0 or the storage dtype = same as the
+                      other Krylov vectors; RK_BF16 with RK_F32 storage = compressed
+                      basis (BF16 vectors, FP32 arithmetic)                        */
 } rk_solver_desc;
 
 typedef struct {

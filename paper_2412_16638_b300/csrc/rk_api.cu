@@ -626,6 +626,14 @@ static rk_status check_solver(const rk_solver_desc* s, const rk_problem_desc* d)
     set_error("max_refine must be in 0..10");
     return RK_ERR_ARG;
   }
+  if (!(s->basis == 0 || s->basis == s->storage || (s->basis == RK_BF16 && s->storage == RK_F32))) {
+    set_error("GMRES basis: 0 or the storage dtype, or RK_BF16 with RK_F32 storage (got %d)", s->basis);
+    return RK_ERR_ARG;
+  }
+  if (s->basis == RK_BF16 && s->storage == RK_F32 && s->krylov != RK_KRYLOV_GMRES) {
+    set_error("a compressed basis applies to GMRES only");
+    return RK_ERR_ARG;
+  }
   if (s->precond != RK_PREC_BLOCK_JACOBI && s->precond != RK_PREC_FDM) {
     set_error("unknown preconditioner %d", s->precond);
     return RK_ERR_ARG;

@@ -199,7 +199,7 @@ rk_status csr_setup(rk_problem* p) {
     p->gw = w;
     const size_t s = dtype_size(p->sol.storage);
     const int m = p->sol.restart;
-    RK_TRY(alloc_dev(p, &w->V, (size_t)(m + 1) * p->N * s));
+    RK_TRY(alloc_dev(p, &w->V, (size_t)(m + 1) * p->N * dtype_size(basis_dtype(p->sol))));
     RK_TRY(alloc_dev(p, &w->z, (size_t)p->N * s));
     const int seg = gm_seg(p->sol.storage, p->sol.bj_block);
     const int R = std::max(1, 32 / seg);
@@ -352,12 +352,22 @@ rk_status gmres_solve(rk_problem* p, double shift, const double* g64, RhsScalars
   hs->m = m;
   hs->tol_rel = p->sol.tol_rel;
   hs->tol_abs = p->sol.tol_abs;
+  hs->verify = basis_dtype(p->sol) != p->sol.storage ? 1 : 0;
   RK_CUDA(cudaMemcpyAsync(w->sc, hs, kGmHeader, cudaMemcpyHostToDevice, p->st));
   const int solve = ++p->solve_seq;
   rk_status st = RK_OK;
-  dispatch_st(p->sol.storage, [&](auto ts, auto tt) {
+  // basis type: the storage type, or BF16 with FP32 storage (compressed basis)
+  auto with_basis = [&](auto ts, auto tt, auto fn) {
+    using S = typename decltype(ts)::type;
+    if constexpr (std::is_same<S, float>::value) {
+      if (basis_dtype(p->sol) == RK_BF16) return fn(ts, tt, Tag<__nv_bfloat16>{});
+    }
+    return fn(ts, tt, ts);
+  };
+  dispatch_st(p->sol.storage, [&](auto ts0, auto tt0) { with_basis(ts0, tt0, [&](auto ts, auto tt, auto tb) {
     using S = typename decltype(ts)::type;
     using T = typename decltype(tt)::type;
+    using B = typename decltype(tb)::type;
     using X = typename XOf<S>::type;
     dispatch_bs(p->sol.bj_block, [&](auto bsc) {
       constexpr int BS = decltype(bsc)::value;
@@ -366,7 +376,7 @@ rk_status gmres_solve(rk_problem* p, double shift, const double* g64, RhsScalars
       HeatGeo g{p->n, (p->n + SEG - 1) / SEG, (long long)p->n * p->n, p->N};
       const long long nsegs = g.n2 * g.nseg;
       const int gdots = (int)(((nsegs + R - 1) / R + kThreads - 1) / kThreads);
-      S* V = static_cast<S*>(w->V);
+      B* V = static_cast<B*>(w->V);
       S* z = static_cast<S*>(w->z);
       X* xs = static_cast<X*>(x);
       const S* lv = static_cast<const S*>(p->csr.vS);
@@ -374,16 +384,17 @@ rk_status gmres_solve(rk_problem* p, double shift, const double* g64, RhsScalars
       const T cs = (T)(shift / p->csr.lscale);
       const long long ldv = p->N;
       const double Ns = (double)p->N * sizeof(S), Nx = (double)p->N * sizeof(X);
+      const double Nb = (double)p->N * sizeof(B);
       const double mat = (double)p->csr.nnz * (4.0 + sizeof(S)) + 4.0 * (p->N + 1);
-      auto k_start = gm_start<S, T, SEG>;
-      auto k_restart = gm_restart<S, T, SEG>;
-      auto k_prec = gm_prec<S, T, BS, SEG>;
-      auto k_spmv = gm_spmv_dots<S, T, SEG, R>;
-      auto k_orth = gm_orth<S, T, SEG, R>;
-      auto k_norm = gm_norm<S, T, SEG, R>;
-      auto k_upd = gm_update<S, T, BS, SEG>;
+      auto k_start = gm_start<S, B, T, SEG>;
+      auto k_restart = gm_restart<S, B, T, SEG>;
+      auto k_prec = gm_prec<S, B, T, BS, SEG>;
+      auto k_spmv = gm_spmv_dots<S, B, T, SEG, R>;
+      auto k_orth = gm_orth<S, B, T, SEG, R>;
+      auto k_norm = gm_norm<S, B, T, SEG, R>;
+      auto k_upd = gm_update<S, B, T, BS, SEG>;
       const int gs = grid_for((const void*)k_start, nsegs), gp = grid_for((const void*)k_prec, nsegs);
-      launch(p, K_GM_INIT, 8.0 * p->N + Ns + Nx,
+      launch(p, K_GM_INIT, 8.0 * p->N + Nb + Nx,
              [&] { k_start<<<gs, kThreads, 0, p->st>>>(g, g64, rs, V, xs, w->sc, w->partials); });
       int launched = 0, worked = 0, rounds = 0;
       const int maxlaunch = p->sol.max_iter + 2 * m + 64;
@@ -399,16 +410,16 @@ rk_status gmres_solve(rk_problem* p, double shift, const double* g64, RhsScalars
           const int idx = launched + c;
           // bytes use the basis size at the step's expected index (j = idx mod m)
           const double jb = (double)(idx % m) + 1.0;
-          prof_begin(p, K_GM_PREC, 3.0 * Ns + BS * Ns, solve, idx);
+          prof_begin(p, K_GM_PREC, 2.0 * Nb + Ns + BS * Ns, solve, idx);
           k_prec<<<gp, kThreads, 0, p->st>>>(g, V, ldv, M, z, w->sc);
           prof_end(p);
-          prof_begin(p, K_GM_ARNOLDI, mat + Ns + jb * Ns + Ns, solve, idx);
+          prof_begin(p, K_GM_ARNOLDI, mat + Ns + jb * Nb + Nb, solve, idx);
           k_spmv<<<gdots, kThreads, 0, p->st>>>(g, view(p), lv, cs, z, V, ldv, w->sc, w->partials);
           prof_end(p);
-          prof_begin(p, K_GM_ORTH, 2.0 * jb * Ns + 2.0 * Ns, solve, idx);
+          prof_begin(p, K_GM_ORTH, 2.0 * jb * Nb + 2.0 * Nb, solve, idx);
           k_orth<<<gdots, kThreads, 0, p->st>>>(g, V, ldv, w->sc, w->partials);
           prof_end(p);
-          prof_begin(p, K_GM_NORM, jb * Ns + 2.0 * Ns, solve, idx);
+          prof_begin(p, K_GM_NORM, jb * Nb + 2.0 * Nb, solve, idx);
           k_norm<<<gdots, kThreads, 0, p->st>>>(g, V, ldv, w->sc, w->partials);
           prof_end(p);
         }
@@ -429,10 +440,10 @@ rk_status gmres_solve(rk_problem* p, double shift, const double* g64, RhsScalars
         worked = hs->iter;
         launched = worked;  // launch indices continue from the device step count
         if (hs->cycle_end) {
-          launch(p, K_GM_UPDATE, (double)hs->jused * Ns + 2.0 * Nx + BS * Ns,
+          launch(p, K_GM_UPDATE, (double)hs->jused * Nb + 2.0 * Nx + BS * Ns,
                  [&] { k_upd<<<gp, kThreads, 0, p->st>>>(g, V, ldv, M, xs, w->sc); });
           if (hs->done) break;
-          launch(p, K_GM_INIT, mat + Nx + 8.0 * p->N + Ns, [&] {
+          launch(p, K_GM_INIT, mat + Nx + 8.0 * p->N + Nb, [&] {
             k_restart<<<gs, kThreads, 0, p->st>>>(g, view(p), lv, cs, g64, rs, xs, V, w->sc, w->partials);
           });
         } else if (hs->done) {
@@ -449,7 +460,7 @@ rk_status gmres_solve(rk_problem* p, double shift, const double* g64, RhsScalars
         set_error("GMRES final synchronisation failed");
       }
     });
-  });
+  }); });
   if (st != RK_OK) return st;
   *iters = hs->iter;
   *status = hs->status;

@@ -32,7 +32,10 @@ struct GmScalars {
   int status;     // 0 ok, 4 not converged, 5 non-finite
   int jused;      // basis vectors used by the finished cycle
   unsigned ticket;
-  int pad;
+  int verify;     // 1: a converged cycle is confirmed by the true residual of
+                  // the restart (compressed basis: x is assembled from it)
+  int conv_est;   // verify mode: the cycle that just ended converged by its estimate
+  int pad2;
   double beta;    // residual norm at the start of the cycle
   double bnorm;   // ||sigma g||
   double thresh;  // stopping threshold on the residual norm
@@ -219,41 +222,57 @@ __device__ __forceinline__ SegPos seg_pos(const HeatGeo& g, long long sidx, int 
   return p;
 }
 
-// Sum of v over the CTA, then over CTAs for each of `cnt` values stored at
-// partials[cta*kGmMax + i]; the last CTA returns true with totals in out[i].
-// (`vals` supplied one at a time through the lambda dot(i)).
+// Sum over the CTA, then over CTAs, of each of `cnt` per-thread values dot(i)
+// (per-CTA sums at partials[cta*kGmMax + i]); the last CTA returns true in
+// thread 0 with the totals in out[i].  Each dot is reduced within its warp by
+// shuffles only, so the loads of the next basis vector are not held behind a
+// barrier; one barrier then combines the warps.  Fixed order: deterministic.
 template <typename F>
 __device__ __forceinline__ bool multi_dot_reduce(int cnt, F dot, double* partials, unsigned* ticket, double* out) {
-  __shared__ double sred[32];
+  constexpr int kWarps = kThreads / 32;
+  __shared__ double swarp[kWarps][kGmMax + 1];
   __shared__ int am_last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i = 0; i < cnt; ++i) {
-    double v[1] = {dot(i)};
-    block_reduce<1, 0u>(v, sred);
-    if (threadIdx.x == 0) partials[(size_t)blockIdx.x * kGmMax + i] = v[0];
+    double v = dot(i);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (lane == 0) swarp[warp][i] = v;
   }
-  if (threadIdx.x == 0) {
+  __syncthreads();
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+    double a = 0.0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) a += swarp[w][i];
+    partials[(size_t)blockIdx.x * kGmMax + i] = a;
     __threadfence();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
     unsigned t = atomicAdd(ticket, 1u);
     am_last = (t == gridDim.x - 1);
   }
   __syncthreads();
   if (!am_last) return false;
   __threadfence();
-  for (int i = 0; i < cnt; ++i) {
-    double acc[1] = {0.0};
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) acc[0] += __ldcg(partials + (size_t)b * kGmMax + i);
-    block_reduce<1, 0u>(acc, sred);
-    if (threadIdx.x == 0) out[i] = acc[0];
+  // last CTA: warp w sums dots i = w, w + kWarps, ... over the CTAs
+  for (int i = warp; i < cnt; i += kWarps) {
+    double a = 0.0;
+    for (int b = lane; b < (int)gridDim.x; b += 32) a += __ldcg(partials + (size_t)b * kGmMax + i);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
+    if (lane == 0) out[i] = a;
   }
+  __syncthreads();
   if (threadIdx.x == 0) *ticket = 0u;
   return threadIdx.x == 0;
 }
 
-// Start of a solve from x = 0: V_0 <- sigma g (rounded to S, unnormalised),
+// Start of a solve from x = 0: V_0 <- sigma g (rounded to B, unnormalised),
 // x <- 0, beta = ||V_0||.
-template <typename S, typename T, int SEG>
+template <typename S, typename B, typename T, int SEG>
 __global__ void __launch_bounds__(kThreads) gm_start(HeatGeo g, const double* __restrict__ gv, const RhsScalars* rs,
-                                                     S* __restrict__ V0, typename XOf<S>::type* __restrict__ x,
+                                                     B* __restrict__ V0, typename XOf<S>::type* __restrict__ x,
                                                      GmScalars* sc, double* partials) {
   using X = typename XOf<S>::type;
   const double sigma = rs->sigma;
@@ -267,11 +286,11 @@ __global__ void __launch_bounds__(kThreads) gm_start(HeatGeo g, const double* __
     T v[SEG], zero[SEG];
 #pragma unroll
     for (int e = 0; e < SEG; ++e) {
-      v[e] = (e < m) ? rnd<S, T>((T)(gd[e] * sigma)) : T(0);
+      v[e] = (e < m) ? rnd<B, T>((T)(gd[e] * sigma)) : T(0);
       zero[e] = T(0);
       acc[0] += (double)(v[e] * v[e]);
     }
-    store_seg<S, T, SEG>(V0 + base, m, v);
+    store_seg<B, T, SEG>(V0 + base, m, v);
     store_seg<X, T, SEG>(x + base, m, zero);
   RK_SEG_LOOP_END
   double tot[1];
@@ -298,11 +317,11 @@ __global__ void __launch_bounds__(kThreads) gm_start(HeatGeo g, const double* __
 }
 
 // Restart: V_0 <- sigma g - (I - shift L) x, beta = ||V_0||.
-template <typename S, typename T, int SEG>
+template <typename S, typename B, typename T, int SEG>
 __global__ void __launch_bounds__(kThreads) gm_restart(HeatGeo g, CsrView A, const S* __restrict__ lv, T cs,
                                                        const double* __restrict__ gv, const RhsScalars* rs,
                                                        const typename XOf<S>::type* __restrict__ x,
-                                                       S* __restrict__ V0, GmScalars* sc, double* partials) {
+                                                       B* __restrict__ V0, GmScalars* sc, double* partials) {
   if (sc->done) return;
   const double sigma = rs->sigma;
   double acc[1] = {0.0};
@@ -316,15 +335,16 @@ __global__ void __launch_bounds__(kThreads) gm_restart(HeatGeo g, CsrView A, con
       v[e] = T(0);
       if (e < m) {
         const long long r = base + e;
-        v[e] = rnd<S, T>((T)(gv[r] * sigma) - shifted_row<T>(A, lv, r, x, cs));
+        v[e] = rnd<B, T>((T)(gv[r] * sigma) - shifted_row<T>(A, lv, r, x, cs));
         acc[0] += (double)(v[e] * v[e]);
       }
     }
-    store_seg<S, T, SEG>(V0 + base, m, v);
+    store_seg<B, T, SEG>(V0 + base, m, v);
   RK_SEG_LOOP_END
   double tot[1];
   if (grid_reduce<1, 0u>(acc, partials, &sc->ticket, tot)) {
     const double beta = sqrt(tot[0]);
+    const double prev = sc->beta;  // true residual at the start of the cycle that ended
     sc->beta = beta;
     sc->j = 0;
     sc->cycle_end = 0;
@@ -336,63 +356,68 @@ __global__ void __launch_bounds__(kThreads) gm_restart(HeatGeo g, CsrView A, con
       sc->status = 5;
     } else if (beta <= sc->thresh) {
       sc->done = 1;
+    } else if (sc->conv_est && beta > 0.5 * prev) {
+      // a cycle that converged by its estimate no longer halves the true
+      // residual: the attainable accuracy of the working precision is reached
+      sc->done = 1;
     }
+    sc->conv_est = 0;
   }
 }
 
 // Arnoldi step part 1: normalise V_j (lazily: it was stored unnormalised) and
 // z = D^{-1} V_j.
-template <typename S, typename T, int BS, int SEG>
-__global__ void __launch_bounds__(kThreads) gm_prec(HeatGeo g, S* __restrict__ V, long long ldv,
+template <typename S, typename B, typename T, int BS, int SEG>
+__global__ void __launch_bounds__(kThreads) gm_prec(HeatGeo g, B* __restrict__ V, long long ldv,
                                                     const S* __restrict__ minv, S* __restrict__ z, GmScalars* sc) {
   if (sc->done || sc->cycle_end) return;
   const int jj = sc->j;
   const T f = (T)(1.0 / (jj == 0 ? sc->beta : sc->hnext));
-  S* Vj = V + (long long)jj * ldv;
+  B* Vj = V + (long long)jj * ldv;
   const int nbl = (g.n + BS - 1) / BS;
   RK_SEG_LOOP(g, SEG)
     (void)j;
     (void)k;
     T v[SEG], zv[SEG];
-    load_seg<T, S, SEG>(Vj + base, m, v);
+    load_seg<T, B, SEG>(Vj + base, m, v);
 #pragma unroll
-    for (int e = 0; e < SEG; ++e) v[e] = (e < m) ? rnd<S, T>(v[e] * f) : T(0);
+    for (int e = 0; e < SEG; ++e) v[e] = (e < m) ? rnd<B, T>(v[e] * f) : T(0);
     bj_apply_blocks<T, S, BS, SEG>(minv, line, nbl, i0, v, zv);
-    store_seg<S, T, SEG>(Vj + base, m, v);
+    store_seg<B, T, SEG>(Vj + base, m, v);
     store_seg<S, T, SEG>(z + base, m, zv);
   RK_SEG_LOOP_END
 }
 
 // Arnoldi step part 2: w = (I - shift L) z written to V_{j+1}; h1_i = V_i . w
 // for i <= j (first Gram-Schmidt projection coefficients).
-template <typename S, typename T, int SEG, int R>
+template <typename S, typename B, typename T, int SEG, int R>
 __global__ void __launch_bounds__(kThreads) gm_spmv_dots(HeatGeo g, CsrView A, const S* __restrict__ lv, T cs,
-                                                         const S* __restrict__ z, S* __restrict__ V, long long ldv,
+                                                         const S* __restrict__ z, B* __restrict__ V, long long ldv,
                                                          GmScalars* sc, double* partials) {
   if (sc->done || sc->cycle_end) return;
   const int jj = sc->j;
   RK_GM_SEGS(g, SEG, R)
   T w[R][SEG];
   SegPos pos[R];
-  S* W = V + (long long)(jj + 1) * ldv;
+  B* W = V + (long long)(jj + 1) * ldv;
 #pragma unroll
   for (int q = 0; q < R; ++q) {
     pos[q] = seg_pos(g, tid_ + q * tthreads_, SEG);
 #pragma unroll
     for (int e = 0; e < SEG; ++e) {
       w[q][e] = T(0);
-      if (pos[q].valid && e < pos[q].m) w[q][e] = rnd<S, T>(shifted_row<T>(A, lv, pos[q].base + e, z, cs));
+      if (pos[q].valid && e < pos[q].m) w[q][e] = rnd<B, T>(shifted_row<T>(A, lv, pos[q].base + e, z, cs));
     }
-    if (pos[q].valid) store_seg<S, T, SEG>(W + pos[q].base, pos[q].m, w[q]);
+    if (pos[q].valid) store_seg<B, T, SEG>(W + pos[q].base, pos[q].m, w[q]);
   }
   auto dot = [&](int i) {
-    const S* Vi = V + (long long)i * ldv;
+    const B* Vi = V + (long long)i * ldv;
     T a = T(0);
 #pragma unroll
     for (int q = 0; q < R; ++q) {
       if (!pos[q].valid) continue;
       T vi[SEG];
-      load_seg<T, S, SEG>(Vi + pos[q].base, pos[q].m, vi);
+      load_seg<T, B, SEG>(Vi + pos[q].base, pos[q].m, vi);
 #pragma unroll
       for (int e = 0; e < SEG; ++e) a = fma(vi[e], w[q][e], a);
     }
@@ -403,20 +428,20 @@ __global__ void __launch_bounds__(kThreads) gm_spmv_dots(HeatGeo g, CsrView A, c
 
 // Arnoldi step part 3 (second CGS pass): w <- w - sum_i h1_i V_i, then
 // h2_i = V_i . w.
-template <typename S, typename T, int SEG, int R>
-__global__ void __launch_bounds__(kThreads) gm_orth(HeatGeo g, S* __restrict__ V, long long ldv, GmScalars* sc,
+template <typename S, typename B, typename T, int SEG, int R>
+__global__ void __launch_bounds__(kThreads) gm_orth(HeatGeo g, B* __restrict__ V, long long ldv, GmScalars* sc,
                                                     double* partials) {
   if (sc->done || sc->cycle_end) return;
   const int jj = sc->j;
   RK_GM_SEGS(g, SEG, R)
   T w[R][SEG];
   SegPos pos[R];
-  S* W = V + (long long)(jj + 1) * ldv;
+  B* W = V + (long long)(jj + 1) * ldv;
 #pragma unroll
   for (int q = 0; q < R; ++q) {
     pos[q] = seg_pos(g, tid_ + q * tthreads_, SEG);
     if (pos[q].valid) {
-      load_seg<T, S, SEG>(W + pos[q].base, pos[q].m, w[q]);
+      load_seg<T, B, SEG>(W + pos[q].base, pos[q].m, w[q]);
     } else {
 #pragma unroll
       for (int e = 0; e < SEG; ++e) w[q][e] = T(0);
@@ -424,12 +449,12 @@ __global__ void __launch_bounds__(kThreads) gm_orth(HeatGeo g, S* __restrict__ V
   }
   for (int i = 0; i <= jj; ++i) {
     const T hi = (T)sc->h1[i];
-    const S* Vi = V + (long long)i * ldv;
+    const B* Vi = V + (long long)i * ldv;
 #pragma unroll
     for (int q = 0; q < R; ++q) {
       if (!pos[q].valid) continue;
       T vi[SEG];
-      load_seg<T, S, SEG>(Vi + pos[q].base, pos[q].m, vi);
+      load_seg<T, B, SEG>(Vi + pos[q].base, pos[q].m, vi);
 #pragma unroll
       for (int e = 0; e < SEG; ++e) w[q][e] = fma(-hi, vi[e], w[q][e]);
     }
@@ -437,17 +462,17 @@ __global__ void __launch_bounds__(kThreads) gm_orth(HeatGeo g, S* __restrict__ V
 #pragma unroll
   for (int q = 0; q < R; ++q) {
 #pragma unroll
-    for (int e = 0; e < SEG; ++e) w[q][e] = (pos[q].valid && e < pos[q].m) ? rnd<S, T>(w[q][e]) : T(0);
-    if (pos[q].valid) store_seg<S, T, SEG>(W + pos[q].base, pos[q].m, w[q]);
+    for (int e = 0; e < SEG; ++e) w[q][e] = (pos[q].valid && e < pos[q].m) ? rnd<B, T>(w[q][e]) : T(0);
+    if (pos[q].valid) store_seg<B, T, SEG>(W + pos[q].base, pos[q].m, w[q]);
   }
   auto dot = [&](int i) {
-    const S* Vi = V + (long long)i * ldv;
+    const B* Vi = V + (long long)i * ldv;
     T a = T(0);
 #pragma unroll
     for (int q = 0; q < R; ++q) {
       if (!pos[q].valid) continue;
       T vi[SEG];
-      load_seg<T, S, SEG>(Vi + pos[q].base, pos[q].m, vi);
+      load_seg<T, B, SEG>(Vi + pos[q].base, pos[q].m, vi);
 #pragma unroll
       for (int e = 0; e < SEG; ++e) a = fma(vi[e], w[q][e], a);
     }
@@ -459,20 +484,20 @@ __global__ void __launch_bounds__(kThreads) gm_orth(HeatGeo g, S* __restrict__ V
 // Arnoldi step part 4: w <- w - sum_i h2_i V_i, ||w||; the last CTA forms the
 // Hessenberg column (h1 + h2, ||w||), applies the Givens rotations, tests
 // convergence and, at the end of a cycle, solves the triangular system.
-template <typename S, typename T, int SEG, int R>
-__global__ void __launch_bounds__(kThreads) gm_norm(HeatGeo g, S* __restrict__ V, long long ldv, GmScalars* sc,
+template <typename S, typename B, typename T, int SEG, int R>
+__global__ void __launch_bounds__(kThreads) gm_norm(HeatGeo g, B* __restrict__ V, long long ldv, GmScalars* sc,
                                                     double* partials) {
   if (sc->done || sc->cycle_end) return;
   const int jj = sc->j;
   RK_GM_SEGS(g, SEG, R)
   T w[R][SEG];
   SegPos pos[R];
-  S* W = V + (long long)(jj + 1) * ldv;
+  B* W = V + (long long)(jj + 1) * ldv;
 #pragma unroll
   for (int q = 0; q < R; ++q) {
     pos[q] = seg_pos(g, tid_ + q * tthreads_, SEG);
     if (pos[q].valid) {
-      load_seg<T, S, SEG>(W + pos[q].base, pos[q].m, w[q]);
+      load_seg<T, B, SEG>(W + pos[q].base, pos[q].m, w[q]);
     } else {
 #pragma unroll
       for (int e = 0; e < SEG; ++e) w[q][e] = T(0);
@@ -480,12 +505,12 @@ __global__ void __launch_bounds__(kThreads) gm_norm(HeatGeo g, S* __restrict__ V
   }
   for (int i = 0; i <= jj; ++i) {
     const T hi = (T)sc->h2[i];
-    const S* Vi = V + (long long)i * ldv;
+    const B* Vi = V + (long long)i * ldv;
 #pragma unroll
     for (int q = 0; q < R; ++q) {
       if (!pos[q].valid) continue;
       T vi[SEG];
-      load_seg<T, S, SEG>(Vi + pos[q].base, pos[q].m, vi);
+      load_seg<T, B, SEG>(Vi + pos[q].base, pos[q].m, vi);
 #pragma unroll
       for (int e = 0; e < SEG; ++e) w[q][e] = fma(-hi, vi[e], w[q][e]);
     }
@@ -495,10 +520,10 @@ __global__ void __launch_bounds__(kThreads) gm_norm(HeatGeo g, S* __restrict__ V
   for (int q = 0; q < R; ++q) {
 #pragma unroll
     for (int e = 0; e < SEG; ++e) {
-      w[q][e] = (pos[q].valid && e < pos[q].m) ? rnd<S, T>(w[q][e]) : T(0);
+      w[q][e] = (pos[q].valid && e < pos[q].m) ? rnd<B, T>(w[q][e]) : T(0);
       acc[0] += (double)(w[q][e] * w[q][e]);
     }
-    if (pos[q].valid) store_seg<S, T, SEG>(W + pos[q].base, pos[q].m, w[q]);
+    if (pos[q].valid) store_seg<B, T, SEG>(W + pos[q].base, pos[q].m, w[q]);
   }
   double tot[1];
   if (!grid_reduce<1, 0u>(acc, partials, &sc->ticket, tot)) return;
@@ -544,9 +569,11 @@ __global__ void __launch_bounds__(kThreads) gm_norm(HeatGeo g, S* __restrict__ V
     if (bad) {
       sc->done = 1;
       sc->status = 5;
-    } else if (conv || breakdown) {
+    } else if ((conv || breakdown) && !sc->verify) {
       sc->done = 1;
       sc->status = 0;
+    } else if (conv || breakdown) {
+      sc->conv_est = 1;  // the restart checks the true residual
     } else if (sc->iter >= sc->max_iter) {
       sc->done = 1;
       sc->status = 4;
@@ -555,8 +582,8 @@ __global__ void __launch_bounds__(kThreads) gm_norm(HeatGeo g, S* __restrict__ V
 }
 
 // End of cycle: x += D^{-1} (V y) (right preconditioning).
-template <typename S, typename T, int BS, int SEG>
-__global__ void __launch_bounds__(kThreads) gm_update(HeatGeo g, const S* __restrict__ V, long long ldv,
+template <typename S, typename B, typename T, int BS, int SEG>
+__global__ void __launch_bounds__(kThreads) gm_update(HeatGeo g, const B* __restrict__ V, long long ldv,
                                                       const S* __restrict__ minv,
                                                       typename XOf<S>::type* __restrict__ x, GmScalars* sc) {
   using X = typename XOf<S>::type;
@@ -572,7 +599,7 @@ __global__ void __launch_bounds__(kThreads) gm_update(HeatGeo g, const S* __rest
     for (int i = 0; i < ju; ++i) {
       const T yi = (T)sc->y[i];
       T vi[SEG];
-      load_seg<T, S, SEG>(V + (long long)i * ldv + base, m, vi);
+      load_seg<T, B, SEG>(V + (long long)i * ldv + base, m, vi);
 #pragma unroll
       for (int e = 0; e < SEG; ++e) u[e] = fma(yi, vi[e], u[e]);
     }

@@ -42,6 +42,12 @@ template <typename T> struct Tag { using type = T; };
 template <int V> struct IntC { static constexpr int value = V; };
 
 inline size_t dtype_size(int dt) { return dt == RK_F64 ? 8 : dt == RK_F32 ? 4 : 2; }
+
+// dtype of the GMRES basis: the storage type unless a compressed (BF16) basis
+// was asked for with FP32 storage.
+inline int basis_dtype(const rk_solver_desc& s) {
+  return (s.basis == RK_BF16 && s.storage == RK_F32) ? RK_BF16 : s.storage;
+}
 // bytes per element of the Krylov solution k^eps (FP32 when work vectors are 16-bit)
 inline size_t xsize(int dt) { return dt == RK_F64 ? 8 : 4; }
 

@@ -141,3 +141,43 @@ def test_nonfinite_state_reported(rk):
         with pytest.raises(rk.RKError) as e:
             rk.rk_step(p.h, 5e-4)
         assert e.value.status == rk.RK_ERR_NONFINITE
+
+
+@pytest.mark.parametrize("n,tol", [(16, 1e-6), (33, 1e-7)])
+def test_gmres_compressed_basis(rk, n, tol):
+    """FP32 GMRES with the Krylov basis stored in BF16 (FP32 arithmetic): the
+    solve still reaches the FP32 tolerance on the recursive residual and
+    agrees with the oracle's tight solution to the tolerance times a modest
+    factor; iterations may grow against the FP32 basis."""
+    shift = 4e-4
+    g = oracle_L(n) @ synth.gaussian_bump(n)
+    out = {}
+    for basis in (None, "bf16"):
+        p = rk.Problem(rk.problem_desc(op=rk.RK_OP_ADVDIFF_CSR, n=n, kappa_field=synth.kappa_field(n, seed=0),
+                                       vel=VEL),
+                       rk.solver_desc(krylov=rk.RK_KRYLOV_GMRES, restart=30, bj_block=8, tol_rel=tol,
+                                      storage="f32", max_iter=2000, basis=basis))
+        with p:
+            k = np.empty_like(g)
+            st = rk.rk_solve(p.h, shift, g, k)
+        out[basis] = (k, st.iters_total)
+    M = krylov.shifted(oracle_L(n), shift)
+    ref = krylov.gmres(lambda v: M @ v, krylov.BlockJacobi(M, n, 8).apply, g, restart=30, tol_rel=1e-13).x
+    e32, ebf = rel_l2(out[None][0], ref), rel_l2(out["bf16"][0], ref)
+    assert e32 < 50 * tol and ebf < 50 * tol, (e32, ebf)
+    assert out["bf16"][1] <= 2 * out[None][1] + 5
+
+
+def test_step_compressed_basis_within_fp32_bound(rk):
+    n, dt, steps = 24, 5e-4, 4
+    u0 = synth.gaussian_bump(n)
+    p = rk.Problem(rk.problem_desc(op=rk.RK_OP_ADVDIFF_CSR, n=n, kappa_field=synth.kappa_field(n, seed=0), vel=VEL),
+                   rk.solver_desc(krylov=rk.RK_KRYLOV_GMRES, restart=30, bj_block=8, tol_rel=1e-8, storage="f32",
+                                  max_iter=3000, correct=1, basis="bf16"),
+                   tableau="dirk3", u0=u0)
+    with p:
+        rk.rk_integrate(p.h, dt, steps, allow_not_converged=True)
+        u = p.state()
+    ref = dirk.integrate(u0, dt, steps, tableau.get("dirk3"), operators.CSROperator(n, oracle_L(n)),
+                         dirk.Solver("gmres", bs=8, tol_rel=1e-13))
+    assert rel_l2(u, ref) < 1e-6

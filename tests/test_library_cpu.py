@@ -90,6 +90,21 @@ def test_periodic_and_forcing_argument_checks_without_gpu(rk):
     assert create(rk.problem_desc(op=7, n=8), rk.solver_desc()) == rk.RK_ERR_ARG
 
 
+def test_compressed_basis_argument_checks_without_gpu(rk):
+    h = ctypes.c_void_p()
+    d = rk.problem_desc(op=rk.RK_OP_ADV_PERIODIC, n=8, vel=(1, 1, 1))
+
+    def create(s):
+        return rk._lib.rk_create_problem(ctypes.byref(d), ctypes.byref(s), None, ctypes.byref(h))
+
+    assert create(rk.solver_desc(krylov=rk.RK_KRYLOV_GMRES, storage="f64", basis="bf16")) == rk.RK_ERR_ARG
+    assert "basis" in rk.rk_last_error()
+    assert create(rk.solver_desc(krylov=rk.RK_KRYLOV_GMRES, storage="f32", basis="f16")) == rk.RK_ERR_ARG
+    heat = rk.problem_desc(n=8)
+    assert rk._lib.rk_create_problem(ctypes.byref(heat), ctypes.byref(rk.solver_desc(basis="bf16")), None,
+                                     ctypes.byref(h)) == rk.RK_ERR_ARG
+
+
 def test_package_tableaux_match_oracle(rk):
     """The library's tableau table and the oracle's are typed independently
     from the paper; they must agree."""
