@@ -178,15 +178,37 @@ __global__ void __launch_bounds__(kThreads) csr_bj_apply_f64io(HeatGeo g, const 
   RK_SEG_LOOP_END
 }
 
-// (I - shift L) applied to row r of a storage-precision vector:
-// x_r - (shift/lscale) sum_e Lhat_re x_c, Lhat = lscale * L stored in S.
-template <typename T, typename S, typename V>
-__device__ __forceinline__ T shifted_row(CsrView A, const S* __restrict__ lv, long long r, const V* __restrict__ x,
-                                         T cs) {
-  T s = T(0);
-  const int e1 = A.rowptr[r + 1];
-  for (int e = A.rowptr[r]; e < e1; ++e) s = fma(wid<T>(lv[e]), wid<T>(x[A.cols[e]]), s);
-  return fma(-cs, s, wid<T>(x[r]));
+// (I - shift L) applied to the m <= SEG consecutive rows base .. base+m-1 of
+// a storage-precision vector: x_r - (shift/lscale) sum_e Lhat_re x_c, with
+// Lhat = lscale * L stored in S.  The k-th entries of all rows are loaded together (k = 0 .. 6: the
+// operators assembled here have at most 7 entries per row; longer rows finish
+// in a plain loop), so the gathers of a segment are in flight at once instead
+// of one dependent row-pointer -> column -> x chain per row.  Per row the
+// entries are summed in column order.
+template <typename T, typename S, typename V, int SEG>
+__device__ __forceinline__ void shifted_seg(CsrView A, const S* __restrict__ lv, long long base, int m,
+                                            const V* __restrict__ x, T cs, T (&out)[SEG]) {
+  constexpr int kNnz = 7;
+  int rp[SEG + 1];
+#pragma unroll
+  for (int i = 0; i <= SEG; ++i) rp[i] = (i <= m) ? A.rowptr[base + i] : 0;
+  T s[SEG];
+#pragma unroll
+  for (int i = 0; i < SEG; ++i) s[i] = T(0);
+#pragma unroll
+  for (int k = 0; k < kNnz; ++k) {
+#pragma unroll
+    for (int i = 0; i < SEG; ++i) {
+      const int e = rp[i] + k;
+      if (i < m && e < rp[i + 1]) s[i] = fma(wid<T>(lv[e]), wid<T>(x[A.cols[e]]), s[i]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < SEG; ++i) {
+    if (i < m)
+      for (int e = rp[i] + kNnz; e < rp[i + 1]; ++e) s[i] = fma(wid<T>(lv[e]), wid<T>(x[A.cols[e]]), s[i]);
+    out[i] = (i < m) ? fma(-cs, s[i], wid<T>(x[base + i])) : T(0);
+  }
 }
 
 // ------------------------------------------------------------- GMRES kernels
@@ -329,13 +351,13 @@ __global__ void __launch_bounds__(kThreads) gm_restart(HeatGeo g, CsrView A, con
     (void)j;
     (void)k;
     (void)line;
-    T v[SEG];
+    T v[SEG], ax[SEG];
+    shifted_seg<T, S, typename XOf<S>::type, SEG>(A, lv, base, m, x, cs, ax);
 #pragma unroll
     for (int e = 0; e < SEG; ++e) {
       v[e] = T(0);
       if (e < m) {
-        const long long r = base + e;
-        v[e] = rnd<B, T>((T)(gv[r] * sigma) - shifted_row<T>(A, lv, r, x, cs));
+        v[e] = rnd<B, T>((T)(gv[base + e] * sigma) - ax[e]);
         acc[0] += (double)(v[e] * v[e]);
       }
     }
@@ -403,12 +425,15 @@ __global__ void __launch_bounds__(kThreads) gm_spmv_dots(HeatGeo g, CsrView A, c
 #pragma unroll
   for (int q = 0; q < R; ++q) {
     pos[q] = seg_pos(g, tid_ + q * tthreads_, SEG);
+    if (pos[q].valid) {
+      shifted_seg<T, S, S, SEG>(A, lv, pos[q].base, pos[q].m, z, cs, w[q]);
 #pragma unroll
-    for (int e = 0; e < SEG; ++e) {
-      w[q][e] = T(0);
-      if (pos[q].valid && e < pos[q].m) w[q][e] = rnd<B, T>(shifted_row<T>(A, lv, pos[q].base + e, z, cs));
+      for (int e = 0; e < SEG; ++e) w[q][e] = rnd<B, T>(w[q][e]);
+      store_seg<B, T, SEG>(W + pos[q].base, pos[q].m, w[q]);
+    } else {
+#pragma unroll
+      for (int e = 0; e < SEG; ++e) w[q][e] = T(0);
     }
-    if (pos[q].valid) store_seg<B, T, SEG>(W + pos[q].base, pos[q].m, w[q]);
   }
   auto dot = [&](int i) {
     const B* Vi = V + (long long)i * ldv;
