@@ -244,6 +244,7 @@ def workload_config(name, cfg):
     return {"workload": name, "grid": "%d^3" % cfg["n"], "dof": cfg["n"] ** 3, "kappa": cfg["kappa"],
             "tableau": cfg["tableau"], "dt": cfg["dt"], "krylov": "cg", "bj_block": cfg["bs"],
             "precond": cfg.get("precond", "bj"), "precond_fp64": "bj",
+            "initial_guess": "previous step's stage solution" if cfg.get("warm") else "zero",
             "tol_rel": cfg["tol"], "tol_rel_fp64": cfg["tol64"], "storage": cfg["storage"], "arith": "f32",
             "solution": "f32", "high_precision": "f64",
             "u0": "sine mode + 32 random modes (seed 0)", "l2": "working set > L2 (no flush needed)"}
@@ -502,6 +503,8 @@ def main():
                     help="skip the fast-diagonalization variant of a block-Jacobi workload")
     ap.add_argument("--bs", type=int, default=0, help="override the block-Jacobi block size")
     ap.add_argument("--tol", type=float, default=0.0, help="override the solver tolerance")
+    ap.add_argument("--warm", action="store_true",
+                    help="start every stage solve (mixed and FP64) from the previous step's solution")
     ap.add_argument("--batch", action="store_true", help="run the 512-problem batched workload instead")
     ap.add_argument("--batch-steps", type=int, default=50)
     ap.add_argument("--serve", type=int, default=0, help="run the serving workload with this many jobs instead")
@@ -524,6 +527,8 @@ def main():
         cfg["bs"] = args.bs
     if args.tol:
         cfg["tol"] = args.tol
+    if args.warm:
+        cfg["warm"] = True
     if args.impl == "reference":
         return run_reference(args, cfg)
 
@@ -559,7 +564,7 @@ def main():
     def make(storage, tol, correct, precond="bj"):
         return rk.Problem(rk.problem_desc(n=n, kappa=cfg["kappa"]),
                           rk.solver_desc(bj_block=cfg["bs"], tol_rel=tol, storage=storage, correct=correct,
-                                         max_iter=2000, precond=precond),
+                                         max_iter=2000, precond=precond, warm_start=cfg.get("warm", False)),
                           tableau=tab, u0=u0, stream=sptr)
 
     # ---------------- mixed-precision path, device-resident inputs

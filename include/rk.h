@@ -107,6 +107,11 @@ typedef struct {
   int basis;       /* GMRES Krylov basis dtype: 0 or the storage dtype = same as the
                       other Krylov vectors; RK_BF16 with RK_F32 storage = compressed
                       basis (BF16 vectors, FP32 arithmetic)                        */
+  int warm_start;  /* CG only: 1 = start every stage solve of rk_step/rk_integrate
+                      from the previous step's solution of the same stage (the
+                      stopping rule stays relative to ||rhs||); 0 = from zero, as
+                      the paper's description implies.  Not with RK_F16 storage
+                      (its right-hand sides are rescaled per solve)                */
 } rk_solver_desc;
 
 typedef struct {

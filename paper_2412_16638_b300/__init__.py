@@ -44,7 +44,7 @@ class rk_solver_desc(ctypes.Structure):
                 ("tol_rel", ctypes.c_double), ("tol_abs", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("storage", ctypes.c_int), ("arith", ctypes.c_int), ("correct", ctypes.c_int),
                 ("max_refine", ctypes.c_int), ("tol_true", ctypes.c_double), ("precond", ctypes.c_int),
-                ("basis", ctypes.c_int)]
+                ("basis", ctypes.c_int), ("warm_start", ctypes.c_int)]
 
 
 class rk_stats(ctypes.Structure):
@@ -150,7 +150,8 @@ def problem_desc(op=RK_OP_HEAT7, n=32, kappa=1.0, kappa_field=None, vel=(0.0, 0.
 
 
 def solver_desc(krylov=RK_KRYLOV_CG, restart=30, bj_block=8, tol_rel=1e-8, tol_abs=0.0, max_iter=1000,
-                storage="f32", arith=None, correct=None, max_refine=0, tol_true=0.0, precond="bj", basis=None):
+                storage="f32", arith=None, correct=None, max_refine=0, tol_true=0.0, precond="bj", basis=None,
+                warm_start=False):
     s = rk_solver_desc()
     st = DTYPES[storage] if isinstance(storage, str) else storage
     s.krylov, s.restart, s.bj_block = krylov, restart, bj_block
@@ -161,6 +162,7 @@ def solver_desc(krylov=RK_KRYLOV_CG, restart=30, bj_block=8, tol_rel=1e-8, tol_a
     s.max_refine, s.tol_true = max_refine, tol_true
     s.precond = PRECONDS[precond] if isinstance(precond, str) else precond
     s.basis = 0 if basis is None else (DTYPES[basis] if isinstance(basis, str) else basis)
+    s.warm_start = int(bool(warm_start))
     return s
 
 

@@ -332,8 +332,17 @@ static rk_status heat_cg_solve(rk_problem* p, double shift, const double* g64, R
       const double Ns = (double)p->N * sizeof(S);
       const int solve = ++p->solve_seq;
       const double Nx = (double)p->N * sizeof(X);
-      launch(p, K_CG_INIT, 8.0 * p->N + 2.0 * Ns + Nx,
-             [&] { ki<<<gi, kThreads, 0, p->st>>>(g, g64, rs, M, r, z, xs, p->sc, p->partials); });
+      const bool warm = p->sol.warm_start && slot < 8 && p->warm_valid[slot];
+      if (warm) {
+        auto kw = cg_init_warm<S, T, BS, SEG>;
+        launch(p, K_CG_INIT, 8.0 * p->N + 2.0 * Ns + Nx, [&] {
+          kw<<<grid_for((const void*)kw, work), kThreads, 0, p->st>>>(g, g64, rs, d, o, M, r, z, xs, p->sc,
+                                                                     p->partials);
+        });
+      } else {
+        launch(p, K_CG_INIT, 8.0 * p->N + 2.0 * Ns + Nx,
+               [&] { ki<<<gi, kThreads, 0, p->st>>>(g, g64, rs, M, r, z, xs, p->sc, p->partials); });
+      }
       if (fdm && (st = fdm_apply(p, shift, true, solve, 0)) != RK_OK) return;
       const bool tiled = tiled_setup<S, T, BS, SEG>(p);
       const TileGeo tg = tiled ? p->tiled->tg : TileGeo{};
@@ -402,6 +411,7 @@ static rk_status heat_cg_solve(rk_problem* p, double shift, const double* g64, R
   *iters = p->h_sc->iter;
   *status = p->h_sc->status;
   p->last_iters[slot] = p->h_sc->iter;
+  if (slot < 8) p->warm_valid[slot] = p->sol.warm_start && (*status == 0 || *status == 4);
   return RK_OK;
 }
 
@@ -632,6 +642,14 @@ static rk_status check_solver(const rk_solver_desc* s, const rk_problem_desc* d)
   }
   if (s->basis == RK_BF16 && s->storage == RK_F32 && s->krylov != RK_KRYLOV_GMRES) {
     set_error("a compressed basis applies to GMRES only");
+    return RK_ERR_ARG;
+  }
+  if (s->warm_start != 0 && s->warm_start != 1) {
+    set_error("warm_start must be 0 or 1");
+    return RK_ERR_ARG;
+  }
+  if (s->warm_start && (s->krylov != RK_KRYLOV_CG || s->storage == RK_F16)) {
+    set_error("warm_start is implemented for CG with FP64, FP32 or BF16 storage");
     return RK_ERR_ARG;
   }
   if (s->precond != RK_PREC_BLOCK_JACOBI && s->precond != RK_PREC_FDM) {
@@ -865,6 +883,7 @@ rk_status rk_set_tableau(rk_problem* p, int q, const double* A_hi, const double*
     }
   }
   p->q = q;
+  for (auto& v : p->warm_valid) v = false;  // stage slots change meaning
   std::memcpy(p->Ah, A_hi, sizeof(double) * q * q);
   std::memcpy(p->Al, A_lo, sizeof(double) * q * q);
   std::memcpy(p->b, b, sizeof(double) * q);

@@ -33,7 +33,7 @@ struct CgScalars {
   int done;        // 1: stop launching sweeps
   int status;      // 0 converged / running, 4 not converged, 5 non-finite/breakdown
   unsigned ticket;
-  int pad;
+  int warm;        // 1: the solve started from a nonzero x (x is read at iteration 0)
 };
 
 // Per-solve right-hand-side statistics written by heat_apply_f64 / vec_norms.
@@ -308,6 +308,65 @@ __device__ __forceinline__ void bj_apply(const T* sM, int n, int i0, const T (&r
   }
 }
 
+// Initialise from a nonzero guess x (the previous solve of the same stage,
+// storage with sigma = 1): r = g - (I - shift L) x (rounded to S),
+// z = D^{-1} r, and the first reductions r.z, r.r; the stopping threshold
+// stays relative to ||g|| (FP64, from the right-hand side's reduction).
+template <typename S, typename T, int BS, int SEG>
+__global__ void __launch_bounds__(kThreads) cg_init_warm(HeatGeo g, const double* __restrict__ gv,
+                                                         const RhsScalars* rs, T d, T o,
+                                                         const __grid_constant__ BjInv<T, BS> inv,
+                                                         S* __restrict__ r, S* __restrict__ z,
+                                                         const typename XOf<S>::type* __restrict__ x, CgScalars* sc,
+                                                         double* partials) {
+  using X = typename XOf<S>::type;
+  const T* sM = inv.m;
+  T rz = T(0), rr = T(0);
+  RK_SEG_LOOP(g, SEG)
+    T xv[SEG], nb[SEG];
+    load_seg<T, X, SEG>(x + base, m, xv);
+    nb_sum<T, SEG>(
+        g, i0, m, j, k, base, xv, [&](long long off, int mm, T (&v)[SEG]) { load_seg<T, X, SEG>(x + off, mm, v); },
+        [&](long long idx) { return wid<T>(x[idx]); }, nb);
+    double gd[SEG];
+    load_seg<double, double, SEG>(gv + base, m, gd);
+    T rv[SEG], zv[SEG];
+#pragma unroll
+    for (int e = 0; e < SEG; ++e) rv[e] = (e < m) ? rnd<S, T>((T)gd[e] - fma(d, xv[e], o * nb[e])) : T(0);
+    bj_apply<T, BS, SEG>(sM, g.n, i0, rv, zv);
+#pragma unroll
+    for (int e = 0; e < SEG; ++e) {
+      zv[e] = rnd<S, T>(zv[e]);
+      if (e < m) {
+        rz = fma(rv[e], zv[e], rz);
+        rr = fma(rv[e], rv[e], rr);
+      }
+    }
+    store_seg<S, T, SEG>(r + base, m, rv);
+    store_seg<S, T, SEG>(z + base, m, zv);
+  RK_SEG_LOOP_END
+  double acc[2] = {(double)rz, (double)rr};
+  double tot[2];
+  if (grid_reduce<2, 0u>(acc, partials, &sc->ticket, tot)) {
+    sc->rz = tot[0];
+    sc->rr = tot[1];
+    sc->gg = rs->gg;
+    const double ta = sc->tol_abs;
+    sc->thresh2 = fmax(sc->tol_rel * sc->tol_rel * rs->gg, ta * ta);
+    sc->iter = 0;
+    sc->beta = 0.0;
+    sc->warm = 1;
+    sc->done = 0;
+    sc->status = 0;
+    if (!isfinite(tot[0]) || !isfinite(tot[1])) {
+      sc->done = 1;
+      sc->status = 5;
+    } else if (tot[1] <= sc->thresh2) {
+      sc->done = 1;  // the guess already meets the tolerance
+    }
+  }
+}
+
 // Initialise: r = sigma*g (rounded to S), z = D^{-1} r, x = 0, and the first
 // reductions r.z, r.r.  g is the FP64 right-hand side.
 template <typename S, typename T, int BS, int SEG>
@@ -431,7 +490,7 @@ __global__ void __launch_bounds__(kThreads, 4) cg_sweep_b(HeatGeo g, T d, T o, c
   if (sc->done) return;
   const T* sM = inv.m;
   const T alpha = (T)sc->alpha;
-  const bool first = (sc->iter == 0);
+  const bool xzero = (sc->iter == 0) && !sc->warm;
   T rz = T(0), rr = T(0);  // per-thread partials in the arithmetic type
   RK_SEG_LOOP(g, SEG)
     T pv[SEG], nb[SEG];
@@ -441,7 +500,7 @@ __global__ void __launch_bounds__(kThreads, 4) cg_sweep_b(HeatGeo g, T d, T o, c
         [&](long long idx) { return wid<T>(p[idx]); }, nb);
     T rv[SEG], xv[SEG], zv[SEG];
     load_seg<T, S, SEG>(r + base, m, rv);
-    if (!first) {
+    if (!xzero) {
       load_seg<T, X, SEG>(x + base, m, xv);
     } else {
 #pragma unroll

@@ -223,6 +223,7 @@ struct rk_problem {
   rk::MinvEntry minv[8];
   int minv_next = 0;
   int last_iters[10]{};
+  bool warm_valid[10]{};  // slot holds a solution usable as the next initial guess
   bool has_state = false;
   // CSR path
   rk::Csr csr;

@@ -281,7 +281,7 @@ __global__ void __launch_bounds__(256, 2) cg_tiled_b(const __grid_constant__ CUt
   const int z0 = (int)((long long)zc * n / tg.nzc), z1 = (int)((long long)(zc + 1) * n / tg.nzc);
   const int L = z1 - z0 + 2;
   const T alpha = (T)sc->alpha;
-  const bool first = (sc->iter == 0);
+  const bool xzero = (sc->iter == 0) && !sc->warm;  // x = 0 at the first sweep of a cold start
   const uint32_t tx_bytes = (uint32_t)(R * n * sizeof(S));
   if (tid == 0) {
     for (int s = 0; s < kStagesB; ++s) mbar_init(&bar[s], 1);
@@ -301,7 +301,7 @@ __global__ void __launch_bounds__(256, 2) cg_tiled_b(const __grid_constant__ CUt
   // r and x of the first owned plane; later planes are fetched one plane ahead
   T rn[SEG], xn[SEG];
   load_seg<T, S, SEG>(r + (size_t)z0 * n * n + line_off, SEG, rn);
-  if (!first) {
+  if (!xzero) {
     load_seg<T, X, SEG>(x + (size_t)z0 * n * n + line_off, SEG, xn);
   } else {
 #pragma unroll
@@ -325,7 +325,7 @@ __global__ void __launch_bounds__(256, 2) cg_tiled_b(const __grid_constant__ CUt
       }
       if (k + 1 < z1) {
         load_seg<T, S, SEG>(r + (size_t)(k + 1) * n * n + line_off, SEG, rn);
-        if (!first) load_seg<T, X, SEG>(x + (size_t)(k + 1) * n * n + line_off, SEG, xn);
+        if (!xzero) load_seg<T, X, SEG>(x + (size_t)(k + 1) * n * n + line_off, SEG, xn);
       }
     }
     const int s = t % kStagesB;

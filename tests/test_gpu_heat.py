@@ -267,3 +267,47 @@ def test_nonfinite_state_reported(rk, storage, precond):
         rk.rk_integrate(p.h, 1e-3, 2)
         u = p.state()
     assert np.all(np.isfinite(u)) and rel_l2(u, u0) < 0.1
+
+
+@pytest.mark.parametrize("storage,precond,tol,bound", [("f64", "bj", 1e-12, 1e-10), ("f32", "bj", 1e-7, 1e-6),
+                                                       ("f32", "fdm", 1e-7, 1e-6), ("bf16", "bj", 1e-3, 5e-3)])
+def test_warm_start_parity_and_fewer_iterations(rk, storage, precond, tol, bound):
+    """Stage solves started from the previous step's solution of the same
+    stage: the same bound against the (cold-started) oracle, and no more
+    iterations than the cold-started library run."""
+    n, dt, steps = 40, 1e-3, 6
+    u0 = synth.heat_modes(seed=0).evaluate(n)
+    iters = {}
+    for warm in (False, True):
+        with make(rk, n, storage=storage, bs=8, tol=tol, tab="dirk3", u0=u0, max_iter=2000, precond=precond,
+                  warm_start=warm, correct=None if storage == "f64" else 1) as p:
+            st = rk.rk_integrate(p.h, dt, steps, allow_not_converged=True)
+            u = p.state()
+        iters[warm] = st.iters_total
+        ref = dirk.integrate(u0, dt, steps, tableau.get("dirk3"), operators.HeatOperator(n, 1.0),
+                             dirk.Solver("cg", bs=8, tol_rel=1e-13))
+        assert rel_l2(u, ref) < bound, (warm, rel_l2(u, ref))
+    # never more iterations; strictly fewer with block-Jacobi (the fast
+    # diagonalization needs 3 iterations per solve at 1e-7 either way)
+    assert iters[True] <= iters[False], iters
+    if precond == "bj":
+        assert iters[True] < iters[False], iters
+
+
+def test_warm_start_survives_state_and_tableau_changes(rk):
+    n = 24
+    u0 = synth.sine_mode(n)
+    with make(rk, n, storage="f32", bs=8, tol=1e-7, tab="sdirk2", u0=u0, warm_start=True) as p:
+        rk.rk_integrate(p.h, 1e-3, 3)
+        rk.rk_set_state(p.h, 2.0 * u0)  # a new state: the old solutions are only guesses
+        rk.rk_integrate(p.h, 1e-3, 2)
+        u = p.state()
+        rk.rk_set_tableau(p.h, *rk.tableaux.get("dirk3"))  # new stages: cold start again
+        rk.rk_integrate(p.h, 1e-3, 1)
+        v = p.state()
+    ref = dirk.integrate(2.0 * u0, 1e-3, 2, tableau.get("sdirk2"), operators.HeatOperator(n, 1.0),
+                         dirk.Solver("cg", bs=8, tol_rel=1e-13))
+    assert rel_l2(u, ref) < 1e-6
+    ref2 = dirk.integrate(ref, 1e-3, 1, tableau.get("dirk3"), operators.HeatOperator(n, 1.0),
+                          dirk.Solver("cg", bs=8, tol_rel=1e-13))
+    assert rel_l2(v, ref2) < 1e-6

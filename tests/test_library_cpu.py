@@ -105,6 +105,22 @@ def test_compressed_basis_argument_checks_without_gpu(rk):
                                      ctypes.byref(h)) == rk.RK_ERR_ARG
 
 
+def test_warm_start_argument_checks_without_gpu(rk):
+    h = ctypes.c_void_p()
+    d = rk.problem_desc(n=8)
+
+    def create(s, desc=d):
+        return rk._lib.rk_create_problem(ctypes.byref(desc), ctypes.byref(s), None, ctypes.byref(h))
+
+    assert create(rk.solver_desc(storage="f16", warm_start=True)) == rk.RK_ERR_ARG
+    assert "warm_start" in rk.rk_last_error()
+    per = rk.problem_desc(op=rk.RK_OP_ADV_PERIODIC, n=8, vel=(1, 1, 1))
+    assert create(rk.solver_desc(krylov=rk.RK_KRYLOV_GMRES, warm_start=True), per) == rk.RK_ERR_ARG
+    s = rk.solver_desc()
+    s.warm_start = 2
+    assert create(s) == rk.RK_ERR_ARG
+
+
 def test_package_tableaux_match_oracle(rk):
     """The library's tableau table and the oracle's are typed independently
     from the paper; they must agree."""
