@@ -107,3 +107,45 @@ def test_poll_reports_completion(rk):
         assert st.solves >= 1 and lat > 0
     finally:
         rk.rk_server_destroy(srv)
+
+
+def test_new_problem_kinds_same_alone_and_in_mix(rk):
+    """Jobs of every operator and solver option through the server -- periodic
+    advection (GMRES), heat with a forcing term, the tensor-core
+    fast-diagonalization preconditioner, a compressed GMRES basis -- mixed with
+    plain heat jobs: each result equals the same problem stepped alone."""
+    dt, steps = 1e-3, 3
+    beta = (1.0, 1.0, 1.0)
+    jobs = [
+        (rk.problem_desc(op=rk.RK_OP_ADV_PERIODIC, n=24, vel=beta),
+         rk.solver_desc(krylov=rk.RK_KRYLOV_GMRES, bj_block=8, tol_rel=1e-8, storage="f32", max_iter=2000),
+         "dirk3", synth.gaussian_bump_periodic(24)),
+        (rk.problem_desc(op=rk.RK_OP_ADV_PERIODIC, n=20, vel=beta),
+         rk.solver_desc(krylov=rk.RK_KRYLOV_GMRES, bj_block=8, tol_rel=1e-8, storage="f32", max_iter=2000,
+                        basis="bf16"),
+         "sdirk2", synth.gaussian_bump_periodic(20)),
+        (rk.problem_desc(n=32, kappa=1.0, source=synth.sine_mode(32)),
+         rk.solver_desc(bj_block=8, tol_rel=1e-7, storage="f32", max_iter=2000),
+         "sdirk2", np.zeros(32 ** 3)),
+        (rk.problem_desc(n=64, kappa=1.0),
+         rk.solver_desc(tol_rel=1e-7, storage="f32", max_iter=200, precond="fdm"),
+         "dirk3", synth.heat_modes(seed=5, n_random=4).evaluate(64)),
+        (rk.problem_desc(n=40, kappa=0.5),
+         rk.solver_desc(bj_block=8, tol_rel=1e-7, storage="f32", max_iter=2000),
+         "sdirk2", synth.heat_modes(seed=6, n_random=4).evaluate(40)),
+    ]
+    srv = rk.rk_server_create(8 << 30, 8)
+    try:
+        ids = [rk.rk_submit_job(srv, d, s, *rk.tableaux.get(t), u0, dt, steps) for d, s, t, u0 in jobs]
+        outs = []
+        for (d, s, t, u0), jid in zip(jobs, ids):
+            out = np.empty(d.n ** 3)
+            rk.rk_wait_job(srv, jid, out, allow_not_converged=True)
+            outs.append(out)
+    finally:
+        rk.rk_server_destroy(srv)
+    for (d, s, t, u0), out in zip(jobs, outs):
+        with rk.Problem(d, s, tableau=t, u0=u0) as p:
+            rk.rk_integrate(p.h, dt, steps, allow_not_converged=True)
+            ref = p.state()
+        assert rel_l2(out, ref) < 1e-6, (d.op, d.n)
