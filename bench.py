@@ -503,6 +503,7 @@ def main():
                     help="skip the fast-diagonalization variant of a block-Jacobi workload")
     ap.add_argument("--bs", type=int, default=0, help="override the block-Jacobi block size")
     ap.add_argument("--tol", type=float, default=0.0, help="override the solver tolerance")
+    ap.add_argument("--tol64", type=float, default=0.0, help="override the plain FP64 solver tolerance")
     ap.add_argument("--warm", action="store_true",
                     help="start every stage solve (mixed and FP64) from the previous step's solution")
     ap.add_argument("--batch", action="store_true", help="run the 512-problem batched workload instead")
@@ -527,6 +528,8 @@ def main():
         cfg["bs"] = args.bs
     if args.tol:
         cfg["tol"] = args.tol
+    if args.tol64:
+        cfg["tol64"] = args.tol64
     if args.warm:
         cfg["warm"] = True
     if args.impl == "reference":
