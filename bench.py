@@ -48,13 +48,13 @@ METRIC = "DOF*steps/s"
 # exact solve (profiles/heat256_tolerance_sweep.md); 1e-3 is also the
 # tolerance of the paper's accuracy study (Sec. 5.4).
 WORKLOADS = {
-    "heat256": dict(n=256, kappa=1.0, tableau="sdirk2", dt=1e-3, bs=8, tol=1e-3, tol64=1e-4, storage="f32"),
+    "heat256": dict(n=256, kappa=1.0, tableau="sdirk2", dt=1e-3, bs=8, tol=1e-3, tol64=3e-4, storage="f32"),
     "heat256-tight": dict(n=256, kappa=1.0, tableau="sdirk2", dt=1e-3, bs=8, tol=1e-6, tol64=1e-6, storage="f32"),
     "heat256-4s3pB": dict(n=256, kappa=1.0, tableau="4s3pB", dt=1e-3, bs=8, tol=1e-6, tol64=1e-6, storage="f32"),
-    "heat256-f16": dict(n=256, kappa=1.0, tableau="sdirk2", dt=1e-3, bs=8, tol=1e-3, tol64=1e-4, storage="f16"),
+    "heat256-f16": dict(n=256, kappa=1.0, tableau="sdirk2", dt=1e-3, bs=8, tol=1e-3, tol64=3e-4, storage="f16"),
     "heat128": dict(n=128, kappa=1.0, tableau="sdirk2", dt=1e-3, bs=8, tol=1e-3, tol64=1e-4, storage="f32"),
     # the fast-diagonalization preconditioner (tensor-core mode products) in place of block-Jacobi
-    "heat256-fdm": dict(n=256, kappa=1.0, tableau="sdirk2", dt=1e-3, bs=8, tol=1e-3, tol64=1e-4, storage="f32",
+    "heat256-fdm": dict(n=256, kappa=1.0, tableau="sdirk2", dt=1e-3, bs=8, tol=1e-3, tol64=3e-4, storage="f32",
                         precond="fdm"),
 }
 MATCH = 1.05  # matched error: within 5 % of the exact solve's error
