@@ -299,6 +299,7 @@ static rk_status heat_cg_solve(rk_problem* p, double shift, const double* g64, R
   init.max_iter = p->sol.max_iter;
   *p->h_sc = init;
   RK_CUDA(cudaMemcpyAsync(p->sc, p->h_sc, sizeof(CgScalars), cudaMemcpyHostToDevice, p->st));
+  const bool warm = p->sol.warm_start && slot < 8 && p->warm_valid[slot];
   rk_status st = RK_OK;
   dispatch_st(p->sol.storage, [&](auto ts, auto tt) {
     using S = typename decltype(ts)::type;
@@ -332,19 +333,22 @@ static rk_status heat_cg_solve(rk_problem* p, double shift, const double* g64, R
       const double Ns = (double)p->N * sizeof(S);
       const int solve = ++p->solve_seq;
       const double Nx = (double)p->N * sizeof(X);
-      const bool warm = p->sol.warm_start && slot < 8 && p->warm_valid[slot];
       if (warm) {
         auto kw = cg_init_warm<S, T, BS, SEG>;
         launch(p, K_CG_INIT, 8.0 * p->N + 2.0 * Ns + Nx, [&] {
           kw<<<grid_for((const void*)kw, work), kThreads, 0, p->st>>>(g, g64, rs, d, o, M, r, z, xs, p->sc,
                                                                      p->partials);
         });
-      } else {
-        launch(p, K_CG_INIT, 8.0 * p->N + 2.0 * Ns + Nx,
-               [&] { ki<<<gi, kThreads, 0, p->st>>>(g, g64, rs, M, r, z, xs, p->sc, p->partials); });
+      }
+      const bool tiled = tiled_setup<S, T, BS, SEG>(p);
+      if (!warm) {
+        // z and x are stored only where the first sweeps read them
+        const int store_zx = (tiled || fdm) ? 0 : 1;
+        launch(p, K_CG_INIT, 8.0 * p->N + (store_zx ? 2.0 * Ns + Nx : Ns), [&] {
+          ki<<<gi, kThreads, 0, p->st>>>(g, g64, rs, M, r, z, xs, p->sc, p->partials, store_zx);
+        });
       }
       if (fdm && (st = fdm_apply(p, shift, true, solve, 0)) != RK_OK) return;
-      const bool tiled = tiled_setup<S, T, BS, SEG>(p);
       const TileGeo tg = tiled ? p->tiled->tg : TileGeo{};
       const int tgrid = tg.nyt * tg.nzc, tthreads = tg.tpl * tg.ty, athreads = tg.tpl * (tg.ty + 2);
       const size_t sma = tiled ? tiled_smem_a<S, T, BS>(tg.n, tg.ty) : 0;
@@ -408,6 +412,9 @@ static rk_status heat_cg_solve(rk_problem* p, double shift, const double* g64, R
     });
   });
   if (st != RK_OK) return st;
+  // a solve that stops before its first sweep (zero or non-finite right-hand
+  // side) returns x = 0, which cg_init may have left unwritten
+  if (p->h_sc->iter == 0 && !warm) RK_CUDA(cudaMemsetAsync(x, 0, (size_t)p->N * xsize(p->sol.storage), p->st));
   *iters = p->h_sc->iter;
   *status = p->h_sc->status;
   p->last_iters[slot] = p->h_sc->iter;

@@ -15,13 +15,14 @@ __global__ void __launch_bounds__(kThreads) csr_apply_f64_kernel(CsrView A, cons
                                                                  double* __restrict__ y, RhsScalars* rs,
                                                                  double* partials) {
   double acc[2] = {0.0, 0.0};
+  const bool wmax = rs != nullptr && rs->want_scale;  // the max norm only sets the FP16 scale
   for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < N;
        r += (long long)gridDim.x * blockDim.x) {
     double s = f ? f[r] : 0.0;
     for (int e = A.rowptr[r]; e < A.rowptr[r + 1]; ++e) s = fma(vals[e], x[A.cols[e]], s);
     y[r] = s;
     acc[0] = fma(s, s, acc[0]);
-    acc[1] = fmax(acc[1], fabs(s));
+    if (wmax) acc[1] = fmax(acc[1], fabs(s));
   }
   if (rs == nullptr) return;
   double tot[2];

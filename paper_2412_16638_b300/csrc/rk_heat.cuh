@@ -39,7 +39,7 @@ struct CgScalars {
 // Per-solve right-hand-side statistics written by heat_apply_f64 / vec_norms.
 struct RhsScalars {
   double gg;     // ||g||_2^2 of the FP64 right-hand side
-  double gmax;   // ||g||_inf
+  double gmax;   // ||g||_inf (the FP64 operators reduce it only when want_scale)
   double sigma;  // storage scale (1/||g||_inf for FP16, else 1)
   double res2;   // ||true residual||^2 from the FP64 correction
   unsigned ticket;
@@ -108,6 +108,8 @@ __global__ void __launch_bounds__(kThreads) heat_apply_f64(HeatGeo g, const doub
                                                            const double* __restrict__ f, double* __restrict__ y,
                                                            double d, double o, RhsScalars* rs, double* partials) {
   double acc[2] = {0.0, 0.0};
+  // the max norm only sets the FP16 storage scale: skip its FP64 op otherwise
+  const bool wmax = rs != nullptr && rs->want_scale;
   RK_SEG_LOOP(g, SEG)
     double xv[SEG], nb[SEG];
     load_seg<double, double, SEG>(x + base, m, xv);
@@ -127,7 +129,7 @@ __global__ void __launch_bounds__(kThreads) heat_apply_f64(HeatGeo g, const doub
       yv[e] = fma(d, xv[e], fma(o, nb[e], fv[e]));
       if (e < m) {
         acc[0] = fma(yv[e], yv[e], acc[0]);
-        acc[1] = fmax(acc[1], fabs(yv[e]));
+        if (wmax) acc[1] = fmax(acc[1], fabs(yv[e]));
       }
     }
     store_seg<double, double, SEG>(y + base, m, yv);
@@ -368,13 +370,16 @@ __global__ void __launch_bounds__(kThreads) cg_init_warm(HeatGeo g, const double
 }
 
 // Initialise: r = sigma*g (rounded to S), z = D^{-1} r, x = 0, and the first
-// reductions r.z, r.r.  g is the FP64 right-hand side.
+// reductions r.z, r.r.  g is the FP64 right-hand side.  store_zx = 0 leaves z
+// and x unwritten, for callers whose first sweeps do not read them (the tiled
+// sweeps recompute z from r, the fast-diagonalization passes write z, and the
+// first sweep B starts x from zero without reading it).
 template <typename S, typename T, int BS, int SEG>
 __global__ void __launch_bounds__(kThreads) cg_init(HeatGeo g, const double* __restrict__ gv,
                                                     const RhsScalars* rs, const __grid_constant__ BjInv<T, BS> inv,
                                                     S* __restrict__ r, S* __restrict__ z,
                                                     typename XOf<S>::type* __restrict__ x, CgScalars* sc,
-                                                    double* partials) {
+                                                    double* partials, int store_zx = 1) {
   using X = typename XOf<S>::type;
   const T* sM = inv.m;
   const double sigma = rs->sigma;
@@ -398,8 +403,10 @@ __global__ void __launch_bounds__(kThreads) cg_init(HeatGeo g, const double* __r
       }
     }
     store_seg<S, T, SEG>(r + base, m, rv);
-    store_seg<S, T, SEG>(z + base, m, zv);
-    store_seg<X, T, SEG>(x + base, m, zero);
+    if (store_zx) {
+      store_seg<S, T, SEG>(z + base, m, zv);
+      store_seg<X, T, SEG>(x + base, m, zero);
+    }
   RK_SEG_LOOP_END
   double acc[2] = {(double)rz, (double)rr};
   double tot[2];

@@ -158,7 +158,7 @@ rk_status solve_bs(int n, double c, double shift, double tol_rel, double tol_abs
   auto ka = rk::cg_sweep_a<S, T, SEG>;
   auto kb = rk::cg_sweep_b<S, T, BS, SEG>;
   const int gi = grid_of((const void*)ki, work), ga = grid_of((const void*)ka, work), gb = grid_of((const void*)kb, work);
-  ki<<<gi, rk::kThreads, 0, st>>>(g, g_dev, rs, minv, r, z, x, sc, partials);
+  ki<<<gi, rk::kThreads, 0, st>>>(g, g_dev, rs, minv, r, z, x, sc, partials, 1);
   RK_CUDA(cudaGetLastError());
   rk::CgScalars hs{};
   int launched = 0, cur = 0, chunk = 8;
