@@ -8,6 +8,9 @@
 // grid are zero-filled by the TMA unit, which is exactly the homogeneous
 // Dirichlet boundary, so no boundary test is needed in the stencil.
 //
+// Sweep A marches down in z and sweep B up, so each starts on the planes that
+// the other wrote last, which are still in L2.
+//
 // Compared with the per-segment kernels, every input element is fetched from
 // global memory once per sweep (plus the y halo, shared with the neighbouring
 // tile through L2), and loads run two planes ahead of the arithmetic.  The
@@ -148,7 +151,7 @@ __global__ void __launch_bounds__(320, 2) cg_tiled_a(const __grid_constant__ CUt
   const int yt = blockIdx.x % tg.nyt, zc = blockIdx.x / tg.nyt;
   const int y0 = yt * TY;
   const int z0 = (int)((long long)zc * n / tg.nzc), z1 = (int)((long long)(zc + 1) * n / tg.nzc);
-  const int L = z1 - z0 + 2;  // planes z0-1 .. z1
+  const int L = z1 - z0 + 2;  // planes z1, z1-1, .. z0-1 (downwards: plane z1 - t at step t)
   const T beta = (T)sc->beta;
   const bool first = (sc->iter == 0);
   const uint32_t tx_bytes = (first ? 1u : 2u) * (uint32_t)(R * n * sizeof(S));
@@ -160,8 +163,8 @@ __global__ void __launch_bounds__(320, 2) cg_tiled_a(const __grid_constant__ CUt
   auto issue = [&](int t) {
     const int s = t % kStagesA;
     mbar_expect_tx(&bar[s], tx_bytes);
-    tma_load3(st_r(s), &tm_r, &bar[s], 0, y0 - 1, z0 - 1 + t);
-    if (!first) tma_load3(st_p(s), &tm_po, &bar[s], 0, y0 - 1, z0 - 1 + t);
+    tma_load3(st_r(s), &tm_r, &bar[s], 0, y0 - 1, z1 - t);
+    if (!first) tma_load3(st_p(s), &tm_po, &bar[s], 0, y0 - 1, z1 - t);
   };
   if (tid == 0)
     for (int t = 0; t < kStagesA && t < L; ++t) issue(t);
@@ -175,7 +178,7 @@ __global__ void __launch_bounds__(320, 2) cg_tiled_a(const __grid_constant__ CUt
   for (int t = 0; t < L; ++t) {
     const int s = t % kStagesA;
     const bool ok = mbar_wait(&bar[s], (uint32_t)((t / kStagesA) & 1));
-    // p on plane z0-1+t for the own line
+    // p on plane z1-t for the own line
     T pn[SEG];
     {
       T rv[SEG];
@@ -202,7 +205,7 @@ __global__ void __launch_bounds__(320, 2) cg_tiled_a(const __grid_constant__ CUt
       ++issued;
     }
     if (t >= 2 && owner) {
-      // q = A p on plane z0+t-2 (ring slot (t-1)%3), z neighbours from registers
+      // q = A p on plane z1-t+1 (ring slot (t-1)%3), z neighbours from registers
       const S* pc = ring((t - 1) % 3);
       T a[SEG], b[SEG];
       lds_seg<T, S, SEG>(pc + (size_t)(row - 1) * n + xs, a);
@@ -217,7 +220,7 @@ __global__ void __launch_bounds__(320, 2) cg_tiled_a(const __grid_constant__ CUt
         const T w = fma(d, pcur[e], o * nb);
         pw = fma(pcur[e], w, pw);
       }
-      const int k = z0 + t - 2;
+      const int k = z1 - t + 1;
       store_seg<S, T, SEG>(pnew + ((size_t)k * n + (y0 + row - 1)) * n + xs, SEG, pcur);
     }
 #pragma unroll
