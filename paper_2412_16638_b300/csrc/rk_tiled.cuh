@@ -86,6 +86,55 @@ __device__ __forceinline__ void tma_load3(void* dst, const CUtensorMap* map, uin
       : "memory");
 }
 
+// The same 3-D tile load with an L2 evict-first policy, for data that is dead
+// after this read.
+__device__ __forceinline__ void tma_load3_evict_first(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y,
+                                                      int z) {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1, {%3, "
+      "%4, %5}], [%2], %6;" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_addr(bar)), "r"(x), "r"(y), "r"(z), "l"(pol)
+      : "memory");
+}
+
+// Global segment load/store with the streaming (evict-first) cache policy, for
+// x, which the next CG iteration reads only after both sweeps have moved
+// 8 vectors through L2.  Falls back to the plain access when the segment is
+// not made of aligned 16-byte words.
+template <typename T, typename S, int SEG>
+__device__ __forceinline__ void ldcs_seg(const S* __restrict__ p, T (&v)[SEG]) {
+  constexpr int BYTES = SEG * (int)sizeof(S);
+  if constexpr (BYTES % 16 == 0) {
+    if ((reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+      alignas(16) S tmp[SEG];
+#pragma unroll
+      for (int w = 0; w < BYTES / 16; ++w) reinterpret_cast<uint4*>(tmp)[w] = __ldcs(reinterpret_cast<const uint4*>(p) + w);
+#pragma unroll
+      for (int e = 0; e < SEG; ++e) v[e] = wid<T>(tmp[e]);
+      return;
+    }
+  }
+  load_seg<T, S, SEG>(p, SEG, v);
+}
+
+template <typename S, typename T, int SEG>
+__device__ __forceinline__ void stcs_seg(S* __restrict__ p, const T (&v)[SEG]) {
+  constexpr int BYTES = SEG * (int)sizeof(S);
+  if constexpr (BYTES % 16 == 0) {
+    if ((reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+      alignas(16) S tmp[SEG];
+#pragma unroll
+      for (int e = 0; e < SEG; ++e) tmp[e] = nar<S>(v[e]);
+#pragma unroll
+      for (int w = 0; w < BYTES / 16; ++w) __stcs(reinterpret_cast<uint4*>(p) + w, reinterpret_cast<const uint4*>(tmp)[w]);
+      return;
+    }
+  }
+  store_seg<S, T, SEG>(p, SEG, v);
+}
+
 // Shared-memory segment load/store.  A 32-byte segment is moved as two
 // 16-byte halves; lanes with bit 2 set take the halves in the opposite order,
 // so each 8-lane phase touches all 32 banks once (no 2-way conflict between
@@ -164,7 +213,7 @@ __global__ void __launch_bounds__(320, 2) cg_tiled_a(const __grid_constant__ CUt
     const int s = t % kStagesA;
     mbar_expect_tx(&bar[s], tx_bytes);
     tma_load3(st_r(s), &tm_r, &bar[s], 0, y0 - 1, z1 - t);
-    if (!first) tma_load3(st_p(s), &tm_po, &bar[s], 0, y0 - 1, z1 - t);
+    if (!first) tma_load3_evict_first(st_p(s), &tm_po, &bar[s], 0, y0 - 1, z1 - t);  // p_old: last use
   };
   if (tid == 0)
     for (int t = 0; t < kStagesA && t < L; ++t) issue(t);
@@ -305,7 +354,7 @@ __global__ void __launch_bounds__(256, 2) cg_tiled_b(const __grid_constant__ CUt
   T rn[SEG], xn[SEG];
   load_seg<T, S, SEG>(r + (size_t)z0 * n * n + line_off, SEG, rn);
   if (!xzero) {
-    load_seg<T, X, SEG>(x + (size_t)z0 * n * n + line_off, SEG, xn);
+    ldcs_seg<T, X, SEG>(x + (size_t)z0 * n * n + line_off, xn);
   } else {
 #pragma unroll
     for (int e = 0; e < SEG; ++e) xn[e] = T(0);
@@ -328,7 +377,7 @@ __global__ void __launch_bounds__(256, 2) cg_tiled_b(const __grid_constant__ CUt
       }
       if (k + 1 < z1) {
         load_seg<T, S, SEG>(r + (size_t)(k + 1) * n * n + line_off, SEG, rn);
-        if (!xzero) load_seg<T, X, SEG>(x + (size_t)(k + 1) * n * n + line_off, SEG, xn);
+        if (!xzero) ldcs_seg<T, X, SEG>(x + (size_t)(k + 1) * n * n + line_off, xn);
       }
     }
     const int s = t % kStagesB;
@@ -360,7 +409,7 @@ __global__ void __launch_bounds__(256, 2) cg_tiled_b(const __grid_constant__ CUt
         rr = fma(rv[e], rv[e], rr);
       }
       store_seg<S, T, SEG>(r + (size_t)k * n * n + line_off, SEG, rv);
-      store_seg<X, T, SEG>(x + (size_t)k * n * n + line_off, SEG, xv);
+      stcs_seg<X, T, SEG>(x + (size_t)k * n * n + line_off, xv);
     }
 #pragma unroll
     for (int e = 0; e < SEG; ++e) {
