@@ -343,7 +343,7 @@ __global__ void __launch_bounds__(256, 2) cg_tiled_b(const __grid_constant__ CUt
   auto issue = [&](int t) {
     const int s = t % kStagesB;
     mbar_expect_tx(&bar[s], tx_bytes);
-    tma_load3(st(s), &tm_p, &bar[s], 0, y0 - 1, z0 - 1 + t);
+    tma_load3_evict_first(st(s), &tm_p, &bar[s], 0, y0 - 1, z0 - 1 + t);
   };
   if (tid == 0)
     for (int t = 0; t < kStagesB && t < L; ++t) issue(t);
