@@ -388,11 +388,15 @@ __global__ void __launch_bounds__(kThreads) cg_init(HeatGeo g, const double* __r
     double gd[SEG];
     load_seg<double, double, SEG>(gv + base, m, gd);
     T rv[SEG], zv[SEG], zero[SEG];
+    if (sigma == 1.0) {  // unscaled storage: no FP64 multiply (same values)
 #pragma unroll
-    for (int e = 0; e < SEG; ++e) {
-      rv[e] = (e < m) ? rnd<S, T>((T)(gd[e] * sigma)) : T(0);
-      zero[e] = T(0);
+      for (int e = 0; e < SEG; ++e) rv[e] = (e < m) ? rnd<S, T>((T)gd[e]) : T(0);
+    } else {
+#pragma unroll
+      for (int e = 0; e < SEG; ++e) rv[e] = (e < m) ? rnd<S, T>((T)(gd[e] * sigma)) : T(0);
     }
+#pragma unroll
+    for (int e = 0; e < SEG; ++e) zero[e] = T(0);
     bj_apply<T, BS, SEG>(sM, g.n, i0, rv, zv);
 #pragma unroll
     for (int e = 0; e < SEG; ++e) {
