@@ -355,7 +355,7 @@ static rk_status heat_cg_solve(rk_problem* p, double shift, const double* g64, R
       const size_t smb = tiled ? tiled_smem_b<S, T, BS>(tg.n, tg.ty) : 0;
       int launched = 0, cur = 0;
       const int predicted = p->last_iters[slot] > 0 ? p->last_iters[slot] : 8;
-      int chunk = std::max(2, predicted - 1);
+      int chunk = std::max(2, predicted);
       while (true) {
         for (int c = 0; c < chunk; ++c) {
           S* pn = static_cast<S*>(p->wp[cur]);
@@ -404,7 +404,8 @@ static rk_status heat_cg_solve(rk_problem* p, double shift, const double* g64, R
           set_error("CG did not stop after %d sweeps", launched);
           return;
         }
-        chunk = std::max(4, std::min(64, launched / 4));
+        // past the prediction: 2 more, then about doubling the overshoot
+        chunk = std::max(2, std::min(64, launched - predicted + 1));
         // while the solve runs every launched pair advances the device count
         // by one, so the ping-pong parity equals the device iteration parity
         cur = p->h_sc->iter & 1;
