@@ -237,13 +237,14 @@ static bool tiled_setup(rk_problem* p) {
   if (!enc) return false;
   const cuuint64_t dims[3] = {(cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)n};
   const cuuint64_t strides[2] = {(cuuint64_t)n * sizeof(S), (cuuint64_t)n * n * sizeof(S)};
-  const cuuint32_t box[3] = {(cuuint32_t)n, (cuuint32_t)(ty + 2), 1};
+  const cuuint32_t box_b[3] = {(cuuint32_t)n, (cuuint32_t)(ty + 2), 1};  // sweep B: a halo line on each side
+  const cuuint32_t box_a[3] = {(cuuint32_t)n, (cuuint32_t)(ty + 1), 1};  // sweep A: the line above
   const cuuint32_t estr[3] = {1, 1, 1};
-  void* bufs[4] = {p->wr, p->wp[0], p->wp[1], p->wz};
-  CUtensorMap* maps[4] = {&tm.r, &tm.p[0], &tm.p[1], &tm.z};
-  for (int i = 0; i < 4; ++i) {
-    if (enc(maps[i], tma_dtype<S>(), 3, bufs[i], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+  void* bufs[8] = {p->wr, p->wp[0], p->wp[1], p->wz, p->wr, p->wp[0], p->wp[1], p->wz};
+  CUtensorMap* maps[8] = {&tm.r, &tm.p[0], &tm.p[1], &tm.z, &tm.ra, &tm.pa[0], &tm.pa[1], &tm.za};
+  for (int i = 0; i < 8; ++i) {
+    if (enc(maps[i], tma_dtype<S>(), 3, bufs[i], dims, strides, i < 4 ? box_b : box_a, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return false;
   }
@@ -262,7 +263,7 @@ static bool tiled_setup(rk_problem* p) {
   });
   if (!attr_ok) return false;
   int occa = 0, occb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occa, ka, (ty + 2) * tpl, sa) != cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occa, ka, (ty + 1) * tpl, sa) != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occb, kb, ty * tpl, sb) != cudaSuccess) {
     cudaGetLastError();
     return false;
@@ -350,7 +351,7 @@ static rk_status heat_cg_solve(rk_problem* p, double shift, const double* g64, R
       }
       if (fdm && (st = fdm_apply(p, shift, true, solve, 0)) != RK_OK) return;
       const TileGeo tg = tiled ? p->tiled->tg : TileGeo{};
-      const int tgrid = tg.nyt * tg.nzc, tthreads = tg.tpl * tg.ty, athreads = tg.tpl * (tg.ty + 2);
+      const int tgrid = tg.nyt * tg.nzc, tthreads = tg.tpl * tg.ty, athreads = tg.tpl * (tg.ty + 1);
       const size_t sma = tiled ? tiled_smem_a<S, T, BS>(tg.n, tg.ty) : 0;
       const size_t smb = tiled ? tiled_smem_b<S, T, BS>(tg.n, tg.ty) : 0;
       int launched = 0, cur = 0;
@@ -364,9 +365,9 @@ static rk_status heat_cg_solve(rk_problem* p, double shift, const double* g64, R
           if (tiled) {
             // 8 vectors per iteration: A reads r, p_old, writes p; B reads p, r, x, writes r, x
             prof_begin(p, K_CG_A, (idx == 0 ? 2.0 : 3.0) * Ns, solve, idx);
-            cg_tiled_a<S, T, BS, SEG><<<tgrid, athreads, sma, p->st>>>(fdm ? p->tiled->z : p->tiled->r,
-                                                                       p->tiled->p[cur ^ 1], tg, d, o, tri, pn, p->sc,
-                                                                       p->partials);
+            cg_tiled_a<S, T, BS, SEG><<<tgrid, athreads, sma, p->st>>>(fdm ? p->tiled->za : p->tiled->ra,
+                                                                       p->tiled->pa[cur ^ 1], tg, d, o, tri, pn,
+                                                                       p->sc, p->partials);
             prof_end(p);
             prof_begin(p, K_CG_B, (idx == 0 ? 3.0 * Ns + Nx : 3.0 * Ns + 2.0 * Nx), solve, idx);
             cg_tiled_b<S, T, BS, SEG><<<tgrid, tthreads, smb, p->st>>>(p->tiled->p[cur], tg, d, o, tri, xs, r, p->sc,

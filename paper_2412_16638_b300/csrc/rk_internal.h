@@ -144,8 +144,9 @@ struct TiledMaps {
   bool ok = false;       // set up and usable
   bool tried = false;    // eligibility already decided
   TileGeo tg{};
-  CUtensorMap r, p[2];   // r and the two p buffers, box (n, ty+2, 1)
+  CUtensorMap r, p[2];   // r and the two p buffers, box (n, ty+2, 1) (sweep B)
   CUtensorMap z;         // z (the fast-diagonalization output), same box
+  CUtensorMap ra, pa[2], za;  // the same buffers with box (n, ty+1, 1) (sweep A)
 };
 
 // Fast-diagonalization preconditioner state of a heat problem (storage

@@ -2,8 +2,9 @@
 //
 // A CTA owns a tile of TY full x-lines (y0 .. y0+TY-1) and marches in z over
 // a chunk of planes.  For every plane one elected thread issues 3-D TMA tile
-// loads (cp.async.bulk.tensor) of (n x (TY+2) x 1) elements -- the tile plus
-// one halo line on each side in y -- into a ring of shared-memory stages,
+// loads (cp.async.bulk.tensor) of the tile plus its y halo -- one line on
+// each side for sweep B (n x (TY+2) x 1), the line above for sweep A
+// (n x (TY+1) x 1) -- into a ring of shared-memory stages,
 // completion tracked by an mbarrier per stage.  Tiles that reach outside the
 // grid are zero-filled by the TMA unit, which is exactly the homogeneous
 // Dirichlet boundary, so no boundary test is needed in the stencil.
@@ -174,12 +175,16 @@ __device__ __forceinline__ void sts_seg(S* p, const T (&v)[SEG]) {
 }
 
 // ----------------------------------------------------------------- sweep A
-// Thread rows 0..TY+1 each own one line of the (TY+2)-line tile (rows 0 and
-// TY+1 are the y halo).  Per plane: p = D^{-1} r + beta p_old for the own
-// line, kept in registers for the z neighbours and written to a 3-slot ring
-// for the y neighbours; the owned rows 1..TY then form q = A p for the
-// previous plane and the partial p.q, and write p.  One barrier per plane.
-// Last CTA: alpha = r.z / p.q.
+// Thread rows 0..TY each own one line of the (TY+1)-line tile y0..y0+TY (row
+// TY is the halo line above the tile).  The CTA marches down in z from plane
+// z1 (the halo plane above its chunk) to z0.  Per plane: p = D^{-1} r +
+// beta p_old for the own line, written to a 2-slot ring for the y neighbour;
+// after one barrier the owned rows write p and add their share of p.Ap.
+// p.Ap needs no full stencil: A = d I + o (sum of neighbours) is symmetric,
+// so p.Ap = sum_i p_i (d p_i + 2 o (p_{i+x} + p_{i+y} + p_{i+z})), every grid
+// edge counted once, from the element on its lower side (neighbours outside
+// the grid are zero).  Only the upper neighbours are needed: the halo is one
+// line and one plane.  Last CTA: alpha = r.z / p.Ap.
 template <typename S, typename T, int BS, int SEG>
 __global__ void __launch_bounds__(320, 2) cg_tiled_a(const __grid_constant__ CUtensorMap tm_r,
                                                   const __grid_constant__ CUtensorMap tm_po, TileGeo tg, T d, T o,
@@ -187,21 +192,22 @@ __global__ void __launch_bounds__(320, 2) cg_tiled_a(const __grid_constant__ CUt
                                                   CgScalars* sc, double* partials) {
   if (sc->done) return;
   extern __shared__ __align__(128) unsigned char smem[];
-  const int n = tg.n, TY = tg.ty, R = TY + 2;
+  const int n = tg.n, TY = tg.ty, R = TY + 1;
   const size_t tile = align128((size_t)R * n * sizeof(S));
   unsigned char* base = smem;
   auto st_r = [&](int s) { return reinterpret_cast<S*>(base + (size_t)s * 2 * tile); };
   auto st_p = [&](int s) { return reinterpret_cast<S*>(base + (size_t)s * 2 * tile + tile); };
   auto ring = [&](int s) { return reinterpret_cast<S*>(base + (size_t)kStagesA * 2 * tile + (size_t)s * tile); };
-  uint64_t* bar = reinterpret_cast<uint64_t*>(base + (size_t)(kStagesA * 2 + 3) * tile);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(base + (size_t)(kStagesA * 2 + 2) * tile);
   const int tid = threadIdx.x;
-  const int tx = tid % tg.tpl, row = tid / tg.tpl;  // row in 0..TY+1
-  const bool owner = row >= 1 && row <= TY;
+  const int tx = tid % tg.tpl, row = tid / tg.tpl;  // row in 0..TY
+  const bool owner = row < TY;
   const int yt = blockIdx.x % tg.nyt, zc = blockIdx.x / tg.nyt;
   const int y0 = yt * TY;
   const int z0 = (int)((long long)zc * n / tg.nzc), z1 = (int)((long long)(zc + 1) * n / tg.nzc);
-  const int L = z1 - z0 + 2;  // planes z1, z1-1, .. z0-1 (downwards: plane z1 - t at step t)
+  const int L = z1 - z0 + 1;  // planes z1, z1-1, .. z0 (downwards: plane z1 - t at step t)
   const T beta = (T)sc->beta;
+  const T o2 = o + o;
   const bool first = (sc->iter == 0);
   const uint32_t tx_bytes = (first ? 1u : 2u) * (uint32_t)(R * n * sizeof(S));
   if (tid == 0) {
@@ -212,17 +218,17 @@ __global__ void __launch_bounds__(320, 2) cg_tiled_a(const __grid_constant__ CUt
   auto issue = [&](int t) {
     const int s = t % kStagesA;
     mbar_expect_tx(&bar[s], tx_bytes);
-    tma_load3(st_r(s), &tm_r, &bar[s], 0, y0 - 1, z1 - t);
-    if (!first) tma_load3_evict_first(st_p(s), &tm_po, &bar[s], 0, y0 - 1, z1 - t);  // p_old: last use
+    tma_load3(st_r(s), &tm_r, &bar[s], 0, y0, z1 - t);
+    if (!first) tma_load3_evict_first(st_p(s), &tm_po, &bar[s], 0, y0, z1 - t);  // p_old: last use
   };
   if (tid == 0)
     for (int t = 0; t < kStagesA && t < L; ++t) issue(t);
   int issued = (kStagesA < L) ? kStagesA : L;
   const int xs = tx * SEG;
   T pw = T(0);
-  T pprev[SEG], pcur[SEG];
+  T pup[SEG];  // p of the own line one plane up (z + 1)
 #pragma unroll
-  for (int e = 0; e < SEG; ++e) pprev[e] = pcur[e] = T(0);
+  for (int e = 0; e < SEG; ++e) pup[e] = T(0);
   bool timed_out = false;
   for (int t = 0; t < L; ++t) {
     const int s = t % kStagesA;
@@ -241,7 +247,7 @@ __global__ void __launch_bounds__(320, 2) cg_tiled_a(const __grid_constant__ CUt
       }
 #pragma unroll
       for (int e = 0; e < SEG; ++e) pn[e] = rnd<S, T>(pn[e]);
-      sts_seg<S, T, SEG>(ring(t % 3) + (size_t)row * n + xs, pn);
+      sts_seg<S, T, SEG>(ring(t & 1) + (size_t)row * n + xs, pn);
     }
     if (__syncthreads_or(!ok)) {
       timed_out = true;
@@ -253,30 +259,25 @@ __global__ void __launch_bounds__(320, 2) cg_tiled_a(const __grid_constant__ CUt
       issue(issued);
       ++issued;
     }
-    if (t >= 2 && owner) {
-      // q = A p on plane z1-t+1 (ring slot (t-1)%3), z neighbours from registers
-      const S* pc = ring((t - 1) % 3);
-      T a[SEG], b[SEG];
-      lds_seg<T, S, SEG>(pc + (size_t)(row - 1) * n + xs, a);
-      lds_seg<T, S, SEG>(pc + (size_t)(row + 1) * n + xs, b);
-      const T left = (xs > 0) ? wid<T>(pc[(size_t)row * n + xs - 1]) : T(0);
+    if (t >= 1 && owner) {
+      // plane z1-t is owned: its edges to the line above (ring), to the next
+      // element in x and to the plane above (registers)
+      const S* pc = ring(t & 1);
+      T up[SEG];
+      lds_seg<T, S, SEG>(pc + (size_t)(row + 1) * n + xs, up);
       const T right = (xs + SEG < n) ? wid<T>(pc[(size_t)row * n + xs + SEG]) : T(0);
 #pragma unroll
       for (int e = 0; e < SEG; ++e) {
-        const T xl = (e > 0) ? pcur[e - 1] : left;
-        const T xr = (e + 1 < SEG) ? pcur[e + 1] : right;
-        const T nb = ((xl + xr) + (a[e] + b[e])) + (pprev[e] + pn[e]);
-        const T w = fma(d, pcur[e], o * nb);
-        pw = fma(pcur[e], w, pw);
+        const T xr = (e + 1 < SEG) ? pn[e + 1] : right;
+        const T nb = (xr + up[e]) + pup[e];
+        const T w = fma(d, pn[e], o2 * nb);
+        pw = fma(pn[e], w, pw);
       }
-      const int k = z1 - t + 1;
-      store_seg<S, T, SEG>(pnew + ((size_t)k * n + (y0 + row - 1)) * n + xs, SEG, pcur);
+      const int k = z1 - t;
+      store_seg<S, T, SEG>(pnew + ((size_t)k * n + (y0 + row)) * n + xs, SEG, pn);
     }
 #pragma unroll
-    for (int e = 0; e < SEG; ++e) {
-      pprev[e] = pcur[e];
-      pcur[e] = pn[e];
-    }
+    for (int e = 0; e < SEG; ++e) pup[e] = pn[e];
   }
   if (timed_out) {
     // let copies that are still in flight land before the CTA exits
@@ -461,7 +462,7 @@ __global__ void __launch_bounds__(256, 2) cg_tiled_b(const __grid_constant__ CUt
 // Shared-memory bytes of the two sweeps.
 template <typename S, typename T, int BS>
 __host__ constexpr size_t tiled_smem_a(int n, int ty) {
-  return (size_t)(kStagesA * 2 + 3) * align128((size_t)(ty + 2) * n * sizeof(S)) + 8 * kStagesA;
+  return (size_t)(kStagesA * 2 + 2) * align128((size_t)(ty + 1) * n * sizeof(S)) + 8 * kStagesA;
 }
 template <typename S, typename T, int BS>
 __host__ constexpr size_t tiled_smem_b(int n, int ty) {
