@@ -158,6 +158,17 @@ rk_status rk_integrate(rk_problem* p, double dt, int nsteps, rk_stats* stats);
 
 rk_status rk_destroy_problem(rk_problem* p);
 
+/* Failure detection: bound the polls of every bounded device wait in the main
+ * loops of this problem's TMA-fed CG sweeps (the waits for each shared-memory
+ * tile; a poll is one mbarrier try_wait).  0 restores the default bound of
+ * 2^24 polls.  When a wait runs out, the kernel lets its copies in flight land
+ * (always with the default bound), marks the solve and returns; the step then
+ * fails with RK_ERR_TIMEOUT, the state u_n is left as it was before the step
+ * and the problem stays usable.  Small values exist to exercise that path
+ * without a fault; the per-segment sweeps (shapes the TMA sweeps do not take)
+ * have no device waits.  Errors: RK_ERR_ARG. */
+rk_status rk_set_wait_limit(rk_problem* p, unsigned long long spins);
+
 /* ---- single operations of the step (for testing the kernels) ------------- */
 
 /* y = L x in FP64 (the explicit evaluation k = f(y) of Sec. 4.2, without the
@@ -210,6 +221,24 @@ rk_status rk_poll_job(rk_server* s, uint64_t job_id, int* done);
 rk_status rk_wait_job(rk_server* s, uint64_t job_id, double* u_out, rk_stats* stats,
                       double* latency_s);
 
+/* Timeline of a finished job, for checking how jobs shared the device.  Times
+ * are seconds since rk_server_create; a tick is one round in which the server
+ * launches one step of every resident job (the steps of one tick run
+ * concurrently on the device).  -1 where the job never got that far. */
+typedef struct {
+  double t_submit;       /* rk_submit_job returned                             */
+  double t_admit;        /* admitted: a slot and budget were free              */
+  double t_first_step;   /* the tick of its first step started                 */
+  double t_done;         /* finished (result copied to the host)               */
+  long long first_tick;  /* first and last tick in which the job was stepped   */
+  long long last_tick;
+  int steps;             /* steps completed                                    */
+} rk_job_info;
+
+/* rk_wait_job, and the job's timeline into info (may be NULL).  Frees the job. */
+rk_status rk_wait_job_info(rk_server* s, uint64_t job_id, double* u_out, rk_stats* stats,
+                           rk_job_info* info);
+
 rk_status rk_server_destroy(rk_server* s);
 
 /* ---- profiling: CUDA events around every kernel launch of a problem ------ */
@@ -244,12 +273,18 @@ rk_status rk_profile_read(rk_problem* p, rk_kernel_stat* out, int max, int* coun
  * (blocks of bj_block x-nodes), tolerances and iteration cap as in
  * rk_solver_desc, from k = 0.  g_dev and k_dev are caller-owned device arrays of
  * n^3 float64; *iters (may be NULL) receives the iteration count.
- * The workspace is a fixed device array inside the library (about 5.3 MB on
- * every GPU that loads it, kept until the process exits), so n is limited to
- * 1..64; larger n returns RK_ERR_ARG with an explanation.  The first call on a
- * device looks up the array's address (cudaGetSymbolAddress); make it before
- * any stream capture.  All calls share the array: calls that overlap on the
- * GPU race and must be serialised by the caller.  Synchronous on cuda_stream.
+ * The workspace is a fixed device array inside the library (about 5.3 MB), so n
+ * is limited to 1..64; larger n returns RK_ERR_ARG with an explanation.  The
+ * CUDA runtime places that array (with the library's device code) on a device
+ * at its first use there: the FIRST call on a device takes those 5.3 MB and can
+ * fail with RK_ERR_CUDA (out of memory) on a full device, so make it before a
+ * pool claims the device's memory (or set CUDA_MODULE_LOADING=EAGER); the array
+ * then stays until the process exits and later calls allocate nothing.  Every
+ * call looks up the array's address on the current device.  The call is
+ * synchronous (it reads the solver status back between chunks of sweeps) and
+ * must not be made while any stream is being captured.  All calls share the
+ * array: calls that overlap on the GPU race and must be serialised by the
+ * caller.  No counterpart in the paper.
  * Errors: RK_ERR_ARG, RK_ERR_CUDA, RK_ERR_NOT_CONVERGED, RK_ERR_NONFINITE. */
 rk_status rk_heat_solve_noalloc(int n, double kappa, double shift, int bj_block, double tol_rel,
                                 double tol_abs, int max_iter, const double* g_dev, double* k_dev,

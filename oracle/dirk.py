@@ -22,6 +22,8 @@ k^eps_i directly as k_i (no extra operator application).
 """
 from __future__ import annotations
 
+import weakref
+
 import numpy as np
 
 from . import fdm, krylov
@@ -36,18 +38,21 @@ class Solver:
         self.method, self.bs, self.precond = method, bs, precond
         self.tol_rel, self.tol_abs = tol_rel, tol_abs
         self.max_iter, self.restart = max_iter, restart
-        self._cache = {}
+        # preconditioners per operator object and shift; an entry disappears
+        # with its operator, so a later operator never meets a stale one
+        self._cache = weakref.WeakKeyDictionary()
 
     def solve(self, op, s, g):
         """Solve (I - s L) k = g."""
-        key = (id(op), float(s))
-        if key not in self._cache:
+        per_op = self._cache.setdefault(op, {})
+        key = (float(s), self.precond, self.bs)
+        if key not in per_op:
             if self.precond == "fdm":
-                self._cache[key] = fdm.FastDiagonalization(op.n, op.kappa, s).apply
+                per_op[key] = fdm.FastDiagonalization(op.n, op.kappa, s).apply
             else:
                 M = krylov.shifted(op.csr(), s)
-                self._cache[key] = krylov.BlockJacobi(M, op.n, self.bs).apply
-        apply_M = self._cache[key]
+                per_op[key] = krylov.BlockJacobi(M, op.n, self.bs).apply
+        apply_M = per_op[key]
         apply_A = lambda v: v - s * op.apply(v)
         if self.method == "cg":
             return krylov.pcg(apply_A, apply_M, g, self.tol_rel, self.tol_abs, self.max_iter)

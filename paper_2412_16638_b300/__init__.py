@@ -56,6 +56,15 @@ class rk_stats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class rk_job_info(ctypes.Structure):
+    _fields_ = [("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_first_step", ctypes.c_double),
+                ("t_done", ctypes.c_double), ("first_tick", ctypes.c_longlong), ("last_tick", ctypes.c_longlong),
+                ("steps", ctypes.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class rk_kernel_stat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_longlong), ("noop_launches", ctypes.c_longlong),
                 ("ms_total", ctypes.c_double), ("bytes_total", ctypes.c_double)]
@@ -73,6 +82,7 @@ _SIGS = {
     "rk_step": [_P, _D, ctypes.POINTER(rk_stats)],
     "rk_integrate": [_P, _D, _I, ctypes.POINTER(rk_stats)],
     "rk_destroy_problem": [_P],
+    "rk_set_wait_limit": [_P, ctypes.c_ulonglong],
     "rk_apply_op": [_P, _P, _P, _I],
     "rk_solve": [_P, _D, _P, _P, _I, ctypes.POINTER(rk_stats)],
     "rk_apply_precond": [_P, _D, _P, _P, _I],
@@ -82,6 +92,7 @@ _SIGS = {
                       _DP, _D, _I, ctypes.POINTER(ctypes.c_uint64)],
     "rk_poll_job": [_P, ctypes.c_uint64, ctypes.POINTER(_I)],
     "rk_wait_job": [_P, ctypes.c_uint64, _P, ctypes.POINTER(rk_stats), _DP],
+    "rk_wait_job_info": [_P, ctypes.c_uint64, _P, ctypes.POINTER(rk_stats), ctypes.POINTER(rk_job_info)],
     "rk_server_destroy": [_P],
     "rk_profile": [_P, _I],
     "rk_heat_solve_noalloc": [_I, _D, _D, _I, _D, _D, _I, _P, _P, _P, ctypes.POINTER(_I)],
@@ -209,6 +220,10 @@ def rk_destroy_problem(p):
     return _check(_lib.rk_destroy_problem(p))
 
 
+def rk_set_wait_limit(p, spins):
+    return _check(_lib.rk_set_wait_limit(p, int(spins)))
+
+
 def rk_apply_op(p, x, y):
     px, dx, kx = _f64_ptr(x)
     py, dy, ky = _f64_ptr(y)
@@ -271,6 +286,16 @@ def rk_wait_job(server, job_id, u_out=None, allow_not_converged=False):
     ptr = u_out.ctypes.data_as(_P) if u_out is not None else _P(0)
     _check(_lib.rk_wait_job(server, job_id, ptr, ctypes.byref(s), ctypes.byref(lat)), _allow(allow_not_converged))
     return s, lat.value
+
+
+def rk_wait_job_info(server, job_id, u_out=None, allow_not_converged=False):
+    """rk_wait_job that also returns the job's timeline (rk_job_info)."""
+    s = rk_stats()
+    info = rk_job_info()
+    ptr = u_out.ctypes.data_as(_P) if u_out is not None else _P(0)
+    _check(_lib.rk_wait_job_info(server, job_id, ptr, ctypes.byref(s), ctypes.byref(info)),
+           _allow(allow_not_converged))
+    return s, info
 
 
 def rk_server_destroy(server):

@@ -182,8 +182,8 @@ rk_status op_correct_f64(rk_problem* p, double shift, const double* gv, const vo
   constexpr int SEG = 4;
   HeatGeo g = heat_geo(p, SEG);
   rk_status st = RK_OK;
-  dispatch_st(p->sol.storage, [&](auto ts, auto) {
-    using X = typename XOf<typename decltype(ts)::type>::type;
+  dispatch_ke(p->ke_hi, p->sol.storage, [&](auto tx) {
+    using X = typename decltype(tx)::type;
     auto kern = heat_correct_f64<X, SEG>;
     int grid = grid_for((const void*)kern, g.n2 * g.nseg);
     launch(p, K_CORRECT, (16.0 + sizeof(X)) * p->N, [&] {
@@ -298,6 +298,7 @@ static rk_status heat_cg_solve(rk_problem* p, double shift, const double* g64, R
   init.tol_rel = p->sol.tol_rel;
   init.tol_abs = p->sol.tol_abs;
   init.max_iter = p->sol.max_iter;
+  init.wait_spins = p->wait_spins;
   *p->h_sc = init;
   RK_CUDA(cudaMemcpyAsync(p->sc, p->h_sc, sizeof(CgScalars), cudaMemcpyHostToDevice, p->st));
   const bool warm = p->sol.warm_start && slot < 8 && p->warm_valid[slot];
@@ -436,8 +437,8 @@ rk_status krylov_solve(rk_problem* p, double shift, const double* g64, RhsScalar
 
 static rk_status launch_combine(rk_problem* p, const CombineArgs& a) {
   rk_status st = RK_OK;
-  dispatch_st(p->sol.storage, [&](auto ts, auto) {
-    using S = typename XOf<typename decltype(ts)::type>::type;
+  dispatch_ke(p->ke_hi, p->sol.storage, [&](auto tx) {
+    using S = typename decltype(tx)::type;
     auto kern = combine_f64<S>;
     int grid = grid_for((const void*)kern, a.N);
     const double bytes = (double)a.N * ((a.u ? 8.0 : 0.0) + 8.0 * a.nh + (double)sizeof(S) * a.ne + 8.0);
@@ -454,6 +455,18 @@ static rk_status launch_typed(rk_problem* p, F&& f) {
   dispatch_st(p->sol.storage, [&](auto ts, auto) {
     using X = typename XOf<typename decltype(ts)::type>::type;
     f(Tag<X>{});
+    if (cudaGetLastError() != cudaSuccess) st = RK_ERR_CUDA;
+  });
+  if (st != RK_OK) set_error("kernel launch failed");
+  return st;
+}
+
+// The same with the type of k^eps (FP64 when the problem refines its solves).
+template <typename F>
+static rk_status launch_ke(rk_problem* p, F&& f) {
+  rk_status st = RK_OK;
+  dispatch_ke(p->ke_hi, p->sol.storage, [&](auto tx) {
+    f(tx);
     if (cudaGetLastError() != cudaSuccess) st = RK_ERR_CUDA;
   });
   if (st != RK_OK) set_error("kernel launch failed");
@@ -505,7 +518,9 @@ rk_status step_impl(rk_problem* p, double dt, rk_stats* acc) {
     RhsScalars* rs = p->rs + i;
     RK_TRY(op_apply_f64(p, rp, p->g64, rs, p->src));  // g = L r_i + f (FP64) + norms + scale
     int iters = 0, status = 0;
-    RK_TRY(krylov_solve(p, shift, p->g64, rs, p->ke[i], i, &iters, &status));
+    // with an FP64 k^eps the solver writes its own solution type into wx
+    void* xsol = p->ke_hi ? p->wx : p->ke[i];
+    RK_TRY(krylov_solve(p, shift, p->g64, rs, xsol, i, &iters, &status));
     if (acc) {
       acc->iters_total += iters;
       acc->iters_max = std::max(acc->iters_max, iters);
@@ -522,23 +537,44 @@ rk_status step_impl(rk_problem* p, double dt, rk_stats* acc) {
     }
     if (status == 4) worst = RK_ERR_NOT_CONVERGED;
     if (mixed) {
+      if (p->ke_hi) {
+        RK_TRY(launch_typed(p, [&](auto ts) {
+          using X = typename decltype(ts)::type;
+          auto kern = widen_keep_f64<X>;
+          launch(p, K_WIDEN, (8.0 + sizeof(X)) * p->N, [&] {
+            kern<<<grid_for((const void*)kern, p->N), kThreads, 0, p->st>>>(static_cast<const X*>(p->wx),
+                                                                             static_cast<double*>(p->ke[i]), p->N);
+          });
+        }));
+      }
       // k_i = L y_i, y_i = r_i + shift k^eps_i, in FP64; true residual
       RK_TRY(op_correct_f64(p, shift, p->g64, p->ke[i], p->k[i], rs));
-      for (int it = 0; it < p->sol.max_refine && p->sol.tol_true > 0.0; ++it) {
+      // Refinement against the FP64 true residual res = k_i - k^eps_i of the
+      // stage system: solve (I - shift L) delta = res in the solver's
+      // precision and add delta to k^eps in FP64, until the relative true
+      // residual is at most tol_true; still above it after max_refine
+      // refinements: not converged (the state stays valid).
+      for (int it = 0; p->sol.tol_true > 0.0; ++it) {
         RK_CUDA(cudaMemcpyAsync(p->h_rs + i, rs, sizeof(RhsScalars), cudaMemcpyDeviceToHost, p->st));
         RK_CUDA(cudaStreamSynchronize(p->st));
         const double rel = std::sqrt(p->h_rs[i].res2 / std::max(p->h_rs[i].gg, 1e-300));
         if (!(rel > p->sol.tol_true)) break;
-        // refinement: solve (I - shift L) delta = res, k^eps += delta
+        if (it >= p->sol.max_refine) {
+          set_error("stage %d: FP64 true residual %.3e above tol_true %.3e after %d refinements", i, rel,
+                    p->sol.tol_true, it);
+          if (acc) acc->not_converged += 1;
+          worst = RK_ERR_NOT_CONVERGED;
+          break;
+        }
         if (!p->res64) RK_TRY(alloc_dev(p, (void**)&p->res64, (size_t)p->N * 8));
         if (!p->wdelta) RK_TRY(alloc_dev(p, &p->wdelta, (size_t)p->N * xsize(p->sol.storage)));
         RhsScalars* rsd = p->rs + 9;
-        RK_TRY(launch_typed(p, [&](auto ts) {
-          using S = typename decltype(ts)::type;
-          auto kern = true_residual_f64<S>;
-          launch(p, K_TRUERES, (16.0 + sizeof(S)) * p->N, [&] {
+        RK_TRY(launch_ke(p, [&](auto tk) {
+          using K = typename decltype(tk)::type;
+          auto kern = true_residual_f64<K>;
+          launch(p, K_TRUERES, (16.0 + sizeof(K)) * p->N, [&] {
             kern<<<grid_for((const void*)kern, p->N), kThreads, 0, p->st>>>(
-                p->k[i], static_cast<const S*>(p->ke[i]), rs, p->res64, p->N);
+                p->k[i], static_cast<const K*>(p->ke[i]), rs, p->res64, p->N);
           });
         }));
         {
@@ -550,18 +586,27 @@ rk_status step_impl(rk_problem* p, double dt, rk_stats* acc) {
         }
         int it2 = 0, st2 = 0;
         RK_TRY(krylov_solve(p, shift, p->res64, rsd, p->wdelta, 8, &it2, &st2));
+        if (st2 == 5 || st2 == 6) {
+          set_error("stage %d refinement solve failed (status %d)", i, st2);
+          return st2 == 5 ? RK_ERR_NONFINITE : RK_ERR_TIMEOUT;
+        }
         if (acc) {
           acc->iters_total += it2;
           acc->refinements += 1;
         }
-        RK_TRY(launch_typed(p, [&](auto ts) {
-          using S = typename decltype(ts)::type;
-          auto kern = add_scaled_inplace<S>;
-          launch(p, K_ADDSCALED, 3.0 * sizeof(S) * p->N, [&] {
-            kern<<<grid_for((const void*)kern, p->N), kThreads, 0, p->st>>>(
-                static_cast<S*>(p->ke[i]), static_cast<const S*>(p->wdelta), rs, rsd, p->N);
+        rk_status ast = RK_OK;
+        dispatch_ke(p->ke_hi, p->sol.storage, [&](auto tk) {
+          using K = typename decltype(tk)::type;
+          ast = launch_typed(p, [&](auto ts) {
+            using D = typename decltype(ts)::type;
+            auto kern = add_scaled_inplace<K, D>;
+            launch(p, K_ADDSCALED, (2.0 * sizeof(K) + sizeof(D)) * p->N, [&] {
+              kern<<<grid_for((const void*)kern, p->N), kThreads, 0, p->st>>>(
+                  static_cast<K*>(p->ke[i]), static_cast<const D*>(p->wdelta), rs, rsd, p->N);
+            });
           });
-        }));
+        });
+        RK_TRY(ast);
         RK_TRY(op_correct_f64(p, shift, p->g64, p->ke[i], p->k[i], rs));
       }
     } else if (!p->ke_alias[i]) {
@@ -657,6 +702,10 @@ static rk_status check_solver(const rk_solver_desc* s, const rk_problem_desc* d)
     set_error("warm_start must be 0 or 1");
     return RK_ERR_ARG;
   }
+  if (s->warm_start && s->correct && s->storage != RK_F64 && s->max_refine > 0 && s->tol_true > 0.0) {
+    set_error("warm_start is not combined with refinement (max_refine > 0, tol_true > 0)");
+    return RK_ERR_ARG;
+  }
   if (s->warm_start && (s->krylov != RK_KRYLOV_CG || s->storage == RK_F16)) {
     set_error("warm_start is implemented for CG with FP64, FP32 or BF16 storage");
     return RK_ERR_ARG;
@@ -702,6 +751,7 @@ static void free_problem(rk_problem* p) {
   f(p->wp[0]);
   f(p->wp[1]);
   f(p->wdelta);
+  f(p->wx);
   f(p->partials);
   f(p->sc);
   f(p->rs);
@@ -780,6 +830,9 @@ rk_status rk_create_problem(const rk_problem_desc* desc, const rk_solver_desc* s
   p->N = (long long)desc->n * desc->n * desc->n;
   p->h = desc->op == RK_OP_ADV_PERIODIC ? 1.0 / desc->n : 1.0 / (desc->n + 1);
   p->c = desc->kappa / (p->h * p->h);
+  // refined stage solves keep k^eps in FP64 (the FP32 rounding of k^eps would
+  // otherwise bound the refinement)
+  p->ke_hi = solver->correct && solver->storage != RK_F64 && solver->max_refine > 0 && solver->tol_true > 0.0;
   const size_t N = (size_t)p->N, s = dtype_size(solver->storage);
   rk_status st = RK_OK;
   auto A = [&](void** ptr, size_t bytes) {
@@ -828,6 +881,19 @@ rk_status rk_create_problem(const rk_problem_desc* desc, const rk_solver_desc* s
     return st;
   }
   *out = p;
+  return RK_OK;
+}
+
+rk_status rk_set_wait_limit(rk_problem* p, unsigned long long spins) {
+  if (!p) {
+    set_error("problem is NULL");
+    return RK_ERR_ARG;
+  }
+  if (spins > 0xffffffffull) {
+    set_error("rk_set_wait_limit: at most 2^32 - 1 polls");
+    return RK_ERR_ARG;
+  }
+  p->wait_spins = (unsigned)spins;
   return RK_OK;
 }
 
@@ -887,10 +953,11 @@ rk_status rk_set_tableau(rk_problem* p, int q, const double* A_hi, const double*
         p->ke[i] = p->k[i];
         p->ke_alias[i] = true;
       } else {
-        RK_TRY(alloc_dev(p, &p->ke[i], N * xsize(p->sol.storage)));
+        RK_TRY(alloc_dev(p, &p->ke[i], N * (p->ke_hi ? 8 : xsize(p->sol.storage))));
       }
     }
   }
+  if (p->ke_hi && !p->wx) RK_TRY(alloc_dev(p, &p->wx, N * xsize(p->sol.storage)));
   p->q = q;
   for (auto& v : p->warm_valid) v = false;  // stage slots change meaning
   std::memcpy(p->Ah, A_hi, sizeof(double) * q * q);

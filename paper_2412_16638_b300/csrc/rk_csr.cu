@@ -253,8 +253,8 @@ rk_status csr_apply_f64(rk_problem* p, const double* x, double* y, RhsScalars* r
 rk_status csr_correct_f64(rk_problem* p, double shift, const double* gv, const void* ke, double* kout,
                           RhsScalars* rs) {
   rk_status st = RK_OK;
-  dispatch_st(p->sol.storage, [&](auto ts, auto) {
-    using X = typename XOf<typename decltype(ts)::type>::type;
+  dispatch_ke(p->ke_hi, p->sol.storage, [&](auto tx) {
+    using X = typename decltype(tx)::type;
     auto kern = csr_correct_f64_kernel<X>;
     const int grid = grid_for((const void*)kern, p->N);
     const double bytes = (double)p->csr.nnz * 12.0 + 4.0 * (p->N + 1) + (16.0 + sizeof(X)) * p->N;

@@ -74,6 +74,21 @@ inline void dispatch_bs(int bs, F&& f) {
   }
 }
 
+// Type of k^eps: FP64 when the problem refines its stage solves against an
+// FP64 true residual (the corrections then accumulate in FP64), else the
+// solver's solution type XOf<storage>.  f receives Tag<type>.
+template <typename F>
+inline void dispatch_ke(bool ke_hi, int storage, F&& f) {
+  if (ke_hi) {
+    f(Tag<double>{});
+    return;
+  }
+  switch (storage) {
+    case RK_F64: f(Tag<double>{}); break;
+    default: f(Tag<float>{}); break;  // FP32 storage, and FP32 solutions of 16-bit storage
+  }
+}
+
 // elements per thread segment for storage S and block size BS
 template <typename S, int BS>
 constexpr int seg_of() {
@@ -214,6 +229,11 @@ struct rk_problem {
   void* wz = nullptr;
   void* wp[2]{};
   void* wdelta = nullptr;
+  // k^eps held in FP64 (stage solves refined against the FP64 true residual):
+  // the solver writes its solution into wx (solution type), which is widened
+  // into ke[i]
+  bool ke_hi = false;
+  void* wx = nullptr;
   // reductions / device scalars
   double* partials = nullptr;
   rk::CgScalars* sc = nullptr;
@@ -224,6 +244,7 @@ struct rk_problem {
   rk::MinvEntry minv[8];
   int minv_next = 0;
   int last_iters[10]{};
+  unsigned wait_spins = 0;  // bound of the sweeps' main-loop TMA waits (0 = default)
   bool warm_valid[10]{};  // slot holds a solution usable as the next initial guess
   bool has_state = false;
   // CSR path

@@ -11,18 +11,27 @@
 // nothing.
 //
 // Properties a caller must know:
-//  - The array g_noalloc_scratch (RK_NOALLOC_BYTES, about 5.3 MB) exists on
-//    every GPU that loads this library and stays there until the process
-//    exits.  It bounds the problem size: n <= RK_NOALLOC_MAX_N (64).
-//  - The first call on a device looks up the array's device address with
-//    cudaGetSymbolAddress (once per device, with that device current).  Make
-//    that first call before any stream capture begins.
+//  - The array g_noalloc_scratch (RK_NOALLOC_BYTES, about 5.3 MB) bounds the
+//    problem size: n <= RK_NOALLOC_MAX_N (64).
+//  - The CUDA runtime loads a library's device code and its __device__ arrays
+//    onto a device lazily, at their first use there.  So the FIRST call on a
+//    device places the array (and the CG kernels' code) in that device's
+//    memory; that one call can fail with an out-of-memory error if the device
+//    is already full.  Make it before a pool or arena claims the device's
+//    memory (or run with CUDA_MODULE_LOADING=EAGER, which loads everything
+//    when the context is created).  From then on the array stays on that
+//    device until the process exits and later calls allocate nothing.
+//  - Every call looks up the array's device address with
+//    cudaGetSymbolAddress, with the caller's device current.  The address is
+//    not cached: after a cudaDeviceReset the module is loaded again and the
+//    array may sit elsewhere.
+//  - The call is synchronous (it reads the CG status back to the host between
+//    chunks of sweeps): never call it while a stream is being captured.
 //  - Every call uses the same array and leaves its contents behind; each call
 //    re-initialises everything that must start from a known value.  Calls
 //    that overlap on the GPU (different streams, threads or processes sharing
 //    the context) race on the array and give wrong results: serialise them.
 #include <cmath>
-#include <mutex>
 
 #include "rk_internal.h"
 
@@ -44,29 +53,19 @@ constexpr size_t RK_NOALLOC_BYTES = kOffVec + 5 * kVecBytes;  // r, z, p0, p1, x
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[RK_NOALLOC_BYTES];
 
-std::mutex g_mu;
-unsigned char* g_addr[64] = {};  // device address of the array, per device ordinal
-
-// Device address of g_noalloc_scratch on the current device (set-up on the
-// first call per device).  In host code the symbol itself is only a stand-in.
+// Device address of g_noalloc_scratch on the current device.  In host code
+// the symbol itself is only a stand-in.  Looked up on every call (a cheap host
+// lookup once the module is loaded), never cached: a cudaDeviceReset reloads
+// the module and may move the array.
 rk_status scratch_address(unsigned char** out) {
-  int dev = 0;
-  RK_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 64) {
-    rk::set_error("rk_heat_solve_noalloc: device ordinal %d out of range", dev);
-    return RK_ERR_ARG;
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) {
+    cudaGetLastError();
+    rk::set_error("rk_heat_solve_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+    return RK_ERR_CUDA;
   }
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) {
-      rk::set_error("rk_heat_solve_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
-      return RK_ERR_CUDA;
-    }
-    g_addr[dev] = static_cast<unsigned char*>(p);
-  }
-  *out = g_addr[dev];
+  *out = static_cast<unsigned char*>(p);
   return RK_OK;
 }
 

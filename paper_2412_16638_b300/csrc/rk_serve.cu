@@ -178,6 +178,12 @@ extern "C" rk_status rk_integrate_batch(rk_problem** ps, int count, double dt, i
       set_error("rk_integrate_batch: problem %d is not a heat/CG/block-Jacobi problem without forcing", i);
       return RK_ERR_ARG;
     }
+    if (p->ke_hi || p->sol.tol_true > 0.0) {
+      set_error("rk_integrate_batch: problem %d refines its solves against the true residual (tol_true > 0), "
+                "which the batched kernel does not; step it with rk_integrate",
+                i);
+      return RK_ERR_ARG;
+    }
     if (p->q == 0) {
       set_error("rk_integrate_batch: problem %d has no tableau", i);
       return RK_ERR_ARG;
@@ -337,7 +343,8 @@ struct Job {
   std::string error;
   rk_stats stats{};
   std::vector<double> result;
-  std::chrono::steady_clock::time_point t_submit, t_admit, t_done;
+  std::chrono::steady_clock::time_point t_submit, t_admit, t_first, t_done;
+  long long first_tick = -1, last_tick = -1;  // server ticks in which the job stepped
 };
 
 constexpr int kBatchMaxN = 64;  // jobs up to this size step in the batched kernel
@@ -429,6 +436,8 @@ struct rk_server {
   uint64_t next_id = 1;
   size_t used = 0;
   bool stop = false;
+  long long tick = 0;  // rounds of one step for every resident job
+  std::chrono::steady_clock::time_point t0;  // creation time
   std::thread worker;
   std::unique_ptr<rk::Pool> pool;
 };
@@ -519,7 +528,19 @@ static void worker_loop(rk_server* s) {
       act = s->active;
     }
     if (act.empty()) continue;
-    // one step for every resident job
+    // one step for every resident job: this tick's index and start time
+    const long long tick = s->tick++;
+    {
+      const auto now = std::chrono::steady_clock::now();
+      std::lock_guard<std::mutex> lk(s->mu);
+      for (auto& j : act) {
+        if (j->first_tick < 0) {
+          j->first_tick = tick;
+          j->t_first = now;
+        }
+        j->last_tick = tick;
+      }
+    }
     std::map<double, std::vector<std::shared_ptr<Job>>> small;  // by step size
     std::vector<std::function<void()>> tasks;
     std::vector<rk_status> results(act.size(), RK_OK);
@@ -528,7 +549,7 @@ static void worker_loop(rk_server* s) {
     for (size_t i = 0; i < act.size(); ++i) {
       Job* j = act[i].get();
       if (j->desc.op == RK_OP_HEAT7 && j->sol.krylov == RK_KRYLOV_CG && j->sol.precond == RK_PREC_BLOCK_JACOBI &&
-          j->source.empty() && j->desc.n <= kBatchMaxN) {
+          j->source.empty() && j->desc.n <= kBatchMaxN && !(j->sol.tol_true > 0.0)) {
         small[j->dt].push_back(act[i]);
       } else {
         tasks.push_back([&, i, j] {
@@ -595,6 +616,7 @@ rk_status rk_server_create(size_t hbm_budget_bytes, int max_slots, rk_server** o
   rk_server* s = new rk_server();
   s->budget = hbm_budget_bytes;
   s->max_slots = max_slots;
+  s->t0 = std::chrono::steady_clock::now();
   cudaGetDevice(&s->device);
   s->pool.reset(new Pool(8));
   s->worker = std::thread(worker_loop, s);
@@ -669,7 +691,7 @@ rk_status rk_poll_job(rk_server* s, uint64_t job_id, int* done) {
   return RK_OK;
 }
 
-rk_status rk_wait_job(rk_server* s, uint64_t job_id, double* u_out, rk_stats* stats, double* latency_s) {
+rk_status rk_wait_job_info(rk_server* s, uint64_t job_id, double* u_out, rk_stats* stats, rk_job_info* info) {
   if (!s) {
     set_error("rk_wait_job: NULL server");
     return RK_ERR_ARG;
@@ -691,10 +713,30 @@ rk_status rk_wait_job(rk_server* s, uint64_t job_id, double* u_out, rk_stats* st
     *stats = j->stats;
     stats->seconds = std::chrono::duration<double>(j->t_done - j->t_admit).count();
   }
-  if (latency_s) *latency_s = std::chrono::duration<double>(j->t_done - j->t_submit).count();
+  if (info) {
+    auto since = [&](std::chrono::steady_clock::time_point t) {
+      return std::chrono::duration<double>(t - s->t0).count();
+    };
+    info->t_submit = since(j->t_submit);
+    const bool admitted = j->t_admit.time_since_epoch().count() != 0;
+    const bool finished = j->t_done.time_since_epoch().count() != 0;  // cancelled jobs never finish
+    info->t_admit = admitted ? since(j->t_admit) : -1.0;
+    info->t_first_step = j->first_tick >= 0 ? since(j->t_first) : -1.0;
+    info->t_done = finished ? since(j->t_done) : -1.0;
+    info->first_tick = j->first_tick;
+    info->last_tick = j->last_tick;
+    info->steps = j->done_steps;
+  }
   if (j->status != RK_OK && j->status != RK_ERR_NOT_CONVERGED) set_error("job %llu failed: %s",
                                                                           (unsigned long long)job_id, j->error.c_str());
   return j->status;
+}
+
+rk_status rk_wait_job(rk_server* s, uint64_t job_id, double* u_out, rk_stats* stats, double* latency_s) {
+  rk_job_info info{};
+  const rk_status st = rk_wait_job_info(s, job_id, u_out, stats, &info);
+  if (latency_s) *latency_s = info.t_done >= 0.0 ? info.t_done - info.t_submit : -1.0;
+  return st;
 }
 
 rk_status rk_server_destroy(rk_server* s) {

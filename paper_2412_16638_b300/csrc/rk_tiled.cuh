@@ -68,9 +68,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait: false after kWaitSpins unsuccessful polls.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (unsigned i = 0; i < kWaitSpins; ++i)
+// Bounded wait: false after `spins` unsuccessful polls.  The main loops of
+// the sweeps take their bound from the solver scalars (a problem can lower it
+// to exercise the timeout path); the drain of copies still in flight always
+// uses the full bound kWaitSpins, so no copy lands after the CTA has exited.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned spins = kWaitSpins) {
+  for (unsigned i = 0; i < spins; ++i)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
@@ -209,6 +212,7 @@ __global__ void __launch_bounds__(320, 2) cg_tiled_a(const __grid_constant__ CUt
   const T beta = (T)sc->beta;
   const T o2 = o + o;
   const bool first = (sc->iter == 0);
+  const unsigned spins = sc->wait_spins ? sc->wait_spins : kWaitSpins;
   const uint32_t tx_bytes = (first ? 1u : 2u) * (uint32_t)(R * n * sizeof(S));
   if (tid == 0) {
     for (int s = 0; s < kStagesA; ++s) mbar_init(&bar[s], 1);
@@ -232,7 +236,7 @@ __global__ void __launch_bounds__(320, 2) cg_tiled_a(const __grid_constant__ CUt
   bool timed_out = false;
   for (int t = 0; t < L; ++t) {
     const int s = t % kStagesA;
-    const bool ok = mbar_wait(&bar[s], (uint32_t)((t / kStagesA) & 1));
+    const bool ok = mbar_wait(&bar[s], (uint32_t)((t / kStagesA) & 1), spins);
     // p on plane z1-t for the own line
     T pn[SEG];
     {
@@ -335,6 +339,7 @@ __global__ void __launch_bounds__(256, 2) cg_tiled_b(const __grid_constant__ CUt
   const int L = z1 - z0 + 2;
   const T alpha = (T)sc->alpha;
   const bool xzero = (sc->iter == 0) && !sc->warm;  // x = 0 at the first sweep of a cold start
+  const unsigned spins = sc->wait_spins ? sc->wait_spins : kWaitSpins;
   const uint32_t tx_bytes = (uint32_t)(R * n * sizeof(S));
   if (tid == 0) {
     for (int s = 0; s < kStagesB; ++s) mbar_init(&bar[s], 1);
@@ -382,7 +387,7 @@ __global__ void __launch_bounds__(256, 2) cg_tiled_b(const __grid_constant__ CUt
       }
     }
     const int s = t % kStagesB;
-    const bool ok = mbar_wait(&bar[s], (uint32_t)((t / kStagesB) & 1));
+    const bool ok = mbar_wait(&bar[s], (uint32_t)((t / kStagesB) & 1), spins);
     T pn[SEG];
     lds_seg<T, S, SEG>(st(s) + (size_t)l * n + xs, pn);
     if (t >= 2) {

@@ -80,15 +80,26 @@ __global__ void __launch_bounds__(kThreads) widen_f64(const S* __restrict__ x, c
 }
 
 // x holds sigma_x * k, dx holds sigma_dx * delta: x <- x + (sigma_x/sigma_dx) dx
-// (refinement update of k^eps, arithmetic in FP64).
-template <typename S>
-__global__ void __launch_bounds__(kThreads) add_scaled_inplace(S* __restrict__ x, const S* __restrict__ dx,
+// (refinement update of k^eps, arithmetic in FP64).  With an FP64 x the
+// corrections accumulate without rounding k^eps back to the solver's type.
+template <typename SX, typename SD>
+__global__ void __launch_bounds__(kThreads) add_scaled_inplace(SX* __restrict__ x, const SD* __restrict__ dx,
                                                                const RhsScalars* rs_x, const RhsScalars* rs_dx,
                                                                long long N) {
   const double f = rs_x->sigma / rs_dx->sigma;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
        i += (long long)gridDim.x * blockDim.x)
-    x[i] = nar<S>(fma(f, wid<double>(dx[i]), wid<double>(x[i])));
+    x[i] = nar<SX>(fma(f, wid<double>(dx[i]), wid<double>(x[i])));
+}
+
+// out = x widened to FP64, keeping its storage scale (out holds sigma * k as x
+// does): the solver output moved into an FP64 k^eps.
+template <typename S>
+__global__ void __launch_bounds__(kThreads) widen_keep_f64(const S* __restrict__ x, double* __restrict__ out,
+                                                           long long N) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = wid<double>(x[i]);
 }
 
 // res = k - ke/sigma (FP64): the true residual of the last stage solve, used
