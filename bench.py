@@ -200,12 +200,23 @@ def _oracle_setup(cfg, n):
     return dirk, op, tab, u0, solver
 
 
+def _one_thread():
+    """Limit BLAS/OpenMP pools to one thread (threadpoolctl when installed;
+    numpy's element-wise kernels, the oracle's main cost, are single-threaded
+    anyway)."""
+    try:
+        from threadpoolctl import threadpool_limits
+        return threadpool_limits(1)
+    except ImportError:
+        import contextlib
+        return contextlib.nullcontext()
+
+
 def _oracle_replica(args):
     """One oracle process (1 thread): `warm` untimed steps, a barrier, then
     `steps` timed steps.  Returns (t_start, t_end, CG iterations)."""
     cfg, n, warm, steps, barrier = args
-    from threadpoolctl import threadpool_limits
-    with threadpool_limits(1):
+    with _one_thread():
         dirk, op, tab, u, solver = _oracle_setup(cfg, n)
         for _ in range(warm):
             u = dirk.rk_step(u, cfg["dt"], tab, op, solver)
@@ -239,6 +250,8 @@ def oracle_all_cores(cfg, n, warm, steps):
     barrier: aggregate DOF*steps/s of the host = P n^3 steps / (last end -
     first start)."""
     P = _replica_count(n)
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"  # inherited by the spawned processes: one thread each
     ctx = mp.get_context("spawn")
     with ctx.Manager() as mgr:
         barrier = mgr.Barrier(P)
@@ -253,8 +266,7 @@ def oracle_all_cores(cfg, n, warm, steps):
 def oracle_one_thread(cfg, n, steps, best_of=3):
     """Best of `best_of` single whole oracle steps (1 thread), after one untimed
     step that also builds the preconditioners."""
-    from threadpoolctl import threadpool_limits
-    with threadpool_limits(1):
+    with _one_thread():
         dirk, op, tab, u, solver = _oracle_setup(cfg, n)
         u = dirk.rk_step(u, cfg["dt"], tab, op, solver)
         times, iters, conv = [], [], True
@@ -719,29 +731,33 @@ def main():
 
     extras = {}
     if not args.no_extras and world == 1:
-        # the same step at the paper's accuracy-study tolerance 1e-3
-        r = timed_heat(c, cfg, cfg["storage"], 1e-3, 1, K, W, total=total)
-        r.pop("_problem").close()
-        extras["tol1e-3"] = dict(summary(r), parity_ok=bool(r["err_vs_discrete_T"] <= bound))
-        # 16-bit storage of the Krylov vectors at 256^3 (FP32 arithmetic, FP64 corrections)
-        for st16 in ("f16", "bf16"):
+        def tol1e3():
+            # the same step at the paper's accuracy-study tolerance 1e-3
+            r = timed_heat(c, cfg, cfg["storage"], 1e-3, 1, K, W, total=total)
+            r.pop("_problem").close()
+            return dict(summary(r), parity_ok=bool(r["err_vs_discrete_T"] <= bound))
+
+        def sixteen(st16):
+            # 16-bit storage of the Krylov vectors at 256^3 (FP32 arithmetic, FP64 corrections)
             c16 = dict(WORKLOADS["heat256-" + st16])
             r = timed_heat(c, c16, st16, c16["tol"], 1, K, W, profile=True)
             r.pop("_problem").close()
-            extras["heat256_" + st16] = dict(summary(r), roofline=roofline_of(r["prof"], peak, peak_kind),
-                                             parity_ok=bool(r["err_vs_discrete"] <= PARITY[st16]),
-                                             bound=PARITY[st16])
-        # 128^3: the FP32 Krylov vectors (8.4 MB each) stay in the 126 MB L2
-        c128 = dict(WORKLOADS["heat128"])
-        r = timed_heat(c, c128, "f32", c128["tol"], 1, K, W, total=total, profile=True)
-        r.pop("_problem").close()
-        r64 = timed_heat(c, c128, "f64", c128["tol64"], 0, K, W)
-        r64.pop("_problem").close()
-        extras["heat128"] = dict(summary(r), roofline=roofline_of(r["prof"], peak, peak_kind),
-                                 parity_ok=bool(r["err_vs_discrete_T"] <= bound), note="L2-resident Krylov vectors",
-                                 fp64_plain=summary(r64), speedup_vs_fp64=r["value"] / r64["value"])
-        # fast-diagonalization preconditioner (tensor cores) on the headline problem
-        if cfg.get("precond", "bj") == "bj" and n <= 256:
+            return dict(summary(r), roofline=roofline_of(r["prof"], peak, peak_kind),
+                        parity_ok=bool(r["err_vs_discrete"] <= PARITY[st16]), bound=PARITY[st16])
+
+        def heat128():
+            # 128^3: the FP32 Krylov vectors (8.4 MB each) stay in the 126 MB L2
+            c128 = dict(WORKLOADS["heat128"])
+            r = timed_heat(c, c128, "f32", c128["tol"], 1, K, W, total=total, profile=True)
+            r.pop("_problem").close()
+            r64 = timed_heat(c, c128, "f64", c128["tol64"], 0, K, W)
+            r64.pop("_problem").close()
+            return dict(summary(r), roofline=roofline_of(r["prof"], peak, peak_kind),
+                        parity_ok=bool(r["err_vs_discrete_T"] <= bound), note="L2-resident Krylov vectors",
+                        fp64_plain=summary(r64), speedup_vs_fp64=r["value"] / r64["value"])
+
+        def fdm():
+            # fast-diagonalization preconditioner (tensor cores) on the headline problem
             r = timed_heat(c, cfg, cfg["storage"], 1e-3, 1, K, W, total=total, precond="fdm", profile=True)
             r.pop("_problem").close()
             fprof = r["prof"]
@@ -749,22 +765,37 @@ def main():
             fms = sum(v["ms_total"] for v in fk.values())
             fbytes = sum(v["bytes_total"] for v in fk.values())
             fn = sum(v["launches"] for v in fk.values())
-            extras["fdm"] = dict(summary(r), gpu_launches=r["launches"],
-                                 parity_ok=bool(r["err_vs_discrete_T"] <= bound),
-                                 fdm_pass={"launches": fn, "avg_us": 1e3 * fms / max(fn, 1),
-                                           "GBps": fbytes / max(fms, 1e-9) / 1e6,
-                                           "frac_hbm": fbytes / max(fms, 1e-9) / 1e6 / peak},
-                                 share_fdm_pass=fms / sum(v["ms_total"] for v in fprof.values()),
-                                 speedup_vs_fp64=(r["value"] / fp64["value"]) if fp64 else None)
-        extras["batch512"] = run_batch_key(c, args.batch_steps)
-        extras["advdiff192"] = run_advdiff_key(c, 192, args.advdiff_steps, 2)
+            return dict(summary(r), gpu_launches=r["launches"], parity_ok=bool(r["err_vs_discrete_T"] <= bound),
+                        fdm_pass={"launches": fn, "avg_us": 1e3 * fms / max(fn, 1),
+                                  "GBps": fbytes / max(fms, 1e-9) / 1e6,
+                                  "frac_hbm": fbytes / max(fms, 1e-9) / 1e6 / peak},
+                        share_fdm_pass=fms / sum(v["ms_total"] for v in fprof.values()),
+                        kernels=kernel_table(fprof),
+                        speedup_vs_fp64=(r["value"] / fp64["value"]) if fp64 else None)
+
+        jobs = [("tol1e-3", tol1e3), ("heat256_f16", lambda: sixteen("f16")),
+                ("heat256_bf16", lambda: sixteen("bf16")), ("heat128", heat128)]
+        if cfg.get("precond", "bj") == "bj" and n <= 256:
+            jobs.append(("fdm", fdm))
+        jobs += [("batch512", lambda: run_batch_key(c, args.batch_steps)),
+                 ("advdiff192", lambda: run_advdiff_key(c, 192, args.advdiff_steps, 2))]
         if args.serve_jobs > 0:
-            extras["serve"] = run_serve_key(c, args.serve_jobs, args.serve_slots)
+            jobs.append(("serve", lambda: run_serve_key(c, args.serve_jobs, args.serve_slots)))
+        for key, fn in jobs:
+            t0 = time.perf_counter()
+            try:
+                extras[key] = fn()
+            except Exception as e:  # reported in the line; the other keys still run
+                extras[key] = {"error": repr(e)}
+            extras[key]["wall_s"] = round(time.perf_counter() - t0, 1)
 
     # ---------------- oracle on the host cores
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_baseline(cfg)
+        try:
+            cpu = cpu_baseline(cfg)
+        except Exception as e:  # the GPU line is still printed
+            cpu = {"value": None, "unit": "DOF*steps/s", "kind": "oracle", "error": repr(e)}
 
     if rank == 0:
         line = {

@@ -160,8 +160,8 @@ rk_status rk_destroy_problem(rk_problem* p);
 
 /* Failure detection: bound the polls of every bounded device wait in the main
  * loops of this problem's TMA-fed CG sweeps (the waits for each shared-memory
- * tile; a poll is one mbarrier try_wait).  0 restores the default bound of
- * 2^24 polls.  When a wait runs out, the kernel lets its copies in flight land
+ * tile; a poll is then one non-blocking mbarrier test_wait).  0 restores the
+ * default bound of 2^24 blocking try_wait polls.  When a wait runs out, the kernel lets its copies in flight land
  * (always with the default bound), marks the solve and returns; the step then
  * fails with RK_ERR_TIMEOUT, the state u_n is left as it was before the step
  * and the problem stays usable.  Small values exist to exercise that path

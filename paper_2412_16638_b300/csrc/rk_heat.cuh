@@ -34,8 +34,8 @@ struct CgScalars {
   int status;      // 0 converged / running, 4 not converged, 5 non-finite/breakdown
   unsigned ticket;
   int warm;        // 1: the solve started from a nonzero x (x is read at iteration 0)
-  unsigned wait_spins;  // polls of each bounded TMA wait in the sweeps' main loops
-                        // (0 = the default bound kWaitSpins)
+  unsigned wait_spins;  // non-blocking polls of each TMA wait in the sweeps' main
+                        // loops (0 = the default bound of kWaitSpins try_wait polls)
 };
 
 // Per-solve right-hand-side statistics written by heat_apply_f64 / vec_norms.

@@ -68,13 +68,37 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait: false after `spins` unsuccessful polls.  The main loops of
-// the sweeps take their bound from the solver scalars (a problem can lower it
-// to exercise the timeout path); the drain of copies still in flight always
-// uses the full bound kWaitSpins, so no copy lands after the CTA has exited.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned spins = kWaitSpins) {
-  for (unsigned i = 0; i < spins; ++i)
+// Non-blocking probe of the phase (mbarrier.test_wait returns at once, unlike
+// try_wait, which may suspend the thread for a hardware-defined time).
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: false after kWaitSpins unsuccessful try_wait polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (unsigned i = 0; i < kWaitSpins; ++i)
     if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// The main-loop wait of the sweeps: `limit` = 0 is the default bound above;
+// a problem can set a small limit (rk_set_wait_limit) to exercise the
+// timeout path, and then each poll is a non-blocking test_wait, so the bound
+// counts checks, not hardware suspend windows.  The drain of copies still in
+// flight after a timeout always uses mbar_wait with the full bound, so no
+// copy lands after the CTA has exited.
+__device__ __forceinline__ bool mbar_wait_main(uint64_t* bar, uint32_t parity, unsigned limit) {
+  if (limit == 0) return mbar_wait(bar, parity);
+  for (unsigned i = 0; i < limit; ++i)
+    if (mbar_test_wait(bar, parity)) return true;
   return false;
 }
 
@@ -212,7 +236,7 @@ __global__ void __launch_bounds__(320, 2) cg_tiled_a(const __grid_constant__ CUt
   const T beta = (T)sc->beta;
   const T o2 = o + o;
   const bool first = (sc->iter == 0);
-  const unsigned spins = sc->wait_spins ? sc->wait_spins : kWaitSpins;
+  const unsigned spins = sc->wait_spins;  // 0: default bound
   const uint32_t tx_bytes = (first ? 1u : 2u) * (uint32_t)(R * n * sizeof(S));
   if (tid == 0) {
     for (int s = 0; s < kStagesA; ++s) mbar_init(&bar[s], 1);
@@ -236,7 +260,7 @@ __global__ void __launch_bounds__(320, 2) cg_tiled_a(const __grid_constant__ CUt
   bool timed_out = false;
   for (int t = 0; t < L; ++t) {
     const int s = t % kStagesA;
-    const bool ok = mbar_wait(&bar[s], (uint32_t)((t / kStagesA) & 1), spins);
+    const bool ok = mbar_wait_main(&bar[s], (uint32_t)((t / kStagesA) & 1), spins);
     // p on plane z1-t for the own line
     T pn[SEG];
     {
@@ -339,7 +363,7 @@ __global__ void __launch_bounds__(256, 2) cg_tiled_b(const __grid_constant__ CUt
   const int L = z1 - z0 + 2;
   const T alpha = (T)sc->alpha;
   const bool xzero = (sc->iter == 0) && !sc->warm;  // x = 0 at the first sweep of a cold start
-  const unsigned spins = sc->wait_spins ? sc->wait_spins : kWaitSpins;
+  const unsigned spins = sc->wait_spins;  // 0: default bound
   const uint32_t tx_bytes = (uint32_t)(R * n * sizeof(S));
   if (tid == 0) {
     for (int s = 0; s < kStagesB; ++s) mbar_init(&bar[s], 1);
@@ -387,7 +411,7 @@ __global__ void __launch_bounds__(256, 2) cg_tiled_b(const __grid_constant__ CUt
       }
     }
     const int s = t % kStagesB;
-    const bool ok = mbar_wait(&bar[s], (uint32_t)((t / kStagesB) & 1), spins);
+    const bool ok = mbar_wait_main(&bar[s], (uint32_t)((t / kStagesB) & 1), spins);
     T pn[SEG];
     lds_seg<T, S, SEG>(st(s) + (size_t)l * n + xs, pn);
     if (t >= 2) {
