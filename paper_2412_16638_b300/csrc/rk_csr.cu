@@ -5,6 +5,7 @@
 #include <utility>
 
 #include "rk_csr.cuh"
+#include "rk_gmres.cuh"
 #include "rk_internal.h"
 
 namespace rk {
@@ -40,8 +41,12 @@ struct CsrMinv {
 };
 
 struct GmresWork {
-  void* V = nullptr;          // (m+1) basis vectors, storage type
+  void* V = nullptr;          // (m+1) basis vectors of ldv elements (zero padded), basis type
+  void* wbuf = nullptr;       // w = (I - shift L) z of the current step, ldv elements, basis type
   void* z = nullptr;          // preconditioned vector
+  int* scol = nullptr;        // sliced-ELL copy of L: columns (ldv * kSellW) ...
+  void* sval = nullptr;       // ... and values lscale * L in the storage type
+  long long ldv = 0;          // leading dimension: N rounded up to a whole tile
   double* partials = nullptr; // per-CTA multi-dot partials
   GmScalars* sc = nullptr;
   GmScalars* h_sc = nullptr;  // pinned header mirror
@@ -173,6 +178,12 @@ rk_status csr_setup(rk_problem* p) {
     assemble(p->n, p->desc.kappa_field, p->desc.vel, rowptr, cols, vals);
   Csr& c = p->csr;
   c.nnz = (long long)vals.size();
+  for (size_t r = 0; r + 1 < rowptr.size(); ++r)
+    if (rowptr[r + 1] - rowptr[r] > kSellW) {
+      set_error("CSR row %zu has %d entries; the sliced-ELL copy holds at most %d", r, rowptr[r + 1] - rowptr[r],
+                kSellW);
+      return RK_ERR_ARG;
+    }
   double vmax = 0.0;
   for (double v : vals) vmax = std::max(vmax, std::fabs(v));
   if (!(vmax > 0.0) || !std::isfinite(vmax)) {
@@ -200,13 +211,27 @@ rk_status csr_setup(rk_problem* p) {
     p->gw = w;
     const size_t s = dtype_size(p->sol.storage);
     const int m = p->sol.restart;
-    RK_TRY(alloc_dev(p, &w->V, (size_t)(m + 1) * p->N * dtype_size(basis_dtype(p->sol))));
+    const size_t bsz = dtype_size(basis_dtype(p->sol));
+    w->ldv = (p->N + kGmTile - 1) / kGmTile * kGmTile;
+    RK_TRY(alloc_dev(p, &w->V, (size_t)(m + 1) * w->ldv * bsz));
+    RK_TRY(alloc_dev(p, &w->wbuf, (size_t)w->ldv * bsz));
+    RK_CUDA(cudaMemsetAsync(w->V, 0, (size_t)(m + 1) * w->ldv * bsz, p->st));  // padding stays zero
+    RK_CUDA(cudaMemsetAsync(w->wbuf, 0, (size_t)w->ldv * bsz, p->st));
     RK_TRY(alloc_dev(p, &w->z, (size_t)p->N * s));
+    RK_TRY(alloc_dev(p, (void**)&w->scol, (size_t)w->ldv * kSellW * sizeof(int)));
+    RK_TRY(alloc_dev(p, &w->sval, (size_t)w->ldv * kSellW * s));
+    dispatch_st(p->sol.storage, [&](auto ts, auto) {
+      using S = typename decltype(ts)::type;
+      auto kern = sell_from_csr<S>;
+      kern<<<grid_for((const void*)kern, w->ldv), kThreads, 0, p->st>>>(
+          CsrView{c.rowptr, c.cols}, c.v64, c.lscale, p->N, w->ldv, w->scol, static_cast<S*>(w->sval));
+      if (cudaGetLastError() != cudaSuccess) st = RK_ERR_CUDA;
+    });
+    RK_TRY(st);
     const int seg = gm_seg(p->sol.storage, p->sol.bj_block);
-    const int R = std::max(1, 32 / seg);
     const long long nsegs = (long long)p->n * p->n * ((p->n + seg - 1) / seg);
-    const long long ctas = ((nsegs + R - 1) / R + kThreads - 1) / kThreads;
-    w->npart = std::max<long long>(ctas, (long long)device_sms() * 32) * kGmMax;
+    const long long ctas = (nsegs + kThreads - 1) / kThreads;
+    w->npart = std::max<long long>(ctas * kGmMax, (long long)device_sms() * 8 * kGmDots);
     RK_TRY(alloc_dev(p, (void**)&w->partials, (size_t)w->npart * sizeof(double)));
     RK_TRY(alloc_dev(p, (void**)&w->sc, sizeof(GmScalars)));
     RK_CUDA(cudaMemset(w->sc, 0, sizeof(GmScalars)));
@@ -226,7 +251,10 @@ rk_status csr_free(rk_problem* p) {
   if (p->gw) {
     GmresWork* w = p->gw;
     if (w->V) cudaFree(w->V);
+    if (w->wbuf) cudaFree(w->wbuf);
     if (w->z) cudaFree(w->z);
+    if (w->scol) cudaFree(w->scol);
+    if (w->sval) cudaFree(w->sval);
     if (w->partials) cudaFree(w->partials);
     if (w->sc) cudaFree(w->sc);
     if (w->h_sc) cudaFreeHost(w->h_sc);
@@ -332,8 +360,9 @@ rk_status csr_precond_f64(rk_problem* p, double shift, const double* r, double* 
 }
 
 // Right-preconditioned restarted GMRES(m) on (I - shift L) x = sigma g, x0 = 0.
-// Each Arnoldi step launches four kernels (precondition, SpMV + first
-// projection dots, second CGS pass, norm + Hessenberg/Givens); they return at
+// Each Arnoldi step launches three kernels (preconditioner; product on the
+// sliced-ELL copy + the step's one reduction + Hessenberg/Givens; basis
+// update with the delayed reorthogonalisation, rk_gmres.cuh); they return at
 // once when the device state says the cycle or the solve has ended.  The host
 // polls the state once per chunk of steps and launches the cycle-end update
 // and the restart.
@@ -355,6 +384,7 @@ rk_status gmres_solve(rk_problem* p, double shift, const double* g64, RhsScalars
   hs->tol_abs = p->sol.tol_abs;
   hs->verify = basis_dtype(p->sol) != p->sol.storage ? 1 : 0;
   RK_CUDA(cudaMemcpyAsync(w->sc, hs, kGmHeader, cudaMemcpyHostToDevice, p->st));
+  RK_CUDA(cudaMemsetAsync(&w->sc->ticket2, 0, sizeof(unsigned), p->st));
   const int solve = ++p->solve_seq;
   rk_status st = RK_OK;
   // basis type: the storage type, or BF16 with FP32 storage (compressed basis)
@@ -373,32 +403,59 @@ rk_status gmres_solve(rk_problem* p, double shift, const double* g64, RhsScalars
     dispatch_bs(p->sol.bj_block, [&](auto bsc) {
       constexpr int BS = decltype(bsc)::value;
       constexpr int SEG = seg_of<S, BS>();
-      constexpr int R = (32 / SEG) > 1 ? 32 / SEG : 1;
       HeatGeo g{p->n, (p->n + SEG - 1) / SEG, (long long)p->n * p->n, p->N};
       const long long nsegs = g.n2 * g.nseg;
-      const int gdots = (int)(((nsegs + R - 1) / R + kThreads - 1) / kThreads);
       B* V = static_cast<B*>(w->V);
+      B* wb = static_cast<B*>(w->wbuf);
       S* z = static_cast<S*>(w->z);
       X* xs = static_cast<X*>(x);
       const S* lv = static_cast<const S*>(p->csr.vS);
       const S* M = static_cast<const S*>(minv);
       const T cs = (T)(shift / p->csr.lscale);
-      const long long ldv = p->N;
+      const long long ldv = w->ldv;
       const double Ns = (double)p->N * sizeof(S), Nx = (double)p->N * sizeof(X);
       const double Nb = (double)p->N * sizeof(B);
       const double mat = (double)p->csr.nnz * (4.0 + sizeof(S)) + 4.0 * (p->N + 1);
+      const double sell = (double)p->N * kSellW * (4.0 + sizeof(S));
       auto k_start = gm_start<S, B, T, SEG>;
       auto k_restart = gm_restart<S, B, T, SEG>;
-      auto k_prec = gm_prec<S, B, T, BS, SEG>;
-      auto k_spmv = gm_spmv_dots<S, B, T, SEG, R>;
-      auto k_orth = gm_orth<S, B, T, SEG, R>;
-      auto k_norm = gm_norm<S, B, T, SEG, R>;
+      auto k_prec = gm_dc_prec<S, B, T, BS, SEG>;
+      auto k_arn = gm_dc_arnoldi<S, B, T>;
+      auto k_upd_basis = gm_dc_update<S, B, T>;
       auto k_upd = gm_update<S, B, T, BS, SEG>;
       const int gs = grid_for((const void*)k_start, nsegs), gp = grid_for((const void*)k_prec, nsegs);
+      // persistent grids of the two streaming kernels (ring in dynamic shared memory)
+      const size_t smem = gm_dc_smem<B>();
+      if (cudaFuncSetAttribute((const void*)k_arn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+              cudaSuccess ||
+          cudaFuncSetAttribute((const void*)k_upd_basis, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+              cudaSuccess) {
+        cudaGetLastError();
+        st = RK_ERR_CUDA;
+        set_error("GMRES: shared-memory attribute of the Arnoldi kernels refused");
+        return;
+      }
+      int occ_a = 0, occ_u = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_a, k_arn, kGmThreads, smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_u, k_upd_basis, kGmThreads, smem);
+      cudaGetLastError();
+      const long long ntiles = ldv / kGmTile;
+      const int ga = (int)std::max(1LL, std::min<long long>(ntiles, (long long)device_sms() * std::max(1, occ_a)));
+      const int gu = (int)std::max(1LL, std::min<long long>(ntiles, (long long)device_sms() * std::max(1, occ_u)));
+      if ((long long)ga * kGmDots > w->npart) {
+        st = RK_ERR_ARG;
+        set_error("GMRES: reduction workspace too small for %d CTAs", ga);
+        return;
+      }
       launch(p, K_GM_INIT, 8.0 * p->N + Nb + Nx,
              [&] { k_start<<<gs, kThreads, 0, p->st>>>(g, g64, rs, V, xs, w->sc, w->partials); });
+      // Arnoldi steps in chunks; each kernel returns at once when the device
+      // state says the cycle or the solve has ended.  Step j of a cycle moves
+      // j + 1 basis vectors in gm_dc_arnoldi and j + 2 (plus two written) in
+      // gm_dc_update; a cycle has m + 1 steps (the last one only finishes
+      // column m - 1), so the host's step count modulo m + 1 is j.
       int launched = 0, worked = 0, rounds = 0;
-      const int maxlaunch = p->sol.max_iter + 2 * m + 64;
+      const int maxlaunch = p->sol.max_iter + 4 * (m + 1) + 64;
       const int maxrounds = 2 * (maxlaunch / 8) + 16;  // every round advances the device state
       while (true) {
         if (++rounds > maxrounds) {
@@ -409,19 +466,16 @@ rk_status gmres_solve(rk_problem* p, double shift, const double* g64, RhsScalars
         const int chunk = 8;
         for (int c = 0; c < chunk; ++c) {
           const int idx = launched + c;
-          // bytes use the basis size at the step's expected index (j = idx mod m)
-          const double jb = (double)(idx % m) + 1.0;
-          prof_begin(p, K_GM_PREC, 2.0 * Nb + Ns + BS * Ns, solve, idx);
+          const double jb = (double)(idx % (m + 1));
+          prof_begin(p, K_GM_PREC, Nb + Ns + BS * Ns, solve, idx);
           k_prec<<<gp, kThreads, 0, p->st>>>(g, V, ldv, M, z, w->sc);
           prof_end(p);
-          prof_begin(p, K_GM_ARNOLDI, mat + Ns + jb * Nb + Nb, solve, idx);
-          k_spmv<<<gdots, kThreads, 0, p->st>>>(g, view(p), lv, cs, z, V, ldv, w->sc, w->partials);
+          prof_begin(p, K_GM_ARNOLDI, sell + Ns + Nb + (jb + 1.0) * Nb, solve, idx);
+          k_arn<<<ga, kGmThreads, smem, p->st>>>(w->scol, static_cast<const S*>(w->sval), cs, z, V, ldv, wb,
+                                                  p->N, w->sc, w->partials);
           prof_end(p);
-          prof_begin(p, K_GM_ORTH, 2.0 * jb * Nb + 2.0 * Nb, solve, idx);
-          k_orth<<<gdots, kThreads, 0, p->st>>>(g, V, ldv, w->sc, w->partials);
-          prof_end(p);
-          prof_begin(p, K_GM_NORM, jb * Nb + 2.0 * Nb, solve, idx);
-          k_norm<<<gdots, kThreads, 0, p->st>>>(g, V, ldv, w->sc, w->partials);
+          prof_begin(p, K_GM_ORTH, (jb + 2.0) * Nb + 2.0 * Nb, solve, idx);
+          k_upd_basis<<<gu, kGmThreads, smem, p->st>>>(V, ldv, wb, p->N, w->sc);
           prof_end(p);
         }
         launched += chunk;
@@ -436,10 +490,15 @@ rk_status gmres_solve(rk_problem* p, double shift, const double* g64, RhsScalars
           set_error("GMRES status readback failed");
           return;
         }
-        const int did = hs->iter - worked;
+        const int did = hs->steps - worked;
         prof_mark_noops(p, solve, launched - chunk + did, launched);
-        worked = hs->iter;
+        worked = hs->steps;
         launched = worked;  // launch indices continue from the device step count
+        if (hs->status == 6) {
+          st = RK_ERR_TIMEOUT;
+          set_error("GMRES: a bounded wait for a streamed basis tile gave up");
+          return;
+        }
         if (hs->cycle_end) {
           launch(p, K_GM_UPDATE, (double)hs->jused * Nb + 2.0 * Nx + BS * Ns,
                  [&] { k_upd<<<gp, kThreads, 0, p->st>>>(g, V, ldv, M, xs, w->sc); });

@@ -1,8 +1,9 @@
 // Kernels of the advection-diffusion path: CSR operator (FP64 and storage
-// precision), block-Jacobi with per-block inverses, and right-preconditioned
-// restarted GMRES(m) with classical Gram-Schmidt applied twice (CGS2).  The
-// Arnoldi/Hessenberg/Givens state lives on the device; the last CTA of each
-// reduction updates it, so the host only polls a status word.
+// precision), block-Jacobi with per-block inverses, and the start, restart and
+// cycle-end update of the right-preconditioned restarted GMRES(m) (the
+// Arnoldi step itself is in rk_gmres.cuh).  The Arnoldi/Hessenberg/Givens
+// state lives on the device; the last CTA of each reduction updates it, so the
+// host only polls a status word.
 //
 // Thread mapping of the vector kernels is the x-line segment mapping of the
 // heat path (RK_SEG_LOOP): block-Jacobi blocks (x-line segments of BS nodes)
@@ -10,6 +11,7 @@
 #pragma once
 #include "rk_device.cuh"
 #include "rk_heat.cuh"
+#include "rk_tiled.cuh"
 
 namespace rk {
 
@@ -35,7 +37,7 @@ struct GmScalars {
   int verify;     // 1: a converged cycle is confirmed by the true residual of
                   // the restart (compressed basis: x is assembled from it)
   int conv_est;   // verify mode: the cycle that just ended converged by its estimate
-  int pad2;
+  int steps;      // Arnoldi steps that did work (launch bookkeeping of the host)
   double beta;    // residual norm at the start of the cycle
   double bnorm;   // ||sigma g||
   double thresh;  // stopping threshold on the residual norm
@@ -45,6 +47,12 @@ struct GmScalars {
   double h1[kGmMax + 1], h2[kGmMax + 1];
   double H[(kGmMax + 1) * kGmMax];  // column-major (m+1) x m
   double cs[kGmMax], sn[kGmMax], gv[kGmMax + 1], y[kGmMax];
+  // delayed reorthogonalization (see gm_dc_arnoldi)
+  double Hraw[(kGmMax + 1) * kGmMax];  // unrotated Hessenberg, column-major (m+1) x m
+  double sv[kGmMax];      // reorthogonalization coefficients s of the current step
+  double cv[kGmMax + 1];  // coefficients c of u_{j+1} = w / nrm - V c
+  double inv_nrm;         // 1 / ||v_j|| before normalisation
+  unsigned ticket2;       // completion ticket of gm_dc_update
 };
 
 // ------------------------------------------------------------- FP64 CSR ops
@@ -212,84 +220,6 @@ __device__ __forceinline__ void shifted_seg(CsrView A, const S* __restrict__ lv,
 }
 
 // ------------------------------------------------------------- GMRES kernels
-// Per-thread multi-segment layout of the reduction kernels: thread t of T
-// handles segments t, t+T, ..., t+(R-1)T.
-#define RK_GM_SEGS(g, SEG, R)                                                    \
-  const long long nsegs_ = (long long)(g).n2 * (g).nseg;                         \
-  const long long tthreads_ = (long long)gridDim.x * blockDim.x;                 \
-  const long long tid_ = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-
-struct SegPos {
-  long long base;
-  int m;
-  int i0;
-  long long line;
-  bool valid;
-};
-
-__device__ __forceinline__ SegPos seg_pos(const HeatGeo& g, long long sidx, int SEG) {
-  SegPos p;
-  p.valid = sidx < (long long)g.n2 * g.nseg;
-  if (!p.valid) {
-    p.base = 0;
-    p.m = 0;
-    p.i0 = 0;
-    p.line = 0;
-    return p;
-  }
-  p.line = sidx / g.nseg;
-  p.i0 = (int)(sidx - p.line * g.nseg) * SEG;
-  p.m = min(SEG, g.n - p.i0);
-  p.base = p.line * g.n + p.i0;
-  return p;
-}
-
-// Sum over the CTA, then over CTAs, of each of `cnt` per-thread values dot(i)
-// (per-CTA sums at partials[cta*kGmMax + i]); the last CTA returns true in
-// thread 0 with the totals in out[i].  Each dot is reduced within its warp by
-// shuffles only, so the loads of the next basis vector are not held behind a
-// barrier; one barrier then combines the warps.  Fixed order: deterministic.
-template <typename F>
-__device__ __forceinline__ bool multi_dot_reduce(int cnt, F dot, double* partials, unsigned* ticket, double* out) {
-  constexpr int kWarps = kThreads / 32;
-  __shared__ double swarp[kWarps][kGmMax + 1];
-  __shared__ int am_last;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i = 0; i < cnt; ++i) {
-    double v = dot(i);
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-    if (lane == 0) swarp[warp][i] = v;
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-    double a = 0.0;
-#pragma unroll
-    for (int w = 0; w < kWarps; ++w) a += swarp[w][i];
-    partials[(size_t)blockIdx.x * kGmMax + i] = a;
-    __threadfence();
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned t = atomicAdd(ticket, 1u);
-    am_last = (t == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (!am_last) return false;
-  __threadfence();
-  // last CTA: warp w sums dots i = w, w + kWarps, ... over the CTAs
-  for (int i = warp; i < cnt; i += kWarps) {
-    double a = 0.0;
-    for (int b = lane; b < (int)gridDim.x; b += 32) a += __ldcg(partials + (size_t)b * kGmMax + i);
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
-    if (lane == 0) out[i] = a;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) *ticket = 0u;
-  return threadIdx.x == 0;
-}
-
 // Start of a solve from x = 0: V_0 <- sigma g (rounded to B, unnormalised),
 // x <- 0, beta = ||V_0||.
 template <typename S, typename B, typename T, int SEG>
@@ -384,225 +314,6 @@ __global__ void __launch_bounds__(kThreads) gm_restart(HeatGeo g, CsrView A, con
       sc->done = 1;
     }
     sc->conv_est = 0;
-  }
-}
-
-// Arnoldi step part 1: normalise V_j (lazily: it was stored unnormalised) and
-// z = D^{-1} V_j.
-template <typename S, typename B, typename T, int BS, int SEG>
-__global__ void __launch_bounds__(kThreads) gm_prec(HeatGeo g, B* __restrict__ V, long long ldv,
-                                                    const S* __restrict__ minv, S* __restrict__ z, GmScalars* sc) {
-  if (sc->done || sc->cycle_end) return;
-  const int jj = sc->j;
-  const T f = (T)(1.0 / (jj == 0 ? sc->beta : sc->hnext));
-  B* Vj = V + (long long)jj * ldv;
-  const int nbl = (g.n + BS - 1) / BS;
-  RK_SEG_LOOP(g, SEG)
-    (void)j;
-    (void)k;
-    T v[SEG], zv[SEG];
-    load_seg<T, B, SEG>(Vj + base, m, v);
-#pragma unroll
-    for (int e = 0; e < SEG; ++e) v[e] = (e < m) ? rnd<B, T>(v[e] * f) : T(0);
-    bj_apply_blocks<T, S, BS, SEG>(minv, line, nbl, i0, v, zv);
-    store_seg<B, T, SEG>(Vj + base, m, v);
-    store_seg<S, T, SEG>(z + base, m, zv);
-  RK_SEG_LOOP_END
-}
-
-// Arnoldi step part 2: w = (I - shift L) z written to V_{j+1}; h1_i = V_i . w
-// for i <= j (first Gram-Schmidt projection coefficients).
-template <typename S, typename B, typename T, int SEG, int R>
-__global__ void __launch_bounds__(kThreads) gm_spmv_dots(HeatGeo g, CsrView A, const S* __restrict__ lv, T cs,
-                                                         const S* __restrict__ z, B* __restrict__ V, long long ldv,
-                                                         GmScalars* sc, double* partials) {
-  if (sc->done || sc->cycle_end) return;
-  const int jj = sc->j;
-  RK_GM_SEGS(g, SEG, R)
-  T w[R][SEG];
-  SegPos pos[R];
-  B* W = V + (long long)(jj + 1) * ldv;
-#pragma unroll
-  for (int q = 0; q < R; ++q) {
-    pos[q] = seg_pos(g, tid_ + q * tthreads_, SEG);
-    if (pos[q].valid) {
-      shifted_seg<T, S, S, SEG>(A, lv, pos[q].base, pos[q].m, z, cs, w[q]);
-#pragma unroll
-      for (int e = 0; e < SEG; ++e) w[q][e] = rnd<B, T>(w[q][e]);
-      store_seg<B, T, SEG>(W + pos[q].base, pos[q].m, w[q]);
-    } else {
-#pragma unroll
-      for (int e = 0; e < SEG; ++e) w[q][e] = T(0);
-    }
-  }
-  auto dot = [&](int i) {
-    const B* Vi = V + (long long)i * ldv;
-    T a = T(0);
-#pragma unroll
-    for (int q = 0; q < R; ++q) {
-      if (!pos[q].valid) continue;
-      T vi[SEG];
-      load_seg<T, B, SEG>(Vi + pos[q].base, pos[q].m, vi);
-#pragma unroll
-      for (int e = 0; e < SEG; ++e) a = fma(vi[e], w[q][e], a);
-    }
-    return (double)a;
-  };
-  multi_dot_reduce(jj + 1, dot, partials, &sc->ticket, sc->h1);
-}
-
-// Arnoldi step part 3 (second CGS pass): w <- w - sum_i h1_i V_i, then
-// h2_i = V_i . w.
-template <typename S, typename B, typename T, int SEG, int R>
-__global__ void __launch_bounds__(kThreads) gm_orth(HeatGeo g, B* __restrict__ V, long long ldv, GmScalars* sc,
-                                                    double* partials) {
-  if (sc->done || sc->cycle_end) return;
-  const int jj = sc->j;
-  RK_GM_SEGS(g, SEG, R)
-  T w[R][SEG];
-  SegPos pos[R];
-  B* W = V + (long long)(jj + 1) * ldv;
-#pragma unroll
-  for (int q = 0; q < R; ++q) {
-    pos[q] = seg_pos(g, tid_ + q * tthreads_, SEG);
-    if (pos[q].valid) {
-      load_seg<T, B, SEG>(W + pos[q].base, pos[q].m, w[q]);
-    } else {
-#pragma unroll
-      for (int e = 0; e < SEG; ++e) w[q][e] = T(0);
-    }
-  }
-  for (int i = 0; i <= jj; ++i) {
-    const T hi = (T)sc->h1[i];
-    const B* Vi = V + (long long)i * ldv;
-#pragma unroll
-    for (int q = 0; q < R; ++q) {
-      if (!pos[q].valid) continue;
-      T vi[SEG];
-      load_seg<T, B, SEG>(Vi + pos[q].base, pos[q].m, vi);
-#pragma unroll
-      for (int e = 0; e < SEG; ++e) w[q][e] = fma(-hi, vi[e], w[q][e]);
-    }
-  }
-#pragma unroll
-  for (int q = 0; q < R; ++q) {
-#pragma unroll
-    for (int e = 0; e < SEG; ++e) w[q][e] = (pos[q].valid && e < pos[q].m) ? rnd<B, T>(w[q][e]) : T(0);
-    if (pos[q].valid) store_seg<B, T, SEG>(W + pos[q].base, pos[q].m, w[q]);
-  }
-  auto dot = [&](int i) {
-    const B* Vi = V + (long long)i * ldv;
-    T a = T(0);
-#pragma unroll
-    for (int q = 0; q < R; ++q) {
-      if (!pos[q].valid) continue;
-      T vi[SEG];
-      load_seg<T, B, SEG>(Vi + pos[q].base, pos[q].m, vi);
-#pragma unroll
-      for (int e = 0; e < SEG; ++e) a = fma(vi[e], w[q][e], a);
-    }
-    return (double)a;
-  };
-  multi_dot_reduce(jj + 1, dot, partials, &sc->ticket, sc->h2);
-}
-
-// Arnoldi step part 4: w <- w - sum_i h2_i V_i, ||w||; the last CTA forms the
-// Hessenberg column (h1 + h2, ||w||), applies the Givens rotations, tests
-// convergence and, at the end of a cycle, solves the triangular system.
-template <typename S, typename B, typename T, int SEG, int R>
-__global__ void __launch_bounds__(kThreads) gm_norm(HeatGeo g, B* __restrict__ V, long long ldv, GmScalars* sc,
-                                                    double* partials) {
-  if (sc->done || sc->cycle_end) return;
-  const int jj = sc->j;
-  RK_GM_SEGS(g, SEG, R)
-  T w[R][SEG];
-  SegPos pos[R];
-  B* W = V + (long long)(jj + 1) * ldv;
-#pragma unroll
-  for (int q = 0; q < R; ++q) {
-    pos[q] = seg_pos(g, tid_ + q * tthreads_, SEG);
-    if (pos[q].valid) {
-      load_seg<T, B, SEG>(W + pos[q].base, pos[q].m, w[q]);
-    } else {
-#pragma unroll
-      for (int e = 0; e < SEG; ++e) w[q][e] = T(0);
-    }
-  }
-  for (int i = 0; i <= jj; ++i) {
-    const T hi = (T)sc->h2[i];
-    const B* Vi = V + (long long)i * ldv;
-#pragma unroll
-    for (int q = 0; q < R; ++q) {
-      if (!pos[q].valid) continue;
-      T vi[SEG];
-      load_seg<T, B, SEG>(Vi + pos[q].base, pos[q].m, vi);
-#pragma unroll
-      for (int e = 0; e < SEG; ++e) w[q][e] = fma(-hi, vi[e], w[q][e]);
-    }
-  }
-  double acc[1] = {0.0};
-#pragma unroll
-  for (int q = 0; q < R; ++q) {
-#pragma unroll
-    for (int e = 0; e < SEG; ++e) {
-      w[q][e] = (pos[q].valid && e < pos[q].m) ? rnd<B, T>(w[q][e]) : T(0);
-      acc[0] += (double)(w[q][e] * w[q][e]);
-    }
-    if (pos[q].valid) store_seg<B, T, SEG>(W + pos[q].base, pos[q].m, w[q]);
-  }
-  double tot[1];
-  if (!grid_reduce<1, 0u>(acc, partials, &sc->ticket, tot)) return;
-  // ---- last CTA, thread 0: Hessenberg column, Givens, convergence
-  const int m = sc->m;
-  double* Hc = sc->H + (size_t)jj * (kGmMax + 1);
-  const double hn = sqrt(tot[0]);
-  for (int i = 0; i <= jj; ++i) Hc[i] = sc->h1[i] + sc->h2[i];
-  Hc[jj + 1] = hn;
-  sc->hnext = hn;
-  for (int i = 0; i < jj; ++i) {
-    const double t = sc->cs[i] * Hc[i] + sc->sn[i] * Hc[i + 1];
-    Hc[i + 1] = -sc->sn[i] * Hc[i] + sc->cs[i] * Hc[i + 1];
-    Hc[i] = t;
-  }
-  const double den = hypot(Hc[jj], Hc[jj + 1]);
-  const double c = (den > 0.0) ? Hc[jj] / den : 1.0;
-  const double s = (den > 0.0) ? Hc[jj + 1] / den : 0.0;
-  sc->cs[jj] = c;
-  sc->sn[jj] = s;
-  Hc[jj] = den;
-  Hc[jj + 1] = 0.0;
-  sc->gv[jj + 1] = -s * sc->gv[jj];
-  sc->gv[jj] = c * sc->gv[jj];
-  const double res = fabs(sc->gv[jj + 1]);
-  sc->res = res;
-  sc->iter += 1;
-  const int jn = jj + 1;
-  sc->j = jn;
-  const bool conv = res <= sc->thresh;
-  const bool bad = !isfinite(res) || !isfinite(den);
-  const bool breakdown = (hn == 0.0);
-  if (conv || bad || breakdown || jn >= m || sc->iter >= sc->max_iter) {
-    // back substitution H(0:jn,0:jn) y = g(0:jn)
-    for (int i = jn - 1; i >= 0; --i) {
-      double v = sc->gv[i];
-      for (int kk = i + 1; kk < jn; ++kk) v -= sc->H[(size_t)kk * (kGmMax + 1) + i] * sc->y[kk];
-      const double d = sc->H[(size_t)i * (kGmMax + 1) + i];
-      sc->y[i] = (d != 0.0) ? v / d : 0.0;
-    }
-    sc->jused = jn;
-    sc->cycle_end = 1;
-    if (bad) {
-      sc->done = 1;
-      sc->status = 5;
-    } else if ((conv || breakdown) && !sc->verify) {
-      sc->done = 1;
-      sc->status = 0;
-    } else if (conv || breakdown) {
-      sc->conv_est = 1;  // the restart checks the true residual
-    } else if (sc->iter >= sc->max_iter) {
-      sc->done = 1;
-      sc->status = 4;
-    }
   }
 }
 
