@@ -127,11 +127,21 @@ __global__ void __launch_bounds__(kThreads) gm_dc_prec(HeatGeo g, const B* __res
   RK_SEG_LOOP_END
 }
 
-// Sum of v over the warp (fixed shuffle order), added by lane 0 to *dst.
-__device__ __forceinline__ void warp_add(double v, double* dst) {
+// Sums of a and b over the warp (fixed shuffle order, the two chains
+// interleaved), added by lane 0 to *da and *db.  In the arithmetic type T: on
+// this part an FP64 operation costs about 30 FP32 ones, so FP32 paths reduce
+// in FP32 and convert to FP64 once per kernel.
+template <typename T>
+__device__ __forceinline__ void warp_add2(T a, T b, T* da, T* db) {
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-  if ((threadIdx.x & 31) == 0) *dst += v;
+  for (int off = 16; off > 0; off >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, off);
+    b += __shfl_down_sync(0xffffffffu, b, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    *da += a;
+    *db += b;
+  }
 }
 
 // Last CTA of gm_dc_arnoldi, all threads: finish column j-1 of the Hessenberg
@@ -279,6 +289,8 @@ __host__ __device__ constexpr size_t gm_ring_bytes() {
 }
 template <typename B>
 __host__ __device__ constexpr size_t gm_dc_smem() {
+  // ring, barriers, per-warp accumulators (arithmetic type, at most 8 bytes)
+  // that the last CTA reuses for the FP64 totals
   return gm_ring_bytes<B>() + 8 * kGmStages + sizeof(double) * ((kGmThreads / 32) * kGmDots);
 }
 
@@ -300,7 +312,7 @@ __global__ void __launch_bounds__(kGmThreads, 2) gm_dc_arnoldi(const int* __rest
   __shared__ int am_last;
   B* ring_st = reinterpret_cast<B*>(smem);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + gm_ring_bytes<B>());
-  double* acc = reinterpret_cast<double*>(smem + gm_ring_bytes<B>() + 8 * kGmStages);
+  T* acc = reinterpret_cast<T*>(smem + gm_ring_bytes<B>() + 8 * kGmStages);
   const int jj = sc->j;
   const bool spmv = jj < sc->m;
   const int nd = 2 * jj + 2;
@@ -308,7 +320,7 @@ __global__ void __launch_bounds__(kGmThreads, 2) gm_dc_arnoldi(const int* __rest
   const long long ntiles = ldv / kGmTile;
   const long long mytiles = (long long)blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const int tid = threadIdx.x, warp = tid >> 5;
-  for (int i = tid; i < kWarps * nd; i += blockDim.x) acc[i] = 0.0;
+  for (int i = tid; i < kWarps * nd; i += blockDim.x) acc[i] = T(0);
   if (tid == 0) {
     for (int s = 0; s < kGmStages; ++s) mbar_init(&bar[s], 1);
     mbar_fence_init();
@@ -325,7 +337,7 @@ __global__ void __launch_bounds__(kGmThreads, 2) gm_dc_arnoldi(const int* __rest
   ring.start(src);
   long long q = 0;
   bool timed_out = false;
-  double* accw = acc + warp * nd;
+  T* accw = acc + warp * nd;
   for (long long tt = 0; tt < mytiles && !timed_out; ++tt) {
     const long long r0 = (blockIdx.x + tt * (long long)gridDim.x) * kGmTile;
     T w[kGmRows], u[kGmRows];
@@ -373,8 +385,7 @@ __global__ void __launch_bounds__(kGmThreads, 2) gm_dc_arnoldi(const int* __rest
           pa = fma(u[e], u[e], pa);
           pb = fma(u[e], w[e], pb);
         }
-        warp_add((double)pa, &accw[2 * jj]);
-        warp_add((double)pb, &accw[2 * jj + 1]);
+        warp_add2(pa, pb, &accw[2 * jj], &accw[2 * jj + 1]);
       } else {
 #pragma unroll
         for (int e = 0; e < kGmRows; ++e) {
@@ -382,8 +393,7 @@ __global__ void __launch_bounds__(kGmThreads, 2) gm_dc_arnoldi(const int* __rest
           pa = fma(v, u[e], pa);
           pb = fma(v, w[e], pb);
         }
-        warp_add((double)pa, &accw[it - 1]);
-        warp_add((double)pb, &accw[jj + it - 1]);
+        warp_add2(pa, pb, &accw[it - 1], &accw[jj + it - 1]);
       }
       if (__syncthreads_or(!ok)) {
         timed_out = true;
@@ -403,7 +413,7 @@ __global__ void __launch_bounds__(kGmThreads, 2) gm_dc_arnoldi(const int* __rest
   for (int i = tid; i < nd; i += blockDim.x) {
     double v = 0.0;
 #pragma unroll
-    for (int ww = 0; ww < kWarps; ++ww) v += acc[ww * nd + i];
+    for (int ww = 0; ww < kWarps; ++ww) v += (double)acc[ww * nd + i];
     partials[(size_t)blockIdx.x * kGmDots + i] = v;
   }
   __threadfence();
@@ -413,7 +423,7 @@ __global__ void __launch_bounds__(kGmThreads, 2) gm_dc_arnoldi(const int* __rest
   if (!am_last) return;
   __threadfence();
   // totals in fixed CTA order: warp w sums dots w, w + kWarps, ...
-  double* tot = acc;
+  double* tot = reinterpret_cast<double*>(acc);
   const int lane = tid & 31;
   for (int i = warp; i < nd; i += kWarps) {
     double a = 0.0;
