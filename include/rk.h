@@ -122,6 +122,10 @@ typedef struct {
   int not_converged;     /* solves that hit max_iter                              */
   double true_res;       /* largest relative FP64 true residual seen (-1 if none) */
   double seconds;        /* wall time of the call                                 */
+  double bytes;          /* rk_integrate_batch: algorithmic bytes of its working
+                            launches (every vector element a kernel must read or
+                            write once); 0 for the other calls, whose per-kernel
+                            bytes rk_profile_read reports                        */
 } rk_stats;
 
 typedef struct rk_problem rk_problem;

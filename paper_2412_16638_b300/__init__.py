@@ -50,7 +50,7 @@ class rk_solver_desc(ctypes.Structure):
 class rk_stats(ctypes.Structure):
     _fields_ = [("iters_total", ctypes.c_longlong), ("iters_max", ctypes.c_int), ("solves", ctypes.c_int),
                 ("refinements", ctypes.c_int), ("not_converged", ctypes.c_int), ("true_res", ctypes.c_double),
-                ("seconds", ctypes.c_double)]
+                ("seconds", ctypes.c_double), ("bytes", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -1,9 +1,8 @@
 // Batched-step kernels for bf16 storage (one translation unit per storage type
-// so the large kernel instantiations compile in parallel).
+// so the kernel instantiations compile in parallel).
 #define RK_BATCH_INSTANTIATE
 #include "rk_batch.cuh"
 
 namespace rk {
-template int batch_grid_s<__nv_bfloat16>(int, const LaunchCfg&, int, int);
-template void batch_launch_s<__nv_bfloat16>(int, const LaunchCfg&, int, BatchItem*, const int*, int, double, int*, cudaStream_t);
+template rk_status batch_group_run<__nv_bfloat16>(rk_problem**, int, double, int, cudaStream_t, int, BatchTotals*);
 }  // namespace rk
