@@ -503,23 +503,25 @@ def run_advdiff_key(c, n, steps, warmup, basis=None):
     tab = rk.tableaux.get("dirk3")
     stream = c.stream
 
-    def make(storage, tol, correct, basis=None):
+    def make(storage, tol, correct, basis=None, tau=0.0):
         kw = {} if basis is None else {"basis": basis}
         return rk.Problem(rk.problem_desc(op=rk.RK_OP_ADVDIFF_CSR, n=n, kappa_field=kap, vel=vel),
                           rk.solver_desc(krylov=rk.RK_KRYLOV_GMRES, restart=30, bj_block=8, tol_rel=tol,
-                                         storage=storage, correct=correct, max_iter=3000, **kw),
+                                         storage=storage, correct=correct, max_iter=3000, bj_adapt_tau=tau, **kw),
                           tableau=tab, u0=u0, stream=stream.cuda_stream)
 
     with make("f64", 1e-12, 0) as q:
         rk.rk_integrate(q.h, dt, warmup + steps)
         ref = q.state()
-    variants = {"mixed_f32": ("f32", 1e-8, 1, None), "fp64_plain": ("f64", 1e-8, 0, None)}
+    # adaptive-precision block-Jacobi (tau 1e-2: FP16 block inverses where kappa_1 <= 20)
+    variants = {"mixed_f32": ("f32", 1e-8, 1, None, 0.0), "mixed_f32_adaptive_bj": ("f32", 1e-8, 1, None, 1e-2),
+                "fp64_plain": ("f64", 1e-8, 0, None, 0.0)}
     if basis:
-        variants["mixed_f32_basis_" + basis] = ("f32", 1e-8, 1, basis)
+        variants["mixed_f32_basis_" + basis] = ("f32", 1e-8, 1, basis, 0.0)
     res = {}
     peak, peak_kind = measured_peaks()
-    for name, (storage, tol, corr, bas) in variants.items():
-        with make(storage, tol, corr, bas) as p:
+    for name, (storage, tol, corr, bas, tau) in variants.items():
+        with make(storage, tol, corr, bas, tau) as p:
             rk.rk_integrate(p.h, dt, warmup)
             rk.rk_profile(p.h, True)
             torch.cuda.synchronize()
@@ -531,7 +533,9 @@ def run_advdiff_key(c, n, steps, warmup, basis=None):
             prof, launches = rk.rk_profile_read(p.h)
             secs = e0.elapsed_time(e1) / 1e3
             u = p.state()
+            info = rk.rk_get_problem_info(p.h)
         res[name] = {"value": N * steps / secs, "ms_per_step": 1e3 * secs / steps,
+                     "bj_half_blocks": info.bj_half_blocks, "bj_blocks": info.bj_blocks,
                      "iters_per_solve": st.iters_total / max(st.solves, 1), "err_vs_fp64_tight": rel(u, ref),
                      "gpu_launches": launches, "roofline": roofline_of(prof, peak, peak_kind),
                      "kernels": kernel_table(prof)}
@@ -539,7 +543,8 @@ def run_advdiff_key(c, n, steps, warmup, basis=None):
             "config": {"grid": "%d^3" % n, "kappa": "exp(Gaussian field, sigma 0.5, l 0.1), seed 0",
                        "vel": vel, "tableau": "dirk3", "dt": dt, "krylov": "gmres(30)", "bj_block": 8,
                        "tol_rel": 1e-8, "u0": "Gaussian bump"},
-            "variants": res, "speedup_vs_fp64": res["mixed_f32"]["value"] / res["fp64_plain"]["value"]}
+            "variants": res, "speedup_vs_fp64": res["mixed_f32"]["value"] / res["fp64_plain"]["value"],
+            "speedup_vs_fp64_adaptive_bj": res["mixed_f32_adaptive_bj"]["value"] / res["fp64_plain"]["value"]}
 
 
 def run_serve_key(c, njobs, slots=64, budget=120 << 30):

@@ -112,6 +112,11 @@ typedef struct {
                       stopping rule stays relative to ||rhs||); 0 = from zero, as
                       the paper's description implies.  Not with RK_F16 storage
                       (its right-hand sides are rescaled per solve)                */
+  double bj_adapt_tau; /* > 0: adaptive-precision block-Jacobi (CSR operators, FP32
+                      storage; the Ginkgo feature named in Sec. 1): each block's
+                      inverse is stored in FP16 when its 1-norm condition number
+                      kappa_1 satisfies kappa_1 * 2^-11 <= bj_adapt_tau, else in
+                      FP32; 0 = every block in the storage precision             */
 } rk_solver_desc;
 
 typedef struct {
@@ -172,6 +177,19 @@ rk_status rk_destroy_problem(rk_problem* p);
  * without a fault; the per-segment sweeps (shapes the TMA sweeps do not take)
  * have no device waits.  Errors: RK_ERR_ARG. */
 rk_status rk_set_wait_limit(rk_problem* p, unsigned long long spins);
+
+/* Introspection of a problem: device bytes the library allocated for it, kernel
+ * launches issued so far, and the block-Jacobi blocks of the last
+ * preconditioner set-up on the CSR path with how many of them adaptive
+ * precision stored in FP16 (0 / 0 before a set-up and on the heat path). */
+typedef struct {
+  size_t device_bytes;
+  long long launches;
+  long long bj_blocks;
+  long long bj_half_blocks;
+} rk_problem_info;
+
+rk_status rk_get_problem_info(const rk_problem* p, rk_problem_info* info);
 
 /* ---- single operations of the step (for testing the kernels) ------------- */
 

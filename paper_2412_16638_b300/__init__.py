@@ -44,7 +44,7 @@ class rk_solver_desc(ctypes.Structure):
                 ("tol_rel", ctypes.c_double), ("tol_abs", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("storage", ctypes.c_int), ("arith", ctypes.c_int), ("correct", ctypes.c_int),
                 ("max_refine", ctypes.c_int), ("tol_true", ctypes.c_double), ("precond", ctypes.c_int),
-                ("basis", ctypes.c_int), ("warm_start", ctypes.c_int)]
+                ("basis", ctypes.c_int), ("warm_start", ctypes.c_int), ("bj_adapt_tau", ctypes.c_double)]
 
 
 class rk_stats(ctypes.Structure):
@@ -60,6 +60,14 @@ class rk_job_info(ctypes.Structure):
     _fields_ = [("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_first_step", ctypes.c_double),
                 ("t_done", ctypes.c_double), ("first_tick", ctypes.c_longlong), ("last_tick", ctypes.c_longlong),
                 ("steps", ctypes.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class rk_problem_info(ctypes.Structure):
+    _fields_ = [("device_bytes", ctypes.c_size_t), ("launches", ctypes.c_longlong), ("bj_blocks", ctypes.c_longlong),
+                ("bj_half_blocks", ctypes.c_longlong)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -83,6 +91,7 @@ _SIGS = {
     "rk_integrate": [_P, _D, _I, ctypes.POINTER(rk_stats)],
     "rk_destroy_problem": [_P],
     "rk_set_wait_limit": [_P, ctypes.c_ulonglong],
+    "rk_get_problem_info": [_P, ctypes.POINTER(rk_problem_info)],
     "rk_apply_op": [_P, _P, _P, _I],
     "rk_solve": [_P, _D, _P, _P, _I, ctypes.POINTER(rk_stats)],
     "rk_apply_precond": [_P, _D, _P, _P, _I],
@@ -162,7 +171,7 @@ def problem_desc(op=RK_OP_HEAT7, n=32, kappa=1.0, kappa_field=None, vel=(0.0, 0.
 
 def solver_desc(krylov=RK_KRYLOV_CG, restart=30, bj_block=8, tol_rel=1e-8, tol_abs=0.0, max_iter=1000,
                 storage="f32", arith=None, correct=None, max_refine=0, tol_true=0.0, precond="bj", basis=None,
-                warm_start=False):
+                warm_start=False, bj_adapt_tau=0.0):
     s = rk_solver_desc()
     st = DTYPES[storage] if isinstance(storage, str) else storage
     s.krylov, s.restart, s.bj_block = krylov, restart, bj_block
@@ -174,6 +183,7 @@ def solver_desc(krylov=RK_KRYLOV_CG, restart=30, bj_block=8, tol_rel=1e-8, tol_a
     s.precond = PRECONDS[precond] if isinstance(precond, str) else precond
     s.basis = 0 if basis is None else (DTYPES[basis] if isinstance(basis, str) else basis)
     s.warm_start = int(bool(warm_start))
+    s.bj_adapt_tau = float(bj_adapt_tau)
     return s
 
 
@@ -218,6 +228,12 @@ def rk_integrate(p, dt, nsteps, allow_not_converged=False):
 
 def rk_destroy_problem(p):
     return _check(_lib.rk_destroy_problem(p))
+
+
+def rk_get_problem_info(p):
+    info = rk_problem_info()
+    _check(_lib.rk_get_problem_info(p, ctypes.byref(info)))
+    return info
 
 
 def rk_set_wait_limit(p, spins):

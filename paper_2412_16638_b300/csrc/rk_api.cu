@@ -710,6 +710,15 @@ static rk_status check_solver(const rk_solver_desc* s, const rk_problem_desc* d)
     set_error("warm_start is implemented for CG with FP64, FP32 or BF16 storage");
     return RK_ERR_ARG;
   }
+  if (!(s->bj_adapt_tau >= 0.0) || !std::isfinite(s->bj_adapt_tau)) {
+    set_error("bj_adapt_tau must be finite and >= 0");
+    return RK_ERR_ARG;
+  }
+  if (s->bj_adapt_tau > 0.0 &&
+      (s->storage != RK_F32 || s->precond != RK_PREC_BLOCK_JACOBI || (d && d->op == RK_OP_HEAT7))) {
+    set_error("adaptive-precision block-Jacobi (bj_adapt_tau > 0) is built for the CSR operators with FP32 storage");
+    return RK_ERR_ARG;
+  }
   if (s->precond != RK_PREC_BLOCK_JACOBI && s->precond != RK_PREC_FDM) {
     set_error("unknown preconditioner %d", s->precond);
     return RK_ERR_ARG;
@@ -881,6 +890,18 @@ rk_status rk_create_problem(const rk_problem_desc* desc, const rk_solver_desc* s
     return st;
   }
   *out = p;
+  return RK_OK;
+}
+
+rk_status rk_get_problem_info(const rk_problem* p, rk_problem_info* info) {
+  if (!p || !info) {
+    set_error("rk_get_problem_info: NULL argument");
+    return RK_ERR_ARG;
+  }
+  info->device_bytes = p->bytes;
+  info->launches = p->launches;
+  info->bj_blocks = p->bj_blocks;
+  info->bj_half_blocks = p->bj_half_blocks;
   return RK_OK;
 }
 

@@ -37,7 +37,9 @@ __global__ void __launch_bounds__(kThreads) csr_apply_f64_kernel(CsrView A, cons
 struct CsrMinv {
   double shift = 0.0;
   void* dev = nullptr;
+  unsigned char* flags = nullptr;  // adaptive precision: 1 = block stored in FP16
   bool valid = false;
+  long long half_blocks = 0;       // blocks stored in FP16 (adaptive precision)
 };
 
 struct GmresWork {
@@ -258,8 +260,10 @@ rk_status csr_free(rk_problem* p) {
     if (w->partials) cudaFree(w->partials);
     if (w->sc) cudaFree(w->sc);
     if (w->h_sc) cudaFreeHost(w->h_sc);
-    for (auto& e : w->minv)
+    for (auto& e : w->minv) {
       if (e.dev) cudaFree(e.dev);
+      if (e.flags) cudaFree(e.flags);
+    }
     delete w;
     p->gw = nullptr;
   }
@@ -296,8 +300,9 @@ rk_status csr_correct_f64(rk_problem* p, double shift, const double* gv, const v
   return st;
 }
 
-// Per-block inverses of I - shift L for this shift (cached, 4 shifts).
-static rk_status csr_minv(rk_problem* p, double shift, const void** out) {
+// Per-block inverses of I - shift L for this shift (cached, 4 shifts); with
+// adaptive precision also the per-block FP16 flags.
+static rk_status csr_minv(rk_problem* p, double shift, const void** out, const unsigned char** flags_out = nullptr) {
   if (!p->gw) {
     GmresWork* w = new GmresWork();
     p->gw = w;
@@ -306,6 +311,7 @@ static rk_status csr_minv(rk_problem* p, double shift, const void** out) {
   for (auto& e : w->minv)
     if (e.valid && e.shift == shift) {
       *out = e.dev;
+      if (flags_out) *flags_out = e.flags;
       return RK_OK;
     }
   CsrMinv& e = w->minv[w->minv_next];
@@ -314,6 +320,8 @@ static rk_status csr_minv(rk_problem* p, double shift, const void** out) {
   const long long nbl = (p->n + bs - 1) / bs;
   const long long nblocks = (long long)p->n * p->n * nbl;
   if (!e.dev) RK_TRY(alloc_dev(p, &e.dev, (size_t)nblocks * bs * bs * dtype_size(p->sol.storage)));
+  const double tau = p->sol.bj_adapt_tau;
+  if (tau > 0.0 && !e.flags) RK_TRY(alloc_dev(p, (void**)&e.flags, (size_t)nblocks));
   rk_status st = RK_OK;
   dispatch_st(p->sol.storage, [&](auto ts, auto) {
     using S = typename decltype(ts)::type;
@@ -322,7 +330,7 @@ static rk_status csr_minv(rk_problem* p, double shift, const void** out) {
       auto kern = csr_bj_setup<S, BS>;
       launch(p, K_CSR_BJ_SETUP, (double)p->csr.nnz * 12.0 + (double)nblocks * BS * BS * sizeof(S), [&] {
         kern<<<grid_for((const void*)kern, nblocks), kThreads, 0, p->st>>>(view(p), p->csr.v64, p->n, shift,
-                                                                          static_cast<S*>(e.dev));
+                                                                          static_cast<S*>(e.dev), tau, e.flags);
       });
       if (cudaGetLastError() != cudaSuccess) st = RK_ERR_CUDA;
     });
@@ -331,15 +339,26 @@ static rk_status csr_minv(rk_problem* p, double shift, const void** out) {
     set_error("csr_bj_setup launch failed");
     return st;
   }
+  e.half_blocks = 0;
+  if (e.flags) {  // count the FP16 blocks (statistics of the adaptive choice)
+    std::vector<unsigned char> f((size_t)nblocks);
+    RK_CUDA(cudaMemcpyAsync(f.data(), e.flags, f.size(), cudaMemcpyDeviceToHost, p->st));
+    RK_CUDA(cudaStreamSynchronize(p->st));
+    for (unsigned char v : f) e.half_blocks += v;
+  }
+  p->bj_half_blocks = e.half_blocks;
+  p->bj_blocks = nblocks;
   e.shift = shift;
   e.valid = true;
   *out = e.dev;
+  if (flags_out) *flags_out = e.flags;
   return RK_OK;
 }
 
 rk_status csr_precond_f64(rk_problem* p, double shift, const double* r, double* z) {
   const void* minv = nullptr;
-  RK_TRY(csr_minv(p, shift, &minv));
+  const unsigned char* flags = nullptr;
+  RK_TRY(csr_minv(p, shift, &minv, &flags));
   rk_status st = RK_OK;
   dispatch_st(p->sol.storage, [&](auto ts, auto tt) {
     using S = typename decltype(ts)::type;
@@ -350,7 +369,8 @@ rk_status csr_precond_f64(rk_problem* p, double shift, const double* r, double* 
       HeatGeo g{p->n, (p->n + SEG - 1) / SEG, (long long)p->n * p->n, p->N};
       auto kern = csr_bj_apply_f64io<S, T, BS, SEG>;
       launch(p, K_BJ, (16.0 + BS * sizeof(S)) * p->N, [&] {
-        kern<<<grid_for((const void*)kern, g.n2 * g.nseg), kThreads, 0, p->st>>>(g, static_cast<const S*>(minv), r, z);
+        kern<<<grid_for((const void*)kern, g.n2 * g.nseg), kThreads, 0, p->st>>>(g, static_cast<const S*>(minv), flags,
+                                                                                r, z);
       });
       if (cudaGetLastError() != cudaSuccess) st = RK_ERR_CUDA;
     });
@@ -374,7 +394,8 @@ rk_status gmres_solve(rk_problem* p, double shift, const double* g64, RhsScalars
   }
   GmresWork* w = p->gw;
   const void* minv = nullptr;
-  RK_TRY(csr_minv(p, shift, &minv));
+  const unsigned char* mflags = nullptr;
+  RK_TRY(csr_minv(p, shift, &minv, &mflags));
   const int m = p->sol.restart;
   GmScalars* hs = w->h_sc;
   std::memset(hs, 0, kGmHeader);
@@ -417,6 +438,11 @@ rk_status gmres_solve(rk_problem* p, double shift, const double* g64, RhsScalars
       const double Nb = (double)p->N * sizeof(B);
       const double mat = (double)p->csr.nnz * (4.0 + sizeof(S)) + 4.0 * (p->N + 1);
       const double sell = (double)p->N * kSellW * (4.0 + sizeof(S));
+      // block inverses read per apply: BS entries per row, FP16 for the
+      // adaptively stored blocks, plus one flag byte per block
+      const double fhalf = p->bj_blocks > 0 ? (double)p->bj_half_blocks / (double)p->bj_blocks : 0.0;
+      const double minv_bytes = (double)BS * p->N * (sizeof(S) * (1.0 - fhalf) + 2.0 * fhalf) +
+                                (mflags ? (double)p->bj_blocks : 0.0);
       auto k_start = gm_start<S, B, T, SEG>;
       auto k_restart = gm_restart<S, B, T, SEG>;
       auto k_prec = gm_dc_prec<S, B, T, BS, SEG>;
@@ -467,8 +493,8 @@ rk_status gmres_solve(rk_problem* p, double shift, const double* g64, RhsScalars
         for (int c = 0; c < chunk; ++c) {
           const int idx = launched + c;
           const double jb = (double)(idx % (m + 1));
-          prof_begin(p, K_GM_PREC, Nb + Ns + BS * Ns, solve, idx);
-          k_prec<<<gp, kThreads, 0, p->st>>>(g, V, ldv, M, z, w->sc);
+          prof_begin(p, K_GM_PREC, Nb + Ns + minv_bytes, solve, idx);
+          k_prec<<<gp, kThreads, 0, p->st>>>(g, V, ldv, M, mflags, z, w->sc);
           prof_end(p);
           prof_begin(p, K_GM_ARNOLDI, sell + Ns + Nb + (jb + 1.0) * Nb, solve, idx);
           k_arn<<<ga, kGmThreads, smem, p->st>>>(w->scol, static_cast<const S*>(w->sval), cs, z, V, ldv, wb,
@@ -500,8 +526,8 @@ rk_status gmres_solve(rk_problem* p, double shift, const double* g64, RhsScalars
           return;
         }
         if (hs->cycle_end) {
-          launch(p, K_GM_UPDATE, (double)hs->jused * Nb + 2.0 * Nx + BS * Ns,
-                 [&] { k_upd<<<gp, kThreads, 0, p->st>>>(g, V, ldv, M, xs, w->sc); });
+          launch(p, K_GM_UPDATE, (double)hs->jused * Nb + 2.0 * Nx + minv_bytes,
+                 [&] { k_upd<<<gp, kThreads, 0, p->st>>>(g, V, ldv, M, mflags, xs, w->sc); });
           if (hs->done) break;
           launch(p, K_GM_INIT, mat + Nx + 8.0 * p->N + Nb, [&] {
             k_restart<<<gs, kThreads, 0, p->st>>>(g, view(p), lv, cs, g64, rs, xs, V, w->sc, w->partials);

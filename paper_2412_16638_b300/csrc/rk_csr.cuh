@@ -92,10 +92,16 @@ __global__ void __launch_bounds__(kThreads) csr_correct_f64_kernel(CsrView A, co
 // per block: the block of a 7-point operator restricted to an x-line segment
 // is tridiagonal; its inverse is formed column by column with the Thomas
 // recurrences in FP64 (the blocks are diagonally dominant M-matrices, so no
-// pivoting is needed) and stored row-major, zero padded to BS x BS.
+// pivoting is needed) and stored row-major, zero padded to BS x BS, in a slot
+// of BS*BS storage elements.  Adaptive precision (tau > 0; the
+// adaptive-precision block-Jacobi of Ginkgo, Sec. 1): a block whose 1-norm
+// condition number kappa_1 = ||D||_1 ||D^-1||_1 satisfies
+// kappa_1 * 2^-11 <= tau is stored in FP16 in the first half of its slot and
+// flagged (flags[b] = 1); flags may be null when tau <= 0.
 template <typename S, int BS>
 __global__ void __launch_bounds__(kThreads) csr_bj_setup(CsrView A, const double* __restrict__ vals, int n,
-                                                         double shift, S* __restrict__ minv) {
+                                                         double shift, S* __restrict__ minv, double tau,
+                                                         unsigned char* __restrict__ flags) {
   const int nbl = (n + BS - 1) / BS;
   const long long nblocks = (long long)n * n * nbl;
   for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < nblocks;
@@ -124,7 +130,8 @@ __global__ void __launch_bounds__(kThreads) csr_bj_setup(CsrView A, const double
       den[i] = di[i] - (i > 0 ? lo[i] * cp[i - 1] : 0.0);
       cp[i] = (i + 1 < m) ? up[i] / den[i] : 0.0;
     }
-    S* out = minv + b * BS * BS;
+    double inv[BS][BS];
+    double ninv = 0.0, nblk = 0.0;  // 1-norms of the inverse and of the block
     for (int jcol = 0; jcol < BS; ++jcol) {
       double xcol[BS];
       if (jcol < m) {
@@ -133,18 +140,38 @@ __global__ void __launch_bounds__(kThreads) csr_bj_setup(CsrView A, const double
           const double rhs = (i == jcol) ? 1.0 : 0.0;
           dp[i] = (rhs - (i > 0 ? lo[i] * dp[i - 1] : 0.0)) / den[i];
         }
-        for (int i = m - 1; i >= 0; --i) xcol[i] = dp[i] - (i + 1 < m ? cp[i] * xcol[i + 1] : 0.0);
+        double cs = 0.0;
+        for (int i = m - 1; i >= 0; --i) {
+          xcol[i] = dp[i] - (i + 1 < m ? cp[i] * xcol[i + 1] : 0.0);
+          cs += fabs(xcol[i]);
+        }
+        ninv = fmax(ninv, cs);
+        // column jcol of the block: up[jcol-1], di[jcol], lo[jcol+1]
+        const double bc = fabs(di[jcol]) + (jcol > 0 ? fabs(up[jcol - 1]) : 0.0) +
+                          (jcol + 1 < m ? fabs(lo[jcol + 1]) : 0.0);
+        nblk = fmax(nblk, bc);
       }
-      for (int i = 0; i < BS; ++i)
-        out[i * BS + jcol] = nar<S>((i < m && jcol < m) ? xcol[i] : 0.0);
+      for (int i = 0; i < BS; ++i) inv[i][jcol] = (i < m && jcol < m) ? xcol[i] : 0.0;
     }
+    const bool low = tau > 0.0 && nblk * ninv * 0x1p-11 <= tau;
+    S* out = minv + b * BS * BS;
+    if (low) {
+      __half* oh = reinterpret_cast<__half*>(out);
+      for (int i = 0; i < BS; ++i)
+        for (int jcol = 0; jcol < BS; ++jcol) oh[i * BS + jcol] = __double2half(inv[i][jcol]);
+    } else {
+      for (int i = 0; i < BS; ++i)
+        for (int jcol = 0; jcol < BS; ++jcol) out[i * BS + jcol] = nar<S>(inv[i][jcol]);
+    }
+    if (flags) flags[b] = low ? 1 : 0;
   }
 }
 
-// z = D^{-1} r for the blocks of one segment (per-block inverses in S).
+// z = D^{-1} r for the blocks of one segment (per-block inverses in S, or in
+// FP16 where flags marks the block).
 template <typename T, typename S, int BS, int SEG>
-__device__ __forceinline__ void bj_apply_blocks(const S* __restrict__ minv, long long line, int nbl, int i0,
-                                                const T (&r)[SEG], T (&z)[SEG]) {
+__device__ __forceinline__ void bj_apply_blocks(const S* __restrict__ minv, const unsigned char* __restrict__ flags,
+                                                long long line, int nbl, int i0, const T (&r)[SEG], T (&z)[SEG]) {
 #pragma unroll
   for (int cb = 0; cb < SEG / BS; ++cb) {
     const int bi = i0 / BS + cb;
@@ -153,11 +180,16 @@ __device__ __forceinline__ void bj_apply_blocks(const S* __restrict__ minv, long
       for (int i = 0; i < BS; ++i) z[cb * BS + i] = T(0);
       continue;
     }
-    const S* M = minv + (line * nbl + bi) * (long long)(BS * BS);
+    const long long blk = line * nbl + bi;
+    const S* M = minv + blk * (long long)(BS * BS);
+    const bool half_block = flags != nullptr && flags[blk] != 0;
 #pragma unroll
     for (int i = 0; i < BS; ++i) {
       T row[BS];
-      load_seg<T, S, BS>(M + i * BS, BS, row);
+      if (half_block)
+        load_seg<T, __half, BS>(reinterpret_cast<const __half*>(M) + i * BS, BS, row);
+      else
+        load_seg<T, S, BS>(M + i * BS, BS, row);
       T a = T(0);
 #pragma unroll
       for (int jj = 0; jj < BS; ++jj) a = fma(row[jj], r[cb * BS + jj], a);
@@ -168,6 +200,7 @@ __device__ __forceinline__ void bj_apply_blocks(const S* __restrict__ minv, long
 
 template <typename S, typename T, int BS, int SEG>
 __global__ void __launch_bounds__(kThreads) csr_bj_apply_f64io(HeatGeo g, const S* __restrict__ minv,
+                                                               const unsigned char* __restrict__ flags,
                                                                const double* __restrict__ r, double* __restrict__ z) {
   const int nbl = (g.n + BS - 1) / BS;
   RK_SEG_LOOP(g, SEG)
@@ -178,7 +211,7 @@ __global__ void __launch_bounds__(kThreads) csr_bj_apply_f64io(HeatGeo g, const 
     T rv[SEG], zv[SEG];
 #pragma unroll
     for (int e = 0; e < SEG; ++e) rv[e] = (e < m) ? rnd<S, T>((T)rd[e]) : T(0);
-    bj_apply_blocks<T, S, BS, SEG>(minv, line, nbl, i0, rv, zv);
+    bj_apply_blocks<T, S, BS, SEG>(minv, flags, line, nbl, i0, rv, zv);
     double zd[SEG];
 #pragma unroll
     for (int e = 0; e < SEG; ++e) zd[e] = (double)rnd<S, T>(zv[e]);
@@ -321,6 +354,7 @@ __global__ void __launch_bounds__(kThreads) gm_restart(HeatGeo g, CsrView A, con
 template <typename S, typename B, typename T, int BS, int SEG>
 __global__ void __launch_bounds__(kThreads) gm_update(HeatGeo g, const B* __restrict__ V, long long ldv,
                                                       const S* __restrict__ minv,
+                                                      const unsigned char* __restrict__ flags,
                                                       typename XOf<S>::type* __restrict__ x, GmScalars* sc) {
   using X = typename XOf<S>::type;
   if (!sc->cycle_end) return;
@@ -339,7 +373,7 @@ __global__ void __launch_bounds__(kThreads) gm_update(HeatGeo g, const B* __rest
 #pragma unroll
       for (int e = 0; e < SEG; ++e) u[e] = fma(yi, vi[e], u[e]);
     }
-    bj_apply_blocks<T, S, BS, SEG>(minv, line, nbl, i0, u, zv);
+    bj_apply_blocks<T, S, BS, SEG>(minv, flags, line, nbl, i0, u, zv);
     load_seg<T, X, SEG>(x + base, m, xv);
 #pragma unroll
     for (int e = 0; e < SEG; ++e) xv[e] += zv[e];

@@ -109,10 +109,12 @@ struct TileRing {
   }
 };
 
-// z = M^{-1} u_j (block-Jacobi with per-block inverses), u_j unnormalised.
+// z = M^{-1} u_j (block-Jacobi with per-block inverses, FP16 where flags
+// marks a block), u_j unnormalised.
 template <typename S, typename B, typename T, int BS, int SEG>
 __global__ void __launch_bounds__(kThreads) gm_dc_prec(HeatGeo g, const B* __restrict__ V, long long ldv,
-                                                       const S* __restrict__ minv, S* __restrict__ z,
+                                                       const S* __restrict__ minv,
+                                                       const unsigned char* __restrict__ flags, S* __restrict__ z,
                                                        const GmScalars* sc) {
   if (sc->done || sc->cycle_end || sc->j >= sc->m) return;
   const B* Vj = V + (long long)sc->j * ldv;
@@ -122,7 +124,7 @@ __global__ void __launch_bounds__(kThreads) gm_dc_prec(HeatGeo g, const B* __res
     (void)k;
     T v[SEG], zv[SEG];
     load_seg<T, B, SEG>(Vj + base, m, v);
-    bj_apply_blocks<T, S, BS, SEG>(minv, line, nbl, i0, v, zv);
+    bj_apply_blocks<T, S, BS, SEG>(minv, flags, line, nbl, i0, v, zv);
     store_seg<S, T, SEG>(z + base, m, zv);
   RK_SEG_LOOP_END
 }

@@ -234,6 +234,8 @@ struct rk_problem {
   // into ke[i]
   bool ke_hi = false;
   void* wx = nullptr;
+  // block-Jacobi statistics of the last preconditioner set-up (CSR path)
+  long long bj_blocks = 0, bj_half_blocks = 0;
   // reductions / device scalars
   double* partials = nullptr;
   rk::CgScalars* sc = nullptr;

@@ -181,3 +181,58 @@ def test_step_compressed_basis_within_fp32_bound(rk):
     ref = dirk.integrate(u0, dt, steps, tableau.get("dirk3"), operators.CSROperator(n, oracle_L(n)),
                          dirk.Solver("gmres", bs=8, tol_rel=1e-13))
     assert rel_l2(u, ref) < 1e-6
+
+
+def _adaptive(rk, n, tau, tol=1e-7, correct=None, tab=None, u0=None, bs=8):
+    return rk.Problem(rk.problem_desc(op=rk.RK_OP_ADVDIFF_CSR, n=n, kappa_field=synth.kappa_field(n, seed=0),
+                                      vel=VEL),
+                      rk.solver_desc(krylov=rk.RK_KRYLOV_GMRES, restart=30, bj_block=bs, tol_rel=tol, storage="f32",
+                                     max_iter=3000, correct=correct, bj_adapt_tau=tau),
+                      tableau=tab, u0=u0)
+
+
+@pytest.mark.parametrize("n,bs,shift", [(20, 8, 5e-3), (13, 4, 2e-2)])
+def test_csr_block_jacobi_adaptive_precision(rk, n, bs, shift):
+    """Adaptive-precision block-Jacobi: with tau between two blocks' condition
+    numbers, the library stores the same blocks in FP16 as the oracle's rule,
+    and z = D^{-1} r matches the oracle's rounded inverses to FP32 arithmetic."""
+    M = krylov.shifted(oracle_L(n), shift)
+    kap = np.sort(np.concatenate(krylov.AdaptiveBlockJacobi(M, n, bs).kappas))
+    mid = len(kap) // 2
+    assert kap[mid] > kap[mid - 1]
+    tau = 0.5 * (kap[mid - 1] + kap[mid]) * krylov.U_HALF
+    ref_bj = krylov.AdaptiveBlockJacobi(M, n, bs, tau=tau)
+    r = rng_vec(n, 77)
+    with _adaptive(rk, n, tau, bs=bs) as p:
+        z = np.empty_like(r)
+        rk.rk_apply_precond(p.h, shift, r, z)
+        info = rk.rk_get_problem_info(p.h)
+    assert info.bj_blocks == ref_bj.total_blocks
+    assert info.bj_half_blocks == ref_bj.low_blocks
+    assert 0 < ref_bj.low_blocks < ref_bj.total_blocks
+    # the library rounds r to FP32 and applies in FP32 arithmetic
+    assert rel_l2(z, ref_bj.apply(r.astype(np.float32).astype(np.float64))) < 2e-6
+
+
+def test_gmres_and_step_with_adaptive_block_jacobi(rk):
+    """GMRES with every block stored in FP16 (tau 1e-2: the blocks of this
+    operator have kappa_1 < 6) still converges to the oracle's solution at the
+    FP32 tolerance, and a mixed-precision step stays within the FP32 bound."""
+    n, shift = 24, 5e-4
+    g = oracle_L(n) @ synth.gaussian_bump(n)
+    with _adaptive(rk, n, 1e-2) as p:
+        k = np.empty_like(g)
+        st = rk.rk_solve(p.h, shift, g, k)
+        info = rk.rk_get_problem_info(p.h)
+    assert info.bj_half_blocks == info.bj_blocks > 0
+    M = krylov.shifted(oracle_L(n), shift)
+    ref = krylov.gmres(lambda v: M @ v, krylov.BlockJacobi(M, n, 8).apply, g, restart=30, tol_rel=1e-13).x
+    assert rel_l2(k, ref) < 5e-6 and st.iters_total < 300
+    dt, steps = 5e-4, 3
+    u0 = synth.gaussian_bump(n)
+    with _adaptive(rk, n, 1e-2, tol=1e-8, correct=1, tab="dirk3", u0=u0) as p:
+        rk.rk_integrate(p.h, dt, steps)
+        u = p.state()
+    ref_u = dirk.integrate(u0, dt, steps, tableau.dirk3(), operators.CSROperator(n, oracle_L(n)),
+                           dirk.Solver("gmres", bs=8, tol_rel=1e-13, restart=30))
+    assert rel_l2(u, ref_u) < 1e-6

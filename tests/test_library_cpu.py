@@ -145,3 +145,22 @@ def _load_build():
     mod = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(mod)
     return mod
+
+
+def test_solver_option_checks_without_gpu(rk):
+    """Options accepted only where they are built: adaptive-precision
+    block-Jacobi on the CSR operators with FP32 storage; warm starts not
+    combined with refinement.  Checked before any CUDA call."""
+    h = ctypes.c_void_p()
+    d = rk.problem_desc(n=8)
+    s = rk.solver_desc(storage="f32", bj_adapt_tau=1e-2)
+    assert rk._lib.rk_create_problem(ctypes.byref(d), ctypes.byref(s), None, ctypes.byref(h)) == rk.RK_ERR_ARG
+    assert "adaptive-precision" in rk.rk_last_error()
+    s = rk.solver_desc(storage="f32", bj_adapt_tau=-1.0)
+    assert rk._lib.rk_create_problem(ctypes.byref(d), ctypes.byref(s), None, ctypes.byref(h)) == rk.RK_ERR_ARG
+    s = rk.solver_desc(storage="f32", max_refine=2, tol_true=1e-9, warm_start=True)
+    assert rk._lib.rk_create_problem(ctypes.byref(d), ctypes.byref(s), None, ctypes.byref(h)) == rk.RK_ERR_ARG
+    assert "warm_start" in rk.rk_last_error()
+    assert rk._lib.rk_set_wait_limit(None, 1) == rk.RK_ERR_ARG
+    info = rk.rk_problem_info()
+    assert rk._lib.rk_get_problem_info(None, ctypes.byref(info)) == rk.RK_ERR_ARG

@@ -99,3 +99,51 @@ def test_solvers_zero_rhs_and_abs_tol():
     assert krylov.gmres(lambda v: M @ v, lambda r: r, z).iters == 0
     g = np.full(27, 1e-3)
     assert krylov.pcg(lambda v: M @ v, lambda r: r, g, tol_rel=0.0, tol_abs=1.0).iters == 0
+
+
+def _advdiff_system(n, s):
+    return krylov.shifted(operators.advdiff_csr(n, synth.kappa_field(n, seed=1), (1.0, 0.5, 0.25)), s)
+
+
+@pytest.mark.parametrize("n,bs,s", [(6, 4, 3e-3), (7, 8, 1e-2), (9, 2, 5e-2)])
+def test_adaptive_block_jacobi_choice_and_rounding(n, bs, s):
+    """Adaptive precision: every block's choice follows kappa_1 * 2^-11 <= tau
+    with kappa_1 from LAPACK's 1-norm condition number of that block taken
+    one by one, and its inverse equals the dense inverse rounded once to FP16
+    or FP32 accordingly (tau set between two blocks' condition numbers, so
+    both precisions occur)."""
+    M = _advdiff_system(n, s)
+    probe = krylov.AdaptiveBlockJacobi(M, n, bs, tau=1e-2)
+    kap = np.sort(np.concatenate(probe.kappas))
+    mid = len(kap) // 2
+    tau = 0.5 * (kap[mid - 1] + kap[mid]) * krylov.U_HALF
+    if kap[mid - 1] == kap[mid]:
+        pytest.skip("no gap between the middle condition numbers")
+    A = krylov.AdaptiveBlockJacobi(M, n, bs, tau=tau)
+    assert 0 < A.low_blocks < A.total_blocks
+    Md = M.toarray()
+    for m, starts, inv in A.groups:
+        for st, Binv in zip(starts, inv):
+            B = Md[st:st + m, st:st + m]
+            kappa = np.linalg.cond(B, 1)
+            exact = np.linalg.inv(B)
+            want = exact.astype(np.float16 if kappa * 2.0 ** -11 <= tau else np.float32).astype(np.float64)
+            np.testing.assert_array_equal(Binv, want)
+
+
+def test_adaptive_block_jacobi_limits():
+    """tau = 0 keeps every block in FP32 (the FP32-rounded plain block-Jacobi);
+    a huge tau stores every block in FP16; the apply is linear."""
+    n, bs, s = 6, 4, 1e-2
+    M = _advdiff_system(n, s)
+    plain = krylov.BlockJacobi(M, n, bs)
+    hi = krylov.AdaptiveBlockJacobi(M, n, bs, tau=0.0)
+    lo = krylov.AdaptiveBlockJacobi(M, n, bs, tau=1e30)
+    assert hi.low_blocks == 0 and lo.low_blocks == lo.total_blocks
+    r = np.random.default_rng(3).standard_normal(n ** 3)
+    for (m, st, inv), (_, _, inv32) in zip(plain.groups, hi.groups):
+        np.testing.assert_array_equal(inv.astype(np.float32).astype(np.float64), inv32)
+    for (m, st, inv), (_, _, inv16) in zip(plain.groups, lo.groups):
+        np.testing.assert_array_equal(inv.astype(np.float16).astype(np.float64), inv16)
+    np.testing.assert_allclose(hi.apply(2.0 * r), 2.0 * hi.apply(r), rtol=1e-15)
+    assert np.linalg.norm(lo.apply(r) - plain.apply(r)) / np.linalg.norm(plain.apply(r)) < 2e-3
