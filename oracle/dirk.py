@@ -32,7 +32,8 @@ from . import fdm, krylov
 class Solver:
     """Stage solver settings: 'cg' (heat) or 'gmres' (advection-diffusion);
     precond 'bj' (x-line block-Jacobi of size bs) or 'fdm' (fast
-    diagonalization, constant-coefficient heat operators only)."""
+    diagonalization: the constant-coefficient heat operator, or the periodic
+    advection operator given as operators.PeriodicOperator)."""
 
     def __init__(self, method="cg", bs=8, tol_rel=1e-12, tol_abs=0.0, max_iter=2000, restart=30, precond="bj"):
         self.method, self.bs, self.precond = method, bs, precond
@@ -47,7 +48,9 @@ class Solver:
         per_op = self._cache.setdefault(op, {})
         key = (float(s), self.precond, self.bs)
         if key not in per_op:
-            if self.precond == "fdm":
+            if self.precond == "fdm" and hasattr(op, "beta"):
+                per_op[key] = fdm.PeriodicFastDiagonalization(op.n, op.beta, s).apply
+            elif self.precond == "fdm":
                 per_op[key] = fdm.FastDiagonalization(op.n, op.kappa, s).apply
             else:
                 M = krylov.shifted(op.csr(), s)

@@ -81,3 +81,51 @@ class FastDiagonalization:
         x = _t_m(Qb, x)
         x = _t_l(Qb, x)
         return x.reshape(-1)
+
+
+def periodic_difference(n: int):
+    """The one-dimensional periodic central difference D (Sec. 5.2.2): the
+    matrix Tridiag(-1, 0, 1) with the periodic corner entries, over 2h,
+    h = 1/n."""
+    h = 1.0 / n
+    K = np.zeros((n, n))
+    for i in range(n):
+        K[i, (i + 1) % n] += 1.0
+        K[i, (i - 1) % n] -= 1.0
+    return K / (2.0 * h)
+
+
+class PeriodicFastDiagonalization:
+    """z = P^-1 r for the periodic advection stage matrix I - s L,
+    L = -sum_d beta_d D_d (Sec. 5.2.2), by the complex fast diagonalization of
+    Eq. Pinvform.  The Kronecker-sum splitting of Eq. preconbasic is exact
+    with A = I + s beta_x D, B = s beta_y D, C = s beta_z D: the three factors
+    are polynomials in the same circulant D, so they share its (complex)
+    eigenvector matrix Q, and P_D = Lambda_C (+) Lambda_B (+) Lambda_A with
+    Lambda_A = 1 + s beta_x mu, Lambda_B = s beta_y mu, Lambda_C = s beta_z mu
+    for the eigenvalues mu of D.  D is normal, so its complex Schur
+    decomposition D = Q T Q^H (LAPACK, scipy.linalg.schur) has a diagonal T and
+    a unitary Q: Q^-1 = Q^H, also where eigenvalues repeat (mu_k = mu_{n/2-k})."""
+
+    def __init__(self, n: int, beta, s: float):
+        import scipy.linalg
+        self.n = n
+        T, self.Q = scipy.linalg.schur(periodic_difference(n).astype(np.complex128), output="complex")
+        self.mu = np.diag(T)
+        self.Qinv = self.Q.conj().T
+        la = 1.0 + s * beta[0] * self.mu
+        lb = s * beta[1] * self.mu
+        lc = s * beta[2] * self.mu
+        self.pd = lc[:, None, None] + lb[None, :, None] + la[None, None, :]  # indexed [k, j, i]
+
+    def apply(self, r):
+        n, Q, Qi = self.n, self.Q, self.Qinv
+        x = np.asarray(r, dtype=np.float64).reshape(n, n, n).astype(np.complex128)
+        x = _t_r(Qi, x)
+        x = _t_m(Qi, x)
+        x = _t_l(Qi, x)
+        x = x / self.pd
+        x = _t_r(Q, x)
+        x = _t_m(Q, x)
+        x = _t_l(Q, x)
+        return x.real.reshape(-1)

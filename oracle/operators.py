@@ -137,3 +137,12 @@ class CSROperator:
 
     def csr(self):
         return self.A
+
+
+class PeriodicOperator(CSROperator):
+    """The periodic advection operator of Sec. 5.2.2 (CSR) with its velocity,
+    so that a solver can build the complex fast diagonalization for it."""
+
+    def __init__(self, n: int, beta=(1.0, 1.0, 1.0)):
+        super().__init__(n, adv_periodic_csr(n, beta))
+        self.beta = tuple(float(b) for b in beta)

@@ -723,9 +723,22 @@ static rk_status check_solver(const rk_solver_desc* s, const rk_problem_desc* d)
     set_error("unknown preconditioner %d", s->precond);
     return RK_ERR_ARG;
   }
+  if (s->precond == RK_PREC_FDM && d && d->op == RK_OP_ADV_PERIODIC) {
+    // complex fast diagonalization of the periodic advection stage matrix
+    if (s->krylov != RK_KRYLOV_GMRES || (s->storage != RK_F32 && s->storage != RK_F64)) {
+      set_error("the periodic fast-diagonalization preconditioner runs with GMRES and FP32 or FP64 storage");
+      return RK_ERR_ARG;
+    }
+    if (d->n > 400) {
+      set_error("the periodic fast-diagonalization preconditioner needs n <= 400 (n = %d)", d->n);
+      return RK_ERR_ARG;
+    }
+    return RK_OK;
+  }
   if (s->precond == RK_PREC_FDM) {
     if (s->krylov != RK_KRYLOV_CG || (d && d->op != RK_OP_HEAT7)) {
-      set_error("the fast-diagonalization preconditioner is built for CG on the heat operator");
+      set_error("the fast-diagonalization preconditioner is built for CG on the heat operator and GMRES on the "
+                "periodic advection operator");
       return RK_ERR_ARG;
     }
     if (s->storage == RK_F64) {

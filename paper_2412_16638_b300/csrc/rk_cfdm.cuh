@@ -1,0 +1,151 @@
+// Complex fast diagonalization of the periodic advection stage matrix
+// (Sec. 3, Eq. Pinvform, applied to the operator of Sec. 5.2.2):
+// P = I - s L with L = -sum_d beta_d D_d, D the periodic central difference.
+// Every 1-D factor is a polynomial in the circulant D, whose eigenvectors are
+// the Fourier modes e^{2 pi i j k / n} with eigenvalues i sin(2 pi k / n) / h, so
+//   P^-1 r = F^-1 [ (F r)_k / (1 + i s theta_k) ],
+//   theta_k = sum_d beta_d sin(2 pi k_d / n) / h,
+// with F the 3-D discrete Fourier transform.  Each of the six passes contracts
+// one axis of the n^3 array against the n x n Fourier matrix (the mode-n
+// products T_R, T_M, T_L of Eq. TensorDecomp) and stores the result with the
+// contracted index moved to the slowest position, so every pass reads lines
+// along the fastest index and writes coalesced:
+//   [z][y][x] -> [kx][z][y] -> [ky][kx][z] -> [kz][ky][kx]   (forward, P_D^-1 in
+//   the third pass's epilogue) -> [x][kz][ky] -> [y][x][kz] -> [z][y][x]  (inverse).
+// A CTA takes a tile of kCfTile lines (fixed slow index a, consecutive middle
+// indices b) into shared memory; each output element is an n-term complex sum
+// with the twiddles e^{-+2 pi i m / n} read from a table indexed by j k mod n.
+// Arithmetic in T (FP32 for FP32 storage, FP64 for the FP64 path).
+#pragma once
+#include "rk_csr.cuh"
+
+namespace rk {
+
+constexpr int kCfTile = 32;  // lines per CTA (consecutive middle indices)
+constexpr int kCfThreads = 256;
+
+template <typename T> struct Cplx { T re, im; };
+
+template <typename T>
+__host__ __device__ constexpr size_t cfdm_smem(int n) {
+  return (size_t)kCfTile * (n + 1) * sizeof(Cplx<T>) + (size_t)n * sizeof(Cplx<T>);
+}
+
+// Parameters of the diagonal scaling P_D^-1 (third pass).
+struct CfScale {
+  double s;          // shift s of I - s L
+  double beta[3];    // velocity
+  double inv_h;      // 1 / h = n
+  double norm;       // 1 / n^3 (normalisation of the inverse transform)
+};
+
+// One pass.  in: real S (IN_REAL) or complex; out: complex, or the real part
+// in S (OUT_REAL).  tw: n twiddles e^{-2 pi i m / n}; inverse passes use the
+// conjugates.  scale != 0: divide by 1 + i s theta (and normalise), with the
+// output index (k, a, b) = (kz, ky, kx).  sc != null: the GMRES step's
+// preconditioner application, skipped when the solver state says none is due.
+// in_jstride > 0 (first pass of a GMRES step): the input is basis slot sc->j,
+// in + sc->j * in_jstride elements.
+template <typename SI, typename SO, typename T, bool IN_REAL, bool OUT_REAL>
+__global__ void __launch_bounds__(kCfThreads) cfdm_pass(const void* __restrict__ in, void* __restrict__ out, int n,
+                                                        const Cplx<T>* __restrict__ tw, int inverse, int scale,
+                                                        CfScale sp, const GmScalars* sc, long long in_jstride) {
+  if (sc && (sc->done || sc->cycle_end || sc->j >= sc->m)) return;
+  if (sc && in_jstride > 0) in = static_cast<const SI*>(in) + (long long)sc->j * in_jstride;
+  extern __shared__ __align__(128) unsigned char smem[];
+  using C = Cplx<T>;
+  C* tile = reinterpret_cast<C*>(smem);                       // [kCfTile][n + 1]
+  C* tws = tile + (size_t)kCfTile * (n + 1);                  // [n]
+  const int nbt = (n + kCfTile - 1) / kCfTile;
+  const int a = blockIdx.x / nbt;
+  const int b0 = (blockIdx.x % nbt) * kCfTile;
+  const int tb = min(kCfTile, n - b0);
+  for (int m = threadIdx.x; m < n; m += blockDim.x) {
+    C w = tw[m];
+    if (inverse) w.im = -w.im;
+    tws[m] = w;
+  }
+  // load the lines (a, b0 + bb, 0..n-1), coalesced along the line
+  for (int e = threadIdx.x; e < tb * n; e += blockDim.x) {
+    const int bb = e / n, j = e - bb * n;
+    const long long gi = ((long long)a * n + b0 + bb) * n + j;
+    C v;
+    if constexpr (IN_REAL) {
+      v.re = wid<T>(static_cast<const SI*>(in)[gi]);
+      v.im = T(0);
+    } else {
+      v = static_cast<const C*>(in)[gi];
+    }
+    tile[(size_t)bb * (n + 1) + j] = v;
+  }
+  __syncthreads();
+  // outputs (k, bb): lanes of a warp take consecutive bb (coalesced stores)
+  const int bb = threadIdx.x % kCfTile;
+  for (int k = threadIdx.x / kCfTile; k < n; k += kCfThreads / kCfTile) {
+    if (bb >= tb) continue;
+    const C* row = tile + (size_t)bb * (n + 1);
+    T re = T(0), im = T(0);
+    int idx = 0;  // j k mod n
+    for (int j = 0; j < n; ++j) {
+      const C x = row[j];
+      const C w = tws[idx];
+      re = fma(x.re, w.re, fma(-x.im, w.im, re));
+      im = fma(x.re, w.im, fma(x.im, w.re, im));
+      idx += k;
+      if (idx >= n) idx -= n;
+    }
+    const long long go = ((long long)k * n + a) * n + b0 + bb;
+    if (scale) {
+      // (kz, ky, kx) = (k, a, b); sin(2 pi m / n) = -Im e^{-2 pi i m / n}
+      const int kx = b0 + bb;
+      const T th = ((T)sp.beta[0] * (-tw[kx].im) + (T)sp.beta[1] * (-tw[a].im) + (T)sp.beta[2] * (-tw[k].im)) *
+                   (T)sp.inv_h;
+      const T c = (T)sp.s * th;
+      const T den = (T)sp.norm / fma(c, c, T(1));
+      const T r2 = fma(im, c, re) * den, i2 = fma(-re, c, im) * den;
+      re = r2;
+      im = i2;
+    }
+    if constexpr (OUT_REAL) {
+      static_cast<SO*>(out)[go] = nar<SO>(re);
+    } else {
+      C v;
+      v.re = re;
+      v.im = im;
+      static_cast<C*>(out)[go] = v;
+    }
+  }
+}
+
+// u = sum_{i < jused} y_i V_i (the cycle-end combination of the basis,
+// before the preconditioner is applied to it), stored in S.
+template <typename S, typename B, typename T>
+__global__ void __launch_bounds__(kThreads) gm_basis_combine(const B* __restrict__ V, long long ldv, long long N,
+                                                             const double* __restrict__ y, const int* jused,
+                                                             S* __restrict__ u) {
+  __shared__ T ys[kGmMax];
+  const int ju = *jused;
+  for (int i = threadIdx.x; i < ju; i += blockDim.x) ys[i] = (T)y[i];
+  __syncthreads();
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < N; r += (long long)gridDim.x * blockDim.x) {
+    T a = T(0);
+    for (int i = 0; i < ju; ++i) a = fma(ys[i], wid<T>(V[(long long)i * ldv + r]), a);
+    u[r] = nar<S>(a);
+  }
+}
+
+// out = in converted (FP64 <-> storage type; for the single-application entry point).
+template <typename A, typename B2>
+__global__ void __launch_bounds__(kThreads) convert_vec(const A* __restrict__ in, B2* __restrict__ out, long long N) {
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < N; r += (long long)gridDim.x * blockDim.x)
+    out[r] = nar<B2>(wid<double>(in[r]));
+}
+
+// x += z (x in the solution type, z the preconditioned combination).
+template <typename S, typename X>
+__global__ void __launch_bounds__(kThreads) add_into(X* __restrict__ x, const S* __restrict__ z, long long N) {
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < N; r += (long long)gridDim.x * blockDim.x)
+    x[r] = x[r] + wid<X>(z[r]);
+}
+
+}  // namespace rk

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <utility>
 
+#include "rk_cfdm.cuh"
 #include "rk_csr.cuh"
 #include "rk_gmres.cuh"
 #include "rk_internal.h"
@@ -49,6 +50,11 @@ struct GmresWork {
   int* scol = nullptr;        // sliced-ELL copy of L: columns (ldv * kSellW) ...
   void* sval = nullptr;       // ... and values lscale * L in the storage type
   long long ldv = 0;          // leading dimension: N rounded up to a whole tile
+  // complex fast diagonalization (periodic advection): twiddles, two complex
+  // work arrays, one real work vector in the storage type
+  void* cf_tw = nullptr;
+  void* cf_c[2] = {nullptr, nullptr};
+  void* cf_tmp = nullptr;
   double* partials = nullptr; // per-CTA multi-dot partials
   GmScalars* sc = nullptr;
   GmScalars* h_sc = nullptr;  // pinned header mirror
@@ -237,6 +243,27 @@ rk_status csr_setup(rk_problem* p) {
     RK_TRY(alloc_dev(p, (void**)&w->partials, (size_t)w->npart * sizeof(double)));
     RK_TRY(alloc_dev(p, (void**)&w->sc, sizeof(GmScalars)));
     RK_CUDA(cudaMemset(w->sc, 0, sizeof(GmScalars)));
+    if (p->sol.precond == RK_PREC_FDM) {
+      // twiddles e^{-2 pi i m / n} in the arithmetic type, formed in FP64
+      const int n = p->n;
+      const size_t cs = (p->sol.storage == RK_F64) ? 16 : 8;  // complex element
+      RK_TRY(alloc_dev(p, &w->cf_tw, (size_t)n * cs));
+      RK_TRY(alloc_dev(p, &w->cf_c[0], (size_t)p->N * cs));
+      RK_TRY(alloc_dev(p, &w->cf_c[1], (size_t)p->N * cs));
+      RK_TRY(alloc_dev(p, &w->cf_tmp, (size_t)p->N * s));
+      std::vector<double> t64(2 * (size_t)n);
+      for (int m = 0; m < n; ++m) {
+        const double ang = -2.0 * 3.14159265358979323846 * (double)m / (double)n;
+        t64[2 * m] = std::cos(ang);
+        t64[2 * m + 1] = std::sin(ang);
+      }
+      if (cs == 16) {
+        RK_CUDA(cudaMemcpy(w->cf_tw, t64.data(), t64.size() * 8, cudaMemcpyHostToDevice));
+      } else {
+        std::vector<float> t32(t64.begin(), t64.end());
+        RK_CUDA(cudaMemcpy(w->cf_tw, t32.data(), t32.size() * 4, cudaMemcpyHostToDevice));
+      }
+    }
     RK_CUDA(cudaMallocHost((void**)&w->h_sc, sizeof(GmScalars)));
   }
   RK_CUDA(cudaStreamSynchronize(p->st));
@@ -257,6 +284,10 @@ rk_status csr_free(rk_problem* p) {
     if (w->z) cudaFree(w->z);
     if (w->scol) cudaFree(w->scol);
     if (w->sval) cudaFree(w->sval);
+    if (w->cf_tw) cudaFree(w->cf_tw);
+    if (w->cf_c[0]) cudaFree(w->cf_c[0]);
+    if (w->cf_c[1]) cudaFree(w->cf_c[1]);
+    if (w->cf_tmp) cudaFree(w->cf_tmp);
     if (w->partials) cudaFree(w->partials);
     if (w->sc) cudaFree(w->sc);
     if (w->h_sc) cudaFreeHost(w->h_sc);
@@ -298,6 +329,70 @@ rk_status csr_correct_f64(rk_problem* p, double shift, const double* gv, const v
   });
   if (st != RK_OK) set_error("csr_correct_f64 launch failed");
   return st;
+}
+
+// z = P^-1 u for the periodic advection stage matrix by the six complex
+// passes (rk_cfdm.cuh).  u: basis slot sc->j when sc != null (a GMRES step,
+// skipped on the device when none is due), else the vector `in`.
+template <typename SI, typename S, typename T>
+static rk_status cfdm_apply(rk_problem* p, double shift, const SI* in, long long in_jstride, S* out,
+                            const GmScalars* sc, int solve, int idx) {
+  GmresWork* w = p->gw;
+  const int n = p->n;
+  const int nbt = (n + kCfTile - 1) / kCfTile;
+  const int grid = n * nbt;
+  const size_t smem = cfdm_smem<T>(n);
+  using C = Cplx<T>;
+  const C* tw = static_cast<const C*>(w->cf_tw);
+  CfScale sp{};
+  sp.s = shift;
+  sp.beta[0] = p->desc.vel[0];
+  sp.beta[1] = p->desc.vel[1];
+  sp.beta[2] = p->desc.vel[2];
+  sp.inv_h = (double)n;
+  sp.norm = 1.0 / ((double)n * n * n);
+  auto k_first = cfdm_pass<SI, S, T, true, false>;
+  auto k_mid = cfdm_pass<SI, S, T, false, false>;
+  auto k_last = cfdm_pass<SI, S, T, false, true>;
+  static bool attr_done[3] = {false, false, false};
+  const int slot = sizeof(T) == 8 ? 2 : (sizeof(SI) == 2 ? 1 : 0);
+  if (!attr_done[slot]) {
+    const int lim = (int)cfdm_smem<T>(400);
+    if (cudaFuncSetAttribute((const void*)k_first, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) != cudaSuccess ||
+        cudaFuncSetAttribute((const void*)k_mid, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) != cudaSuccess ||
+        cudaFuncSetAttribute((const void*)k_last, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("periodic fast diagonalization: shared-memory attribute refused");
+      return RK_ERR_CUDA;
+    }
+    attr_done[slot] = true;
+  }
+  const double Nc = (double)p->N * sizeof(C);
+  void* c0 = w->cf_c[0];
+  void* c1 = w->cf_c[1];
+  prof_begin(p, K_CFDM, (double)p->N * sizeof(SI) + Nc, solve, idx);
+  k_first<<<grid, kCfThreads, smem, p->st>>>(in, c0, n, tw, 0, 0, sp, sc, in_jstride);
+  prof_end(p);
+  prof_begin(p, K_CFDM, 2.0 * Nc, solve, idx);
+  k_mid<<<grid, kCfThreads, smem, p->st>>>(c0, c1, n, tw, 0, 0, sp, sc, 0);
+  prof_end(p);
+  prof_begin(p, K_CFDM, 2.0 * Nc, solve, idx);
+  k_mid<<<grid, kCfThreads, smem, p->st>>>(c1, c0, n, tw, 0, 1, sp, sc, 0);
+  prof_end(p);
+  prof_begin(p, K_CFDM, 2.0 * Nc, solve, idx);
+  k_mid<<<grid, kCfThreads, smem, p->st>>>(c0, c1, n, tw, 1, 0, sp, sc, 0);
+  prof_end(p);
+  prof_begin(p, K_CFDM, 2.0 * Nc, solve, idx);
+  k_mid<<<grid, kCfThreads, smem, p->st>>>(c1, c0, n, tw, 1, 0, sp, sc, 0);
+  prof_end(p);
+  prof_begin(p, K_CFDM, Nc + (double)p->N * sizeof(S), solve, idx);
+  k_last<<<grid, kCfThreads, smem, p->st>>>(c0, out, n, tw, 1, 0, sp, sc, 0);
+  prof_end(p);
+  if (cudaGetLastError() != cudaSuccess) {
+    set_error("periodic fast-diagonalization launch failed");
+    return RK_ERR_CUDA;
+  }
+  return RK_OK;
 }
 
 // Per-block inverses of I - shift L for this shift (cached, 4 shifts); with
@@ -356,6 +451,30 @@ static rk_status csr_minv(rk_problem* p, double shift, const void** out, const u
 }
 
 rk_status csr_precond_f64(rk_problem* p, double shift, const double* r, double* z) {
+  if (p->sol.precond == RK_PREC_FDM) {
+    if (!p->gw || !p->gw->cf_tw) {
+      set_error("periodic fast diagonalization: not set up");
+      return RK_ERR_ARG;
+    }
+    rk_status st = RK_OK;
+    dispatch_st(p->sol.storage, [&](auto ts, auto tt) {
+      using S = typename decltype(ts)::type;
+      using T = typename decltype(tt)::type;
+      if constexpr (sizeof(S) >= 4) {
+        S* tmp = static_cast<S*>(p->gw->cf_tmp);
+        S* zs = static_cast<S*>(p->gw->z);
+        auto kin = convert_vec<double, S>;
+        auto kout = convert_vec<S, double>;
+        kin<<<grid_for((const void*)kin, p->N), kThreads, 0, p->st>>>(r, tmp, p->N);
+        st = cfdm_apply<S, S, T>(p, shift, tmp, 0, zs, nullptr, -1, -1);
+        if (st == RK_OK) kout<<<grid_for((const void*)kout, p->N), kThreads, 0, p->st>>>(zs, z, p->N);
+      } else {
+        st = RK_ERR_ARG;
+      }
+    });
+    if (st == RK_OK && cudaGetLastError() != cudaSuccess) st = RK_ERR_CUDA;
+    return st;
+  }
   const void* minv = nullptr;
   const unsigned char* flags = nullptr;
   RK_TRY(csr_minv(p, shift, &minv, &flags));
@@ -395,7 +514,8 @@ rk_status gmres_solve(rk_problem* p, double shift, const double* g64, RhsScalars
   GmresWork* w = p->gw;
   const void* minv = nullptr;
   const unsigned char* mflags = nullptr;
-  RK_TRY(csr_minv(p, shift, &minv, &mflags));
+  const bool cfdm = p->sol.precond == RK_PREC_FDM;  // periodic complex fast diagonalization
+  if (!cfdm) RK_TRY(csr_minv(p, shift, &minv, &mflags));
   const int m = p->sol.restart;
   GmScalars* hs = w->h_sc;
   std::memset(hs, 0, kGmHeader);
@@ -493,9 +613,13 @@ rk_status gmres_solve(rk_problem* p, double shift, const double* g64, RhsScalars
         for (int c = 0; c < chunk; ++c) {
           const int idx = launched + c;
           const double jb = (double)(idx % (m + 1));
-          prof_begin(p, K_GM_PREC, Nb + Ns + minv_bytes, solve, idx);
-          k_prec<<<gp, kThreads, 0, p->st>>>(g, V, ldv, M, mflags, z, w->sc);
-          prof_end(p);
+          if (cfdm) {
+            if ((st = cfdm_apply<B, S, T>(p, shift, V, ldv, z, w->sc, solve, idx)) != RK_OK) return;
+          } else {
+            prof_begin(p, K_GM_PREC, Nb + Ns + minv_bytes, solve, idx);
+            k_prec<<<gp, kThreads, 0, p->st>>>(g, V, ldv, M, mflags, z, w->sc);
+            prof_end(p);
+          }
           prof_begin(p, K_GM_ARNOLDI, sell + Ns + Nb + (jb + 1.0) * Nb, solve, idx);
           k_arn<<<ga, kGmThreads, smem, p->st>>>(w->scol, static_cast<const S*>(w->sval), cs, z, V, ldv, wb,
                                                   p->N, w->sc, w->partials);
@@ -526,8 +650,21 @@ rk_status gmres_solve(rk_problem* p, double shift, const double* g64, RhsScalars
           return;
         }
         if (hs->cycle_end) {
-          launch(p, K_GM_UPDATE, (double)hs->jused * Nb + 2.0 * Nx + minv_bytes,
-                 [&] { k_upd<<<gp, kThreads, 0, p->st>>>(g, V, ldv, M, mflags, xs, w->sc); });
+          if (cfdm) {
+            // x += P^-1 (V y): the combination, the six passes, the sum
+            S* tmp = static_cast<S*>(w->cf_tmp);
+            auto kc = gm_basis_combine<S, B, T>;
+            auto ka = add_into<S, X>;
+            launch(p, K_GM_UPDATE, (double)hs->jused * Nb + Ns, [&] {
+              kc<<<grid_for((const void*)kc, p->N), kThreads, 0, p->st>>>(V, ldv, p->N, w->sc->y, &w->sc->jused, tmp);
+            });
+            if ((st = cfdm_apply<S, S, T>(p, shift, tmp, 0, z, nullptr, -1, -1)) != RK_OK) return;
+            launch(p, K_GM_UPDATE, Ns + 2.0 * Nx,
+                   [&] { ka<<<grid_for((const void*)ka, p->N), kThreads, 0, p->st>>>(xs, z, p->N); });
+          } else {
+            launch(p, K_GM_UPDATE, (double)hs->jused * Nb + 2.0 * Nx + minv_bytes,
+                   [&] { k_upd<<<gp, kThreads, 0, p->st>>>(g, V, ldv, M, mflags, xs, w->sc); });
+          }
           if (hs->done) break;
           launch(p, K_GM_INIT, mat + Nx + 8.0 * p->N + Nb, [&] {
             k_restart<<<gs, kThreads, 0, p->st>>>(g, view(p), lv, cs, g64, rs, xs, V, w->sc, w->partials);

@@ -183,7 +183,7 @@ struct FdmState {
 enum Kid {
   K_CG_INIT, K_CG_A, K_CG_B, K_OP, K_CORRECT, K_COMBINE, K_NORMS, K_WIDEN, K_TRUERES, K_ADDSCALED, K_BJ,
   K_CSR_SPMV, K_CSR_CORRECT, K_CSR_BJ_SETUP, K_GM_INIT, K_GM_ARNOLDI, K_GM_ORTH, K_GM_UPDATE,
-  K_GM_PREC, K_BATCH, K_FDM, K_FDM_SCALE, K_FDM_DOT, K_COUNT
+  K_GM_PREC, K_BATCH, K_FDM, K_FDM_SCALE, K_FDM_DOT, K_CFDM, K_COUNT
 };
 extern const char* const kKernelNames[K_COUNT];
 

@@ -8,7 +8,7 @@ const char* const kKernelNames[K_COUNT] = {
     "cg_init", "cg_sweep_a", "cg_sweep_b", "op_apply_f64", "correct_f64", "combine_f64", "vec_norms_f64",
     "widen_f64", "true_residual_f64", "add_scaled", "bj_apply", "csr_spmv", "csr_correct_f64", "csr_bj_setup",
     "gmres_init", "gmres_arnoldi", "gmres_orth", "gmres_update", "gmres_precond", "batch_step",
-    "fdm_pass", "fdm_pass_scale", "fdm_pass_dot"};
+    "fdm_pass", "fdm_pass_scale", "fdm_pass_dot", "cfdm_pass"};
 
 static cudaEvent_t take_event(Prof* pr) {
   if (!pr->pool.empty()) {

@@ -10,7 +10,7 @@ import pytest
 import synth
 from closed_forms import forced_sine_after, plane_wave_after
 from gpu_util import rel_l2, require_gpu, rng_vec
-from oracle import dirk, krylov, operators, tableau
+from oracle import dirk, fdm, krylov, operators, tableau
 
 pytestmark = pytest.mark.gpu
 
@@ -163,3 +163,59 @@ def test_forced_problems_rejected_by_batch(rk):
         with pytest.raises(rk.RKError) as e:
             rk.rk_integrate_batch([p.h], 1e-3, 1)
         assert e.value.status == rk.RK_ERR_ARG
+
+
+# ------------------------------------------- complex fast diagonalization (periodic)
+def periodic_fdm(rk, n, storage="f32", tol=1e-7, correct=None, tab=None, u0=None, beta=BETA, max_iter=200,
+                 basis=None):
+    kw = {} if basis is None else {"basis": basis}
+    return rk.Problem(rk.problem_desc(op=rk.RK_OP_ADV_PERIODIC, n=n, vel=beta),
+                      rk.solver_desc(krylov=rk.RK_KRYLOV_GMRES, restart=30, tol_rel=tol, storage=storage,
+                                     correct=correct, max_iter=max_iter, precond="fdm", **kw),
+                      tableau=tab, u0=u0)
+
+
+@pytest.mark.parametrize("n,beta,shift,storage,bound", [(20, BETA, 0.05, "f32", 2e-6), (33, (1.0, 0.5, 0.25), 0.3, "f32", 2e-6),
+                                                        (17, BETA, 0.1, "f64", 1e-12), (64, BETA, 0.1, "f32", 2e-6)])
+def test_periodic_fdm_apply_matches_oracle(rk, n, beta, shift, storage, bound):
+    """The six complex Fourier passes apply P^-1 of the periodic advection
+    stage matrix: against the oracle's fast diagonalization (LAPACK Schur
+    basis), for grids that fill the 32-line tiles and grids that do not."""
+    r = synth.gaussian_bump_periodic(n) + 0.1 * np.random.default_rng(n).standard_normal(n ** 3)
+    with periodic_fdm(rk, n, storage=storage, beta=beta) as p:
+        z = np.empty_like(r)
+        rk.rk_apply_precond(p.h, shift, r, z)
+    ref = fdm.PeriodicFastDiagonalization(n, beta, shift).apply(r)
+    assert rel_l2(z, ref) < bound
+
+
+@pytest.mark.parametrize("storage,tol,bound", [("f32", 1e-7, 1e-6), ("f64", 1e-12, 1e-10)])
+def test_periodic_fdm_gmres_few_iterations(rk, storage, tol, bound):
+    """GMRES preconditioned by the exact inverse converges in a handful of
+    iterations even at a large step (where block-Jacobi GMRES stalls), to the
+    oracle's dense-accuracy solution."""
+    n, shift = 24, 0.1 * 0.4358665215
+    g = operators.adv_periodic_csr(n, BETA) @ synth.gaussian_bump_periodic(n)
+    with periodic_fdm(rk, n, storage=storage, tol=tol) as p:
+        k = np.empty_like(g)
+        st = rk.rk_solve(p.h, shift, g, k)
+    M = krylov.shifted(operators.adv_periodic_csr(n, BETA), shift)
+    ref = fdm.PeriodicFastDiagonalization(n, BETA, shift).apply(g)
+    np.testing.assert_allclose(M @ ref, g, rtol=0, atol=1e-10 * np.abs(g).max())
+    assert rel_l2(k, ref) < bound
+    assert st.iters_total <= 4
+
+
+def test_periodic_fdm_step_large_tau_vs_oracle(rk):
+    """A mixed-precision DIRK3 step of the Gaussian bump at tau = 1/10 (beyond
+    block-Jacobi GMRES): the FP32 solves with the complex fast diagonalization
+    stay within the FP32 bound of the oracle's FP64 step."""
+    n, dt, steps = 32, 0.1, 2
+    u0 = synth.gaussian_bump_periodic(n)
+    with periodic_fdm(rk, n, tol=1e-8, correct=1, tab="dirk3", u0=u0) as p:
+        st = rk.rk_integrate(p.h, dt, steps)
+        u = p.state()
+    ref = dirk.integrate(u0, dt, steps, tableau.dirk3(), operators.PeriodicOperator(n, BETA),
+                         dirk.Solver("gmres", tol_rel=1e-13, restart=30, precond="fdm"))
+    assert rel_l2(u, ref) < 1e-6
+    assert st.iters_total <= 8 * st.solves

@@ -5,6 +5,7 @@ and the one-iteration convergence of CG with an exact preconditioner."""
 import math
 
 import numpy as np
+import scipy.sparse as sp
 import pytest
 
 from oracle import dirk, fdm, krylov, operators
@@ -120,3 +121,41 @@ def test_step_with_fdm_matches_block_jacobi_step():
     a = dirk.integrate(u0, dt, 3, tab, op, dirk.Solver("cg", bs=4, tol_rel=1e-13))
     b = dirk.integrate(u0, dt, 3, tab, op, dirk.Solver("cg", tol_rel=1e-13, precond="fdm"))
     assert np.linalg.norm(a - b) <= 1e-11 * np.linalg.norm(a)
+
+
+@pytest.mark.parametrize("n,beta,s", [(4, (1.0, 1.0, 1.0), 0.1), (6, (1.0, 0.5, 0.25), 0.03), (7, (0.3, 1.0, 2.0), 1.0)])
+def test_periodic_fdm_inverts_the_stage_matrix(n, beta, s):
+    """The complex fast diagonalization of the periodic advection stage matrix
+    is its exact inverse: P^-1 (I - s L) x = x for the independently pinned
+    periodic operator, the dense inverse on the smallest grid, and a real
+    result for real input."""
+    L = operators.adv_periodic_csr(n, beta)
+    M = (sp.identity(n ** 3) - s * L).tocsr()
+    P = fdm.PeriodicFastDiagonalization(n, beta, s)
+    x = np.random.default_rng(n).standard_normal(n ** 3)
+    np.testing.assert_allclose(P.apply(M @ x), x, rtol=0, atol=1e-11 * np.abs(x).max())
+    if n <= 4:
+        np.testing.assert_allclose(P.apply(x), np.linalg.solve(M.toarray(), x), rtol=0, atol=1e-12)
+
+
+def test_periodic_difference_spectrum_closed_form():
+    """The eigenvalues of the periodic central difference are
+    i sin(2 pi k / n) / h, k = 0 .. n-1 (Fourier modes)."""
+    n = 9
+    mu = np.linalg.eigvals(fdm.periodic_difference(n))
+    want = 1j * np.sin(2.0 * np.pi * np.arange(n) / n) * n
+    np.testing.assert_allclose(np.sort(mu.imag), np.sort(want.imag), atol=1e-10)
+    assert np.abs(mu.real).max() < 1e-10
+
+
+def test_periodic_fdm_solver_one_iteration():
+    """GMRES with the oracle's periodic fast diagonalization converges in one
+    Arnoldi step (exact preconditioner) and the step with it equals the step
+    solved densely."""
+    n, s = 6, 0.2
+    op = operators.PeriodicOperator(n, (1.0, 0.5, 0.25))
+    g = np.random.default_rng(1).standard_normal(n ** 3)
+    res = dirk.Solver("gmres", tol_rel=1e-12, precond="fdm").solve(op, s, g)
+    assert res.converged and res.iters <= 2
+    M = (sp.identity(n ** 3) - s * op.csr()).toarray()
+    np.testing.assert_allclose(res.x, np.linalg.solve(M, g), rtol=0, atol=1e-10 * np.abs(g).max())
