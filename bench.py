@@ -605,6 +605,47 @@ def run_serve_key(c, njobs, slots=64, budget=120 << 30):
                        "jobs": "the first %d of the seeded 2000-job stream" % njobs}}
 
 
+def run_fp32_floor(c, steps=10):
+    """The FP32 floor of the perturbed step: errors against the exact fully
+    discrete solution on the 256^3 mode sum (dt 1e-3, FP32 block-Jacobi CG at
+    tol 1e-6) per tableau, without and with refinement against the FP64 true
+    residual (tol_true 1e-9, k^eps then held in FP64); and the stiffest
+    problems of the batched workload (dt ||L|| > 300, 5 steps of SDIRK2)."""
+    rk = c.rk
+    out = {"heat256": [], "stiff_batch": []}
+    n, dt = 256, 1e-3
+    for tab in ("sdirk2", "dirk3", "4s3pB", "4s3pC"):
+        cfg = dict(WORKLOADS["heat256"], tableau=tab)
+        row = {"tableau": tab, "steps": steps, "dt_norm_L": dt * 12.0 * (n + 1) ** 2}
+        t = rk.tableaux.get(tab)
+        disc, _ = closed_form(n, 1.0, dt, steps, t, c.modes)
+        for label, kw in (("plain", {}), ("refined", {"max_refine": 4, "tol_true": 1e-9})):
+            with rk.Problem(rk.problem_desc(n=n, kappa=1.0),
+                            rk.solver_desc(bj_block=8, tol_rel=1e-6, storage="f32", correct=1, max_iter=2000, **kw),
+                            tableau=t, u0=c.u0(n), stream=c.stream.cuda_stream) as p:
+                st = rk.rk_integrate(p.h, dt, steps)
+                row[label] = {"err_vs_discrete": rel(p.state(), disc), "true_res_max": st.true_res,
+                              "refinements": st.refinements}
+        out["heat256"].append(row)
+    tab = rk.tableaux.get("sdirk2")
+    A = np.array(tab[0]) + np.array(tab[1])
+    b = np.array(tab[2])
+    for pr in [q for q in synth.batch_problems(512, seed=0) if 1e-3 * 12 * q.kappa * (q.n + 1) ** 2 > 300][:6]:
+        h = 1.0 / (pr.n + 1)
+        z = 1e-3 * (-12.0 * pr.kappa / h ** 2 * math.sin(math.pi * h / 2) ** 2)
+        R = 1.0 + z * (b @ np.linalg.solve(np.eye(2) - z * A, np.ones(2)))
+        exact = pr.amplitude * R ** 5 * synth.sine_mode(pr.n)
+        row = {"n": pr.n, "kappa": pr.kappa, "dt_norm_L": 1e-3 * 12 * pr.kappa * (pr.n + 1) ** 2}
+        for label, kw in (("plain", {}), ("refined", {"max_refine": 4, "tol_true": 1e-10})):
+            with rk.Problem(rk.problem_desc(n=pr.n, kappa=pr.kappa),
+                            rk.solver_desc(bj_block=8, tol_rel=1e-6, storage="f32", correct=1, max_iter=2000, **kw),
+                            tableau=tab, u0=pr.amplitude * synth.sine_mode(pr.n), stream=c.stream.cuda_stream) as p:
+                rk.rk_integrate(p.h, 1e-3, 5)
+                row[label] = rel(p.state(), exact)
+        out["stiff_batch"].append(row)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -632,6 +673,7 @@ def main():
     ap.add_argument("--advdiff", type=int, default=0, help="run only the advection-diffusion workload at this n")
     ap.add_argument("--advdiff-basis", default="", help="also run the mixed step with this GMRES basis dtype")
     ap.add_argument("--advdiff-steps", type=int, default=6)
+    ap.add_argument("--fp32-floor", action="store_true", help="run only the FP32-floor table (256^3, stiff batch)")
     args = ap.parse_args()
     cfg = dict(WORKLOADS[args.workload])
     if args.bs:
@@ -678,6 +720,9 @@ def main():
         return 0
     if args.batch:
         print(json.dumps(dict(run_batch_key(c, args.batch_steps), metric=METRIC, workload="batch512")))
+        return 0
+    if args.fp32_floor:
+        print(json.dumps(run_fp32_floor(c)))
         return 0
 
     n, dt = cfg["n"], cfg["dt"]
