@@ -16,8 +16,9 @@ timed beside it at its own loosest matched tolerance.  The line carries
 `parity_ok` (both conditions, checked at T = 0.1) and, as further keys of the
 same run: the step at tol 1e-3, FP16 and BF16 storage at 256^3, the 128^3
 (L2-resident) grid, the fast-diagonalization preconditioner, 512 batched
-problems, the 192^3 advection-diffusion GMRES pair and a slice of the serving
-workload.
+problems, the 192^3 advection-diffusion GMRES pair, the paper's periodic
+advection problem at 200^3 (complex fast diagonalization) and a slice of the
+serving workload.
 
 Metric: DOF*steps/s = n^3 * steps / seconds (device time, CUDA events on the
 library's stream), inputs resident in HBM; the 256^3 working set (about
@@ -566,6 +567,66 @@ def run_advdiff_key(c, n, steps, warmup, basis=None):
             "speedup_vs_fp64_adaptive_bj": res["mixed_f32_adaptive_bj"]["value"] / res["fp64_plain"]["value"]}
 
 
+# nominal FP32 FMA rate of the part: 128 FP32 lanes per SM x 148 SMs x 2.032 GHz
+FP32_FMA_PEAK_T = 128 * 148 * 2.032e9 / 1e12
+
+
+def run_periodic_key(c, n=200, steps=3, warmup=1, tau=0.1):
+    """The paper's periodic advection problem (Sec. 5.2.2; beta = (1,1,1), the
+    Gaussian bump, n = 200) at its largest time step tau = 1/10 with 4s3pB:
+    FP32 GMRES(30) at tol 1e-3 preconditioned by the complex fast
+    diagonalization, with FP64 corrections (mixed), against the plain FP64 step
+    with the same preconditioner in FP64.  Timed with CUDA events; errors
+    against the exact solution (the bump translated by beta t).  The roofline
+    of `cfdm_pass` is FP32 arithmetic: n complex multiply-adds (4 FMAs) per
+    element per pass, against the nominal FP32 FMA rate."""
+    rk, torch = c.rk, c.torch
+    stream = c.stream
+    beta = (1.0, 1.0, 1.0)
+    tab = rk.tableaux.get("4s3pB")
+    u0 = synth.gaussian_bump_periodic(n)
+    x, y, z = synth.periodic_coords(n)
+    t_end = (warmup + steps) * tau
+    d2 = sum(((q - 0.5 - t_end * b + 0.5) % 1.0 - 0.5) ** 2 for q, b in zip((x, y, z), beta))
+    exact = np.exp(-100.0 * d2).ravel()
+    res = {}
+    for name, storage, corr in (("mixed_f32", "f32", 1), ("fp64_plain", "f64", 0)):
+        sol = rk.solver_desc(krylov=rk.RK_KRYLOV_GMRES, restart=30, bj_block=8, tol_rel=1e-3, storage=storage,
+                             max_iter=1000, correct=corr, precond="fdm")
+        with rk.Problem(rk.problem_desc(op=rk.RK_OP_ADV_PERIODIC, n=n, vel=beta), sol, tableau=tab, u0=u0,
+                        stream=stream.cuda_stream) as p:
+            rk.rk_integrate(p.h, tau, warmup)
+            rk.rk_profile(p.h, True)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = rk.rk_integrate(p.h, tau, steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            prof, launches = rk.rk_profile_read(p.h)
+            secs = e0.elapsed_time(e1) / 1e3
+            u = p.state()
+        r = {"value": n ** 3 * steps / secs, "ms_per_step": 1e3 * secs / steps,
+             "iters_per_solve": st.iters_total / max(st.solves, 1), "err_vs_exact": rel(u, exact),
+             "gpu_launches": launches, "kernels": kernel_table(prof)}
+        cf = prof.get("cfdm_pass")
+        if cf and cf["launches"] > cf["noop_launches"]:
+            work = cf["launches"] - cf["noop_launches"]
+            fma = 4.0 * n ** 4 * work  # FMAs of the passes that ran
+            achieved = fma / (cf["ms_total"] / 1e3) / 1e12
+            r["cfdm_roofline"] = {"bound": "alu", "achieved": round(achieved, 2), "unit": "T FP32 FMA/s",
+                                  "peak": round(FP32_FMA_PEAK_T, 2), "peak_kind": "nominal (128 lanes x 148 SMs x "
+                                  "2.032 GHz)", "frac": round(achieved / FP32_FMA_PEAK_T, 4),
+                                  "avg_us": round(1e3 * cf["ms_total"] / work, 1)} if storage == "f32" else \
+                {"avg_us": round(1e3 * cf["ms_total"] / work, 1)}
+        res[name] = r
+    return {"unit": METRIC, "steps": steps, "warmup": warmup,
+            "config": {"grid": "%d^3" % n, "problem": "periodic advection, beta (1,1,1), Gaussian bump",
+                       "tableau": "4s3pB", "dt": tau, "krylov": "gmres(30)", "precond": "complex fdm",
+                       "tol_rel": 1e-3},
+            "variants": res, "speedup_vs_fp64": res["mixed_f32"]["value"] / res["fp64_plain"]["value"]}
+
+
 def run_serve_key(c, njobs, slots=64, budget=120 << 30):
     """Serving: the first `njobs` jobs of the seeded stream (Poisson arrivals,
     200 jobs/s; n in {32, 64, 96, 128, 192}, tableau in {midpoint + 1
@@ -693,6 +754,8 @@ def main():
     ap.add_argument("--advdiff-basis", default="", help="also run the mixed step with this GMRES basis dtype")
     ap.add_argument("--advdiff-steps", type=int, default=6)
     ap.add_argument("--fp32-floor", action="store_true", help="run only the FP32-floor table (256^3, stiff batch)")
+    ap.add_argument("--periodic", type=int, default=0,
+                    help="run only the periodic advection key (complex fast diagonalization) at this n")
     args = ap.parse_args()
     cfg = dict(WORKLOADS[args.workload])
     if args.bs:
@@ -742,6 +805,10 @@ def main():
         return 0
     if args.fp32_floor:
         print(json.dumps(run_fp32_floor(c)))
+        return 0
+    if args.periodic:
+        print(json.dumps(dict(run_periodic_key(c, args.periodic), metric=METRIC,
+                              workload="periodic%d" % args.periodic, data="synthetic")))
         return 0
 
     n, dt = cfg["n"], cfg["dt"]
@@ -859,7 +926,8 @@ def main():
         if cfg.get("precond", "bj") == "bj" and n <= 256:
             jobs.append(("fdm", fdm))
         jobs += [("batch512", lambda: run_batch_key(c, args.batch_steps)),
-                 ("advdiff192", lambda: run_advdiff_key(c, 192, args.advdiff_steps, 2))]
+                 ("advdiff192", lambda: run_advdiff_key(c, 192, args.advdiff_steps, 2)),
+                 ("periodic200", lambda: run_periodic_key(c, 200))]
         if args.serve_jobs > 0:
             jobs.append(("serve", lambda: run_serve_key(c, args.serve_jobs, args.serve_slots)))
         for key, fn in jobs:

@@ -14,7 +14,8 @@
 //   the third pass's epilogue) -> [x][kz][ky] -> [y][x][kz] -> [z][y][x]  (inverse).
 // A CTA takes a tile of kCfTile lines (fixed slow index a, consecutive middle
 // indices b) into shared memory; each output element is an n-term complex sum
-// with the twiddles e^{-+2 pi i m / n} read from a table indexed by j k mod n.
+// with the twiddles e^{-+2 pi i m / n} read from a table indexed by j k mod n,
+// kCfK outputs of a line per thread (the line element is read once for all).
 // Arithmetic in T (FP32 for FP32 storage, FP64 for the FP64 path).
 #pragma once
 #include "rk_csr.cuh"
@@ -23,6 +24,7 @@ namespace rk {
 
 constexpr int kCfTile = 32;  // lines per CTA (consecutive middle indices)
 constexpr int kCfThreads = 256;
+constexpr int kCfK = 4;      // outputs per thread per round
 
 template <typename T> struct Cplx { T re, im; };
 
@@ -79,40 +81,59 @@ __global__ void __launch_bounds__(kCfThreads) cfdm_pass(const void* __restrict__
     tile[(size_t)bb * (n + 1) + j] = v;
   }
   __syncthreads();
-  // outputs (k, bb): lanes of a warp take consecutive bb (coalesced stores)
+  // outputs (k, bb): lanes of a warp take consecutive bb (coalesced stores);
+  // each thread forms kCfK outputs k0, k0 + 8, ... of its line at once, so one
+  // shared-memory read of the line element serves kCfK complex products
   const int bb = threadIdx.x % kCfTile;
-  for (int k = threadIdx.x / kCfTile; k < n; k += kCfThreads / kCfTile) {
-    if (bb >= tb) continue;
-    const C* row = tile + (size_t)bb * (n + 1);
-    T re = T(0), im = T(0);
-    int idx = 0;  // j k mod n
+  if (bb >= tb) return;
+  const C* row = tile + (size_t)bb * (n + 1);
+  constexpr int kStep = kCfThreads / kCfTile;
+  for (int k0 = threadIdx.x / kCfTile; k0 < n; k0 += kStep * kCfK) {
+    T re[kCfK], im[kCfK];
+    int idx[kCfK], kk[kCfK];  // j k mod n, and k (0 for outputs past the end)
+#pragma unroll
+    for (int q = 0; q < kCfK; ++q) {
+      const int k = k0 + q * kStep;
+      kk[q] = k < n ? k : 0;
+      idx[q] = 0;
+      re[q] = im[q] = T(0);
+    }
     for (int j = 0; j < n; ++j) {
       const C x = row[j];
-      const C w = tws[idx];
-      re = fma(x.re, w.re, fma(-x.im, w.im, re));
-      im = fma(x.re, w.im, fma(x.im, w.re, im));
-      idx += k;
-      if (idx >= n) idx -= n;
+#pragma unroll
+      for (int q = 0; q < kCfK; ++q) {
+        const C w = tws[idx[q]];
+        re[q] = fma(x.re, w.re, fma(-x.im, w.im, re[q]));
+        im[q] = fma(x.re, w.im, fma(x.im, w.re, im[q]));
+        idx[q] += kk[q];
+        if (idx[q] >= n) idx[q] -= n;
+      }
     }
-    const long long go = ((long long)k * n + a) * n + b0 + bb;
-    if (scale) {
-      // (kz, ky, kx) = (k, a, b); sin(2 pi m / n) = -Im e^{-2 pi i m / n}
-      const int kx = b0 + bb;
-      const T th = ((T)sp.beta[0] * (-tw[kx].im) + (T)sp.beta[1] * (-tw[a].im) + (T)sp.beta[2] * (-tw[k].im)) *
-                   (T)sp.inv_h;
-      const T c = (T)sp.s * th;
-      const T den = (T)sp.norm / fma(c, c, T(1));
-      const T r2 = fma(im, c, re) * den, i2 = fma(-re, c, im) * den;
-      re = r2;
-      im = i2;
-    }
-    if constexpr (OUT_REAL) {
-      static_cast<SO*>(out)[go] = nar<SO>(re);
-    } else {
-      C v;
-      v.re = re;
-      v.im = im;
-      static_cast<C*>(out)[go] = v;
+#pragma unroll
+    for (int q = 0; q < kCfK; ++q) {
+      const int k = k0 + q * kStep;
+      if (k >= n) break;
+      T r = re[q], i = im[q];
+      if (scale) {
+        // (kz, ky, kx) = (k, a, b); sin(2 pi m / n) = -Im e^{-2 pi i m / n}
+        const int kx = b0 + bb;
+        const T th = ((T)sp.beta[0] * (-tw[kx].im) + (T)sp.beta[1] * (-tw[a].im) + (T)sp.beta[2] * (-tw[k].im)) *
+                     (T)sp.inv_h;
+        const T c = (T)sp.s * th;
+        const T den = (T)sp.norm / fma(c, c, T(1));
+        const T r2 = fma(i, c, r) * den, i2 = fma(-r, c, i) * den;
+        r = r2;
+        i = i2;
+      }
+      const long long go = ((long long)k * n + a) * n + b0 + bb;
+      if constexpr (OUT_REAL) {
+        static_cast<SO*>(out)[go] = nar<SO>(r);
+      } else {
+        C v;
+        v.re = r;
+        v.im = i;
+        static_cast<C*>(out)[go] = v;
+      }
     }
   }
 }
