@@ -214,10 +214,18 @@ rk_status rk_apply_precond(rk_problem* p, double shift, const double* r, double*
 
 /* ---- batched stepping (many independent problems per launch) ------------- */
 
-/* Advance `count` problems by nsteps steps of size dt each, all problems in
- * one persistent launch per step (one CTA per problem).  Every problem must
+/* Advance `count` problems by nsteps steps of size dt each.  Problems with
+ * the same storage, block size, correction mode and tableau step together:
+ * every phase of the stage loop is one launch over a work list of
+ * (problem, tile) items of all of them, with each problem's reductions summed
+ * over its own items in item order, so a problem's result does not depend on
+ * the other problems of the batch.  Every problem must
  * be RK_OP_HEAT7 with CG, have a tableau and a state, and share the stream
- * of ps[0].  stats (may be NULL) receives the totals. */
+ * of ps[0].  stats (may be NULL) receives the totals.  The launch shape of the
+ * work-list kernels (CTAs per SM) is timed on the call's first steps and
+ * cached per batch signature; the environment variable RK_BATCH_GRID_CAP
+ * (0 = the occupancy limit, 1..64) fixes it instead.  Results do not depend
+ * on the shape. */
 rk_status rk_integrate_batch(rk_problem** ps, int count, double dt, int nsteps,
                              rk_stats* stats);
 

@@ -28,9 +28,22 @@ constexpr int kCfK = 4;      // outputs per thread per round
 
 template <typename T> struct Cplx { T re, im; };
 
+// Dynamic shared memory of a pass: the line tile, a second tile for the
+// factored transform's intermediate (n1 > 1), and the twiddles.
 template <typename T>
-__host__ __device__ constexpr size_t cfdm_smem(int n) {
-  return (size_t)kCfTile * (n + 1) * sizeof(Cplx<T>) + (size_t)n * sizeof(Cplx<T>);
+__host__ __device__ constexpr size_t cfdm_smem(int n, int n1) {
+  return (size_t)(n1 > 1 ? 2 : 1) * kCfTile * (n + 1) * sizeof(Cplx<T>) + (size_t)n * sizeof(Cplx<T>);
+}
+
+// Factor n = n1 n2 for the two-step transform: n1 the largest divisor of n
+// not above sqrt(n) (1 for a prime n: the direct n-term sums), provided the
+// two tiles fit in smem_limit bytes.
+inline int cfdm_factor(int n, size_t elem_bytes, size_t smem_limit) {
+  int n1 = 1;
+  for (int d = 2; d * d <= n; ++d)
+    if (n % d == 0) n1 = d;
+  const size_t need = 2 * (size_t)kCfTile * (n + 1) * elem_bytes + (size_t)n * elem_bytes;
+  return (n1 > 1 && need <= smem_limit) ? n1 : 1;
 }
 
 // Parameters of the diagonal scaling P_D^-1 (third pass).
@@ -48,16 +61,26 @@ struct CfScale {
 // preconditioner application, skipped when the solver state says none is due.
 // in_jstride > 0 (first pass of a GMRES step): the input is basis slot sc->j,
 // in + sc->j * in_jstride elements.
+//
+// With n = n1 n2 (n1 > 1) each line is transformed in two steps (Cooley-Tukey,
+// decimation in time: j = n2 j1 + j2, k = k1 + n1 k2):
+//   A[k1][j2] = sum_{j1} x[n2 j1 + j2] w^{n2 j1 k1}       (n1 terms)
+//   X[k]      = sum_{j2} A[k mod n1][j2] w^{j2 k}           (n2 terms)
+// (w = e^{-+2 pi i / n}; the second step's twiddle w^{j2 k} is the inner
+// transform's w^{n1 j2 k2} times the usual w^{j2 k1}), n1 + n2 products per
+// output instead of n.
 template <typename SI, typename SO, typename T, bool IN_REAL, bool OUT_REAL>
 __global__ void __launch_bounds__(kCfThreads) cfdm_pass(const void* __restrict__ in, void* __restrict__ out, int n,
-                                                        const Cplx<T>* __restrict__ tw, int inverse, int scale,
-                                                        CfScale sp, const GmScalars* sc, long long in_jstride) {
+                                                        int n1, const Cplx<T>* __restrict__ tw, int inverse,
+                                                        int scale, CfScale sp, const GmScalars* sc,
+                                                        long long in_jstride) {
   if (sc && (sc->done || sc->cycle_end || sc->j >= sc->m)) return;
   if (sc && in_jstride > 0) in = static_cast<const SI*>(in) + (long long)sc->j * in_jstride;
   extern __shared__ __align__(128) unsigned char smem[];
   using C = Cplx<T>;
   C* tile = reinterpret_cast<C*>(smem);                       // [kCfTile][n + 1]
-  C* tws = tile + (size_t)kCfTile * (n + 1);                  // [n]
+  C* tileA = n1 > 1 ? tile + (size_t)kCfTile * (n + 1) : tile;  // [kCfTile][n + 1], A[k1][j2] at k1 n2 + j2
+  C* tws = tile + (size_t)(n1 > 1 ? 2 : 1) * kCfTile * (n + 1);  // [n]
   const int nbt = (n + kCfTile - 1) / kCfTile;
   const int a = blockIdx.x / nbt;
   const int b0 = (blockIdx.x % nbt) * kCfTile;
@@ -81,59 +104,141 @@ __global__ void __launch_bounds__(kCfThreads) cfdm_pass(const void* __restrict__
     tile[(size_t)bb * (n + 1) + j] = v;
   }
   __syncthreads();
-  // outputs (k, bb): lanes of a warp take consecutive bb (coalesced stores);
-  // each thread forms kCfK outputs k0, k0 + 8, ... of its line at once, so one
-  // shared-memory read of the line element serves kCfK complex products
   const int bb = threadIdx.x % kCfTile;
-  if (bb >= tb) return;
-  const C* row = tile + (size_t)bb * (n + 1);
-  constexpr int kStep = kCfThreads / kCfTile;
-  for (int k0 = threadIdx.x / kCfTile; k0 < n; k0 += kStep * kCfK) {
-    T re[kCfK], im[kCfK];
-    int idx[kCfK], kk[kCfK];  // j k mod n, and k (0 for outputs past the end)
-#pragma unroll
-    for (int q = 0; q < kCfK; ++q) {
-      const int k = k0 + q * kStep;
-      kk[q] = k < n ? k : 0;
-      idx[q] = 0;
-      re[q] = im[q] = T(0);
+  const int warp = threadIdx.x / kCfTile;
+  constexpr int kWarps = kCfThreads / kCfTile;
+  // output k of line bb: P_D^-1 in the third pass, then the store; lanes of a
+  // warp take consecutive bb (coalesced stores)
+  auto emit = [&](int k, T r, T i) {
+    if (scale) {
+      // (kz, ky, kx) = (k, a, b); sin(2 pi m / n) = -Im e^{-2 pi i m / n}
+      const int kx = b0 + bb;
+      const T th = ((T)sp.beta[0] * (-tw[kx].im) + (T)sp.beta[1] * (-tw[a].im) + (T)sp.beta[2] * (-tw[k].im)) *
+                   (T)sp.inv_h;
+      const T c = (T)sp.s * th;
+      const T den = (T)sp.norm / fma(c, c, T(1));
+      const T r2 = fma(i, c, r) * den, i2 = fma(-r, c, i) * den;
+      r = r2;
+      i = i2;
     }
-    for (int j = 0; j < n; ++j) {
-      const C x = row[j];
+    const long long go = ((long long)k * n + a) * n + b0 + bb;
+    if constexpr (OUT_REAL) {
+      static_cast<SO*>(out)[go] = nar<SO>(r);
+    } else {
+      C v;
+      v.re = r;
+      v.im = i;
+      static_cast<C*>(out)[go] = v;
+    }
+  };
+  const C* row = tile + (size_t)bb * (n + 1);
+  if (n1 <= 1) {
+    // direct n-term sums; each thread forms kCfK outputs k0, k0 + 8, ... of its
+    // line at once, so one read of the line element serves kCfK products
+    if (bb >= tb) return;
+    for (int k0 = warp; k0 < n; k0 += kWarps * kCfK) {
+      T re[kCfK], im[kCfK];
+      int idx[kCfK], kk[kCfK];  // j k mod n, and k (0 for outputs past the end)
 #pragma unroll
       for (int q = 0; q < kCfK; ++q) {
-        const C w = tws[idx[q]];
-        re[q] = fma(x.re, w.re, fma(-x.im, w.im, re[q]));
-        im[q] = fma(x.re, w.im, fma(x.im, w.re, im[q]));
-        idx[q] += kk[q];
-        if (idx[q] >= n) idx[q] -= n;
+        const int k = k0 + q * kWarps;
+        kk[q] = k < n ? k : 0;
+        idx[q] = 0;
+        re[q] = im[q] = T(0);
+      }
+      for (int j = 0; j < n; ++j) {
+        const C x = row[j];
+#pragma unroll
+        for (int q = 0; q < kCfK; ++q) {
+          const C w = tws[idx[q]];
+          re[q] = fma(x.re, w.re, fma(-x.im, w.im, re[q]));
+          im[q] = fma(x.re, w.im, fma(x.im, w.re, im[q]));
+          idx[q] += kk[q];
+          if (idx[q] >= n) idx[q] -= n;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < kCfK; ++q) {
+        const int k = k0 + q * kWarps;
+        if (k < n) emit(k, re[q], im[q]);
       }
     }
+    return;
+  }
+  const int n2 = n / n1;
+  // step 1: tasks (j2, group of kCfK consecutive k1), one per warp at a time
+  {
+    const int kg = (n1 + kCfK - 1) / kCfK;
+    C* rowA = tileA + (size_t)bb * (n + 1);
+    for (int task = warp; task < n2 * kg; task += kWarps) {
+      const int j2 = task / kg;
+      const int k1b = (task - j2 * kg) * kCfK;
+      T re[kCfK], im[kCfK];
+      int idx[kCfK], inc[kCfK];  // n2 j1 k1 mod n and its step n2 k1 mod n
 #pragma unroll
-    for (int q = 0; q < kCfK; ++q) {
-      const int k = k0 + q * kStep;
-      if (k >= n) break;
-      T r = re[q], i = im[q];
-      if (scale) {
-        // (kz, ky, kx) = (k, a, b); sin(2 pi m / n) = -Im e^{-2 pi i m / n}
-        const int kx = b0 + bb;
-        const T th = ((T)sp.beta[0] * (-tw[kx].im) + (T)sp.beta[1] * (-tw[a].im) + (T)sp.beta[2] * (-tw[k].im)) *
-                     (T)sp.inv_h;
-        const T c = (T)sp.s * th;
-        const T den = (T)sp.norm / fma(c, c, T(1));
-        const T r2 = fma(i, c, r) * den, i2 = fma(-r, c, i) * den;
-        r = r2;
-        i = i2;
+      for (int q = 0; q < kCfK; ++q) {
+        const int k1 = k1b + q < n1 ? k1b + q : 0;
+        inc[q] = n2 * k1;  // < n
+        idx[q] = 0;
+        re[q] = im[q] = T(0);
       }
-      const long long go = ((long long)k * n + a) * n + b0 + bb;
-      if constexpr (OUT_REAL) {
-        static_cast<SO*>(out)[go] = nar<SO>(r);
-      } else {
-        C v;
-        v.re = r;
-        v.im = i;
-        static_cast<C*>(out)[go] = v;
+      if (bb < tb) {
+        for (int j1 = 0; j1 < n1; ++j1) {
+          const C x = row[n2 * j1 + j2];
+#pragma unroll
+          for (int q = 0; q < kCfK; ++q) {
+            const C w = tws[idx[q]];
+            re[q] = fma(x.re, w.re, fma(-x.im, w.im, re[q]));
+            im[q] = fma(x.re, w.im, fma(x.im, w.re, im[q]));
+            idx[q] += inc[q];
+            if (idx[q] >= n) idx[q] -= n;
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < kCfK; ++q)
+          if (k1b + q < n1) {
+            C v;
+            v.re = re[q];
+            v.im = im[q];
+            rowA[(k1b + q) * n2 + j2] = v;
+          }
       }
+    }
+  }
+  __syncthreads();
+  if (bb >= tb) return;
+  // step 2: tasks (k1, group of kCfK consecutive k2): outputs k = k1 + n1 k2
+  // share the reads of A[k1][.]
+  {
+    const int kg = (n2 + kCfK - 1) / kCfK;
+    const C* rowA = tileA + (size_t)bb * (n + 1);
+    for (int task = warp; task < n1 * kg; task += kWarps) {
+      const int k1 = task / kg;
+      const int k2b = (task - k1 * kg) * kCfK;
+      T re[kCfK], im[kCfK];
+      int idx[kCfK], kk[kCfK];  // j2 k mod n, and k (0 for outputs past the end)
+#pragma unroll
+      for (int q = 0; q < kCfK; ++q) {
+        const int k = k1 + n1 * (k2b + q);
+        kk[q] = k2b + q < n2 ? k : 0;
+        idx[q] = 0;
+        re[q] = im[q] = T(0);
+      }
+      const C* a1 = rowA + k1 * n2;
+      for (int j2 = 0; j2 < n2; ++j2) {
+        const C x = a1[j2];
+#pragma unroll
+        for (int q = 0; q < kCfK; ++q) {
+          const C w = tws[idx[q]];
+          re[q] = fma(x.re, w.re, fma(-x.im, w.im, re[q]));
+          im[q] = fma(x.re, w.im, fma(x.im, w.re, im[q]));
+          idx[q] += kk[q];
+          if (idx[q] >= n) idx[q] -= n;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < kCfK; ++q)
+        if (k2b + q < n2) emit(k1 + n1 * (k2b + q), re[q], im[q]);
     }
   }
 }

@@ -341,8 +341,20 @@ static rk_status cfdm_apply(rk_problem* p, double shift, const SI* in, long long
   const int n = p->n;
   const int nbt = (n + kCfTile - 1) / kCfTile;
   const int grid = n * nbt;
-  const size_t smem = cfdm_smem<T>(n);
   using C = Cplx<T>;
+  static int smem_optin = 0;
+  if (smem_optin == 0) {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || v <= 0) {
+      cudaGetLastError();
+      set_error("periodic fast diagonalization: shared-memory limit query failed");
+      return RK_ERR_CUDA;
+    }
+    smem_optin = v;
+  }
+  const int n1 = cfdm_factor(n, sizeof(C), (size_t)smem_optin);
+  const size_t smem = cfdm_smem<T>(n, n1);
   const C* tw = static_cast<const C*>(w->cf_tw);
   CfScale sp{};
   sp.s = shift;
@@ -357,7 +369,7 @@ static rk_status cfdm_apply(rk_problem* p, double shift, const SI* in, long long
   static bool attr_done[3] = {false, false, false};
   const int slot = sizeof(T) == 8 ? 2 : (sizeof(SI) == 2 ? 1 : 0);
   if (!attr_done[slot]) {
-    const int lim = (int)cfdm_smem<T>(400);
+    const int lim = smem_optin;
     if (cudaFuncSetAttribute((const void*)k_first, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) != cudaSuccess ||
         cudaFuncSetAttribute((const void*)k_mid, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) != cudaSuccess ||
         cudaFuncSetAttribute((const void*)k_last, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) != cudaSuccess) {
@@ -371,22 +383,22 @@ static rk_status cfdm_apply(rk_problem* p, double shift, const SI* in, long long
   void* c0 = w->cf_c[0];
   void* c1 = w->cf_c[1];
   prof_begin(p, K_CFDM, (double)p->N * sizeof(SI) + Nc, solve, idx);
-  k_first<<<grid, kCfThreads, smem, p->st>>>(in, c0, n, tw, 0, 0, sp, sc, in_jstride);
+  k_first<<<grid, kCfThreads, smem, p->st>>>(in, c0, n, n1, tw, 0, 0, sp, sc, in_jstride);
   prof_end(p);
   prof_begin(p, K_CFDM, 2.0 * Nc, solve, idx);
-  k_mid<<<grid, kCfThreads, smem, p->st>>>(c0, c1, n, tw, 0, 0, sp, sc, 0);
+  k_mid<<<grid, kCfThreads, smem, p->st>>>(c0, c1, n, n1, tw, 0, 0, sp, sc, 0);
   prof_end(p);
   prof_begin(p, K_CFDM, 2.0 * Nc, solve, idx);
-  k_mid<<<grid, kCfThreads, smem, p->st>>>(c1, c0, n, tw, 0, 1, sp, sc, 0);
+  k_mid<<<grid, kCfThreads, smem, p->st>>>(c1, c0, n, n1, tw, 0, 1, sp, sc, 0);
   prof_end(p);
   prof_begin(p, K_CFDM, 2.0 * Nc, solve, idx);
-  k_mid<<<grid, kCfThreads, smem, p->st>>>(c0, c1, n, tw, 1, 0, sp, sc, 0);
+  k_mid<<<grid, kCfThreads, smem, p->st>>>(c0, c1, n, n1, tw, 1, 0, sp, sc, 0);
   prof_end(p);
   prof_begin(p, K_CFDM, 2.0 * Nc, solve, idx);
-  k_mid<<<grid, kCfThreads, smem, p->st>>>(c1, c0, n, tw, 1, 0, sp, sc, 0);
+  k_mid<<<grid, kCfThreads, smem, p->st>>>(c1, c0, n, n1, tw, 1, 0, sp, sc, 0);
   prof_end(p);
   prof_begin(p, K_CFDM, Nc + (double)p->N * sizeof(S), solve, idx);
-  k_last<<<grid, kCfThreads, smem, p->st>>>(c0, out, n, tw, 1, 0, sp, sc, 0);
+  k_last<<<grid, kCfThreads, smem, p->st>>>(c0, out, n, n1, tw, 1, 0, sp, sc, 0);
   prof_end(p);
   if (cudaGetLastError() != cudaSuccess) {
     set_error("periodic fast-diagonalization launch failed");

@@ -1,6 +1,7 @@
 // Batched stepping (rk_integrate_batch) and the serving loop (rk_server_*).
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -107,7 +108,14 @@ extern "C" rk_status rk_integrate_batch(rk_problem** ps, int count, double dt, i
     const auto key = std::make_tuple(kv.first.storage, kv.first.bs, (int)std::log2((double)items + 1.0));
     const long long launches_before = tot.launches;
     int cap = -1;
-    {
+    if (const char* env = std::getenv("RK_BATCH_GRID_CAP")) {
+      // a fixed launch shape (CTAs per SM of the work-list kernels, 0 = the
+      // occupancy limit) instead of the autotuned one
+      char* end = nullptr;
+      const long v = std::strtol(env, &end, 10);
+      if (end != env && v >= 0 && v <= 64) cap = (int)v;
+    }
+    if (cap < 0) {
       std::lock_guard<std::mutex> lk(g_tune_mu);
       auto it = g_tune.find(key);
       if (it != g_tune.end()) cap = it->second;

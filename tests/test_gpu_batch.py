@@ -51,7 +51,9 @@ def test_batch_matches_solo_and_oracle(rk):
 
 
 def test_batch_composition_invariance(rk):
-    """A problem stepped alone in a batch and inside a larger batch agree."""
+    """A problem stepped alone in a batch and inside a larger batch agree bit
+    for bit: its reductions add its own items' partials in item order, so
+    neither the other problems nor the launch shape enter its arithmetic."""
     dt, steps = 1e-3, 2
     n, kap = 24, 1.0
     u0 = synth.heat_modes(seed=9, n_random=4).evaluate(n)
@@ -63,7 +65,7 @@ def test_batch_composition_invariance(rk):
     target = make(rk, n, kap, "f32", "sdirk2", u0)
     rk.rk_integrate_batch([o.h for o in others] + [target.h], dt, steps)
     mixed = target.state()
-    assert rel_l2(mixed, alone) < 1e-6
+    assert np.array_equal(mixed, alone), rel_l2(mixed, alone)
     for o in others + [target]:
         o.close()
 
