@@ -863,10 +863,11 @@ rk_status rk_create_problem(const rk_problem_desc* desc, const rk_solver_desc* s
   A((void**)&p->u, N * 8);
   A((void**)&p->r, N * 8);
   A((void**)&p->g64, N * 8);
-  A(&p->wr, N * s);
-  A(&p->wz, N * s);
-  A(&p->wp[0], N * s);
-  A(&p->wp[1], N * s);
+  const size_t NK = krylov_elems(desc->op, desc->n);  // padded lines for the batched path (heat)
+  A(&p->wr, NK * s);
+  A(&p->wz, NK * s);
+  A(&p->wp[0], NK * s);
+  A(&p->wp[1], NK * s);
   A((void**)&p->partials, (size_t)device_sms() * 32 * 4 * 8);
   A((void**)&p->sc, sizeof(CgScalars));
   A((void**)&p->rs, 10 * sizeof(RhsScalars));
@@ -987,7 +988,7 @@ rk_status rk_set_tableau(rk_problem* p, int q, const double* A_hi, const double*
         p->ke[i] = p->k[i];
         p->ke_alias[i] = true;
       } else {
-        RK_TRY(alloc_dev(p, &p->ke[i], N * (p->ke_hi ? 8 : xsize(p->sol.storage))));
+        RK_TRY(alloc_dev(p, &p->ke[i], krylov_elems(p->desc.op, p->n) * (p->ke_hi ? 8 : xsize(p->sol.storage))));
       }
     }
   }

@@ -37,9 +37,13 @@ struct BatchProb {
   void* wp[2];
   CgScalars* sc;           // the problem's CG scalars
   RhsScalars* rs;          // the problem's per-stage right-hand-side scalars [0..7]
-  double* part;            // per-item partials, nitems x 2
+  double* part;            // per-item partials, ntiles x 2
   unsigned* ticket;        // per-problem reduction ticket
-  int nitems;              // items (tiles) of this problem
+  int nitems;              // items (kBatchTilesPerItem tiles) of this problem
+  int ntiles;              // its tiles: the single-tile items of the CG tail
+  int fine;                // 1: the current CG work list holds its single-tile items
+  int ld;                  // line pitch of the Krylov vectors and k^eps (elements; >= n)
+  int plane;               // n * ld (n <= 1024, so padded indices fit in int)
   int max_iter;            // CG settings of the problem
   double tol_rel, tol_abs;
   T d[kBatchStages], o[kBatchStages];   // stage matrix I - shift L = d I + o (neighbour sum)
@@ -71,30 +75,6 @@ struct BatchStage {
   int correct;            // 1: FP64 correction k = L y; 0: k = widened solve output
   int use_r;              // 1: r was formed (history terms present), else r = u
 };
-
-// Reduction of NV values of type A across the CTA (fixed order); result in
-// thread 0.
-template <typename A, int NV>
-__device__ __forceinline__ void cta_sum(A (&v)[NV], A* sred /* >= 32 * NV */) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-#pragma unroll
-  for (int c = 0; c < NV; ++c)
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v[c] += __shfl_down_sync(0xffffffffu, v[c], off);
-  if (lane == 0)
-#pragma unroll
-    for (int c = 0; c < NV; ++c) sred[warp * NV + c] = v[c];
-  __syncthreads();
-  if (warp == 0) {
-#pragma unroll
-    for (int c = 0; c < NV; ++c) {
-      v[c] = (lane < nw) ? sred[lane * NV + c] : A(0);
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) v[c] += __shfl_down_sync(0xffffffffu, v[c], off);
-    }
-  }
-  __syncthreads();
-}
 
 // Per-problem reduction of NV sums (NV <= 2): the item's CTA sum (in the
 // arithmetic type A, FP32 for FP32 work: FP64 operations are scarce on this
@@ -189,7 +169,45 @@ __device__ __forceinline__ bool prob_reduce(A (&v)[NV], double* part, unsigned* 
     const int m = live_ ? min((SEG), g.n - i0) : 0;                                \
     const int j = (int)(line % g.n);                                               \
     const int k = (int)(line / g.n);                                               \
-    const long long base = line * g.n + i0;
+    const long long base = line * g.n + i0;                                       \
+    const int pbase = k * (P).plane + j * (P).ld + i0;
+
+// Sum of the six neighbours of a segment in the padded layout of the Krylov
+// vectors and k^eps (line pitch ld, plane pitch `plane`): nb_sum with pitched
+// offsets.  own[] holds the field on the segment (zeros past m).
+template <typename T, int SEG, typename SegF, typename PtF>
+__device__ __forceinline__ void bt_nb_sum(int n, int ld, int plane, int i0, int m, int j, int k, int pb,
+                                          const T (&own)[SEG], SegF seg, PtF pt, T (&nb)[SEG]) {
+  const T left = (i0 > 0) ? pt(pb - 1) : T(0);
+  const T right = (i0 + SEG < n) ? pt(pb + SEG) : T(0);
+#pragma unroll
+  for (int e = 0; e < SEG; ++e) {
+    const T l = (e > 0) ? own[e - 1] : left;
+    const T r = (e + 1 < SEG) ? own[e + 1] : right;
+    nb[e] = l + r;
+  }
+  T tmp[SEG];
+  if (j > 0) {
+    seg(pb - ld, m, tmp);
+#pragma unroll
+    for (int e = 0; e < SEG; ++e) nb[e] += tmp[e];
+  }
+  if (j < n - 1) {
+    seg(pb + ld, m, tmp);
+#pragma unroll
+    for (int e = 0; e < SEG; ++e) nb[e] += tmp[e];
+  }
+  if (k > 0) {
+    seg(pb - plane, m, tmp);
+#pragma unroll
+    for (int e = 0; e < SEG; ++e) nb[e] += tmp[e];
+  }
+  if (k < n - 1) {
+    seg(pb + plane, m, tmp);
+#pragma unroll
+    for (int e = 0; e < SEG; ++e) nb[e] += tmp[e];
+  }
+}
 
 // ------------------------------------------------------------ FP64 phases
 // Stage right-hand side r = u + sum ch k_j + sum ce k^eps_j / sigma_j (Eqs.
@@ -200,8 +218,6 @@ __global__ void __launch_bounds__(kThreads) bt_combine(BatchProb<T, BS>* P, cons
   RK_BATCH_ITEMS(items, nitems)
     const BatchProb<T, BS>& pb = P[item_.prob];
     RK_BATCH_CHUNKS(pb, SEG)
-    (void)j;
-    (void)k;
     if (!live_) continue;
     double v[SEG], t[SEG];
     load_seg<double, double, SEG>(pb.u + base, m, v);
@@ -212,7 +228,7 @@ __global__ void __launch_bounds__(kThreads) bt_combine(BatchProb<T, BS>* P, cons
     }
     for (int h = 0; h < st.ne; ++h) {
       const double c = st.ce[h] / pb.rs[st.ej[h]].sigma;
-      load_seg<double, X, SEG>(static_cast<const X*>(pb.ke[st.ej[h]]) + base, m, t);
+      load_seg<double, X, SEG>(static_cast<const X*>(pb.ke[st.ej[h]]) + pbase, m, t);
 #pragma unroll
       for (int e = 0; e < SEG; ++e) v[e] = fma(c, t[e], v[e]);
     }
@@ -234,6 +250,7 @@ __global__ void __launch_bounds__(kThreads) bt_apply(BatchProb<T, BS>* P, const 
     double* y = implicit ? pb.g64 : pb.k[st.stage];
     double acc[2] = {0.0, 0.0};
     RK_BATCH_CHUNKS(pb, SEG)
+    (void)pbase;
     if (live_) {
       double xv[SEG], nb[SEG], yv[SEG];
       load_seg<double, double, SEG>(x + base, m, xv);
@@ -294,7 +311,7 @@ __global__ void __launch_bounds__(kThreads) bt_correct(BatchProb<T, BS>* P, cons
     RK_BATCH_CHUNKS(pb, SEG)
     if (live_ && !st.correct) {
       double v[SEG];
-      load_seg<double, X, SEG>(ke + base, m, v);
+      load_seg<double, X, SEG>(ke + pbase, m, v);
 #pragma unroll
       for (int e = 0; e < SEG; ++e) v[e] *= inv_sigma;
       store_seg<double, double, SEG>(kout + base, m, v);
@@ -304,9 +321,9 @@ __global__ void __launch_bounds__(kThreads) bt_correct(BatchProb<T, BS>* P, cons
       load_seg<double, double, SEG>(pb.g64 + base, m, gs);
       if constexpr (sizeof(X) == 4) {
         float v[SEG], ym[SEG], yp[SEG], zm[SEG], zp[SEG];
-        load_seg<float, X, SEG>(ke + base, m, v);
-        const float left = (i0 > 0) ? wid<float>(ke[base - 1]) : 0.f;
-        const float right = (i0 + SEG < g.n) ? wid<float>(ke[base + SEG]) : 0.f;
+        load_seg<float, X, SEG>(ke + pbase, m, v);
+        const float left = (i0 > 0) ? wid<float>(ke[pbase - 1]) : 0.f;
+        const float right = (i0 + SEG < g.n) ? wid<float>(ke[pbase + SEG]) : 0.f;
         auto seg_or_zero = [&](bool in, long long off, float (&w)[SEG]) {
           if (in) {
             load_seg<float, X, SEG>(ke + off, m, w);
@@ -315,10 +332,10 @@ __global__ void __launch_bounds__(kThreads) bt_correct(BatchProb<T, BS>* P, cons
             for (int e = 0; e < SEG; ++e) w[e] = 0.f;
           }
         };
-        seg_or_zero(j > 0, base - g.n, ym);
-        seg_or_zero(j < g.n - 1, base + g.n, yp);
-        seg_or_zero(k > 0, base - g.n2, zm);
-        seg_or_zero(k < g.n - 1, base + g.n2, zp);
+        seg_or_zero(j > 0, pbase - pb.ld, ym);
+        seg_or_zero(j < g.n - 1, pbase + pb.ld, yp);
+        seg_or_zero(k > 0, pbase - pb.plane, zm);
+        seg_or_zero(k < g.n - 1, pbase + pb.plane, zp);
 #pragma unroll
         for (int e = 0; e < SEG; ++e) {
           const float xl = (e > 0) ? v[e - 1] : left;
@@ -329,9 +346,9 @@ __global__ void __launch_bounds__(kThreads) bt_correct(BatchProb<T, BS>* P, cons
         }
       } else {
         double v[SEG], nb[SEG];
-        load_seg<double, X, SEG>(ke + base, m, v);
-        nb_sum<double, SEG>(
-            g, i0, m, j, k, base, v,
+        load_seg<double, X, SEG>(ke + pbase, m, v);
+        bt_nb_sum<double, SEG>(
+            g.n, pb.ld, pb.plane, i0, m, j, k, pbase, v,
             [&](long long off, int mm, double (&w)[SEG]) { load_seg<double, X, SEG>(ke + off, mm, w); },
             [&](long long idx) { return wid<double>(ke[idx]); }, nb);
 #pragma unroll
@@ -367,8 +384,7 @@ __global__ void __launch_bounds__(kThreads) bt_update(BatchProb<T, BS>* P, const
   RK_BATCH_ITEMS(items, nitems)
     const BatchProb<T, BS>& pb = P[item_.prob];
     RK_BATCH_CHUNKS(pb, SEG)
-    (void)j;
-    (void)k;
+    (void)pbase;
     if (!live_) continue;
     double v[SEG], t[SEG];
     load_seg<double, double, SEG>(pb.u + base, m, v);
@@ -414,15 +430,21 @@ template <typename S, typename T, int BS, int SEG>
 __global__ void __launch_bounds__(kThreads) bt_cg_init(BatchProb<T, BS>* P, const BatchItem* items, int nitems,
                                                        BatchStage st, int* active) {
   using X = typename XOf<S>::type;
+  __shared__ BjTri<T, BS> stri;
   RK_BATCH_ITEMS(items, nitems)
     BatchProb<T, BS>& pb = P[item_.prob];
     const double sigma = pb.rs[st.stage].sigma;
     T acc[2] = {T(0), T(0)};
+    // the stage's factored block in shared memory (the previous item's last
+    // barrier has passed, so no thread still reads it)
+    {
+      const T* src = reinterpret_cast<const T*>(&pb.tri[st.stage]);
+      T* dst = reinterpret_cast<T*>(&stri);
+      for (int c = threadIdx.x; c < (int)(sizeof(BjTri<T, BS>) / sizeof(T)); c += blockDim.x) dst[c] = src[c];
+    }
+    __syncthreads();
     RK_BATCH_CHUNKS(pb, SEG)
-    (void)j;
-    (void)k;
     if (live_) {
-      const BjTri<T, BS> tri = pb.tri[st.stage];
       double gd[SEG];
       load_seg<double, double, SEG>(pb.g64 + base, m, gd);
       T rv[SEG], zv[SEG], zero[SEG];
@@ -431,16 +453,16 @@ __global__ void __launch_bounds__(kThreads) bt_cg_init(BatchProb<T, BS>* P, cons
         rv[e] = (e < m) ? rnd<S, T>(sigma == 1.0 ? (T)gd[e] : (T)(gd[e] * sigma)) : T(0);
         zero[e] = T(0);
       }
-      bj_apply_tri_m<T, BS, SEG>(tri, rv, zv, m);
+      bj_apply_tri_m<T, BS, SEG>(stri, rv, zv, m);
 #pragma unroll
       for (int e = 0; e < SEG; ++e) {
         zv[e] = rnd<S, T>(zv[e]);
         acc[0] = fma(rv[e], zv[e], acc[0]);
         acc[1] = fma(rv[e], rv[e], acc[1]);
       }
-      store_seg<S, T, SEG>(static_cast<S*>(pb.wr) + base, m, rv);
-      store_seg<S, T, SEG>(static_cast<S*>(pb.wz) + base, m, zv);
-      store_seg<X, T, SEG>(static_cast<X*>(pb.ke[st.stage]) + base, m, zero);
+      store_seg<S, T, SEG>(static_cast<S*>(pb.wr) + pbase, m, rv);
+      store_seg<S, T, SEG>(static_cast<S*>(pb.wz) + pbase, m, zv);
+      store_seg<X, T, SEG>(static_cast<X*>(pb.ke[st.stage]) + pbase, m, zero);
     }
     RK_BATCH_CHUNKS_END
     double tot[2];
@@ -449,6 +471,7 @@ __global__ void __launch_bounds__(kThreads) bt_cg_init(BatchProb<T, BS>* P, cons
       sc->tol_rel = pb.tol_rel;
       sc->tol_abs = pb.tol_abs;
       sc->max_iter = pb.max_iter;
+      pb.fine = 0;
       sc->rz = tot[0];
       sc->rr = tot[1];
       sc->gg = tot[1];
@@ -491,6 +514,7 @@ __global__ void __launch_bounds__(kThreads, 4) bt_cg_a(BatchProb<T, BS>* P, cons
     S* pnew = static_cast<S*>(pb.wp[iter & 1]);
     T acc[1] = {T(0)};
     RK_BATCH_CHUNKS(pb, SEG)
+    (void)base;
     if (live_) {
       auto pseg = [&](long long off, int mm, T (&v)[SEG]) {
         load_seg<T, S, SEG>(z + off, mm, v);
@@ -507,18 +531,18 @@ __global__ void __launch_bounds__(kThreads, 4) bt_cg_a(BatchProb<T, BS>* P, cons
         return v;
       };
       T pv[SEG], nb[SEG];
-      pseg(base, m, pv);
-      nb_sum<T, SEG>(g, i0, m, j, k, base, pv, pseg, ppt, nb);
+      pseg(pbase, m, pv);
+      bt_nb_sum<T, SEG>(g.n, pb.ld, pb.plane, i0, m, j, k, pbase, pv, pseg, ppt, nb);
 #pragma unroll
       for (int e = 0; e < SEG; ++e) {
         const T w = fma(d, pv[e], o * nb[e]);
         if (e < m) acc[0] = fma(pv[e], w, acc[0]);
       }
-      store_seg<S, T, SEG>(pnew + base, m, pv);
+      store_seg<S, T, SEG>(pnew + pbase, m, pv);
     }
     RK_BATCH_CHUNKS_END
     double tot[1];
-    if (prob_reduce<T, 1>(acc, pb.part, pb.ticket, item_.idx, pb.nitems, tot)) {
+    if (prob_reduce<T, 1>(acc, pb.part, pb.ticket, item_.idx, pb.fine ? pb.ntiles : pb.nitems, tot)) {
       sc->pAp = tot[0];
       const double alpha = sc->rz / tot[0];
       sc->alpha = alpha;
@@ -540,6 +564,7 @@ template <typename S, typename T, int BS, int SEG>
 __global__ void __launch_bounds__(kThreads, 4) bt_cg_b(BatchProb<T, BS>* P, const BatchItem* items, const int* nitems_dev,
                                                        BatchStage st, int* active) {
   using X = typename XOf<S>::type;
+  __shared__ BjTri<T, BS> stri;
   const int nitems = *nitems_dev;
   RK_BATCH_ITEMS(items, nitems)
     BatchProb<T, BS>& pb = P[item_.prob];
@@ -554,17 +579,26 @@ __global__ void __launch_bounds__(kThreads, 4) bt_cg_b(BatchProb<T, BS>* P, cons
     S* z = static_cast<S*>(pb.wz);
     X* x = static_cast<X*>(pb.ke[st.stage]);
     T acc[2] = {T(0), T(0)};
+    // the stage's factored block in shared memory (the previous item's last
+    // barrier has passed, so no thread still reads it)
+    {
+      const T* src = reinterpret_cast<const T*>(&pb.tri[st.stage]);
+      T* dst = reinterpret_cast<T*>(&stri);
+      for (int c = threadIdx.x; c < (int)(sizeof(BjTri<T, BS>) / sizeof(T)); c += blockDim.x) dst[c] = src[c];
+    }
+    __syncthreads();
     RK_BATCH_CHUNKS(pb, SEG)
+    (void)base;
     if (live_) {
-      const BjTri<T, BS> tri = pb.tri[st.stage];
       T pv[SEG], nb[SEG], rv[SEG], xv[SEG], zv[SEG];
-      load_seg<T, S, SEG>(p + base, m, pv);
-      nb_sum<T, SEG>(
-          g, i0, m, j, k, base, pv, [&](long long off, int mm, T (&v)[SEG]) { load_seg<T, S, SEG>(p + off, mm, v); },
+      load_seg<T, S, SEG>(p + pbase, m, pv);
+      bt_nb_sum<T, SEG>(
+          g.n, pb.ld, pb.plane, i0, m, j, k, pbase, pv,
+          [&](long long off, int mm, T (&v)[SEG]) { load_seg<T, S, SEG>(p + off, mm, v); },
           [&](long long idx) { return wid<T>(p[idx]); }, nb);
-      load_seg<T, S, SEG>(r + base, m, rv);
+      load_seg<T, S, SEG>(r + pbase, m, rv);
       if (!xzero) {
-        load_seg<T, X, SEG>(x + base, m, xv);
+        load_seg<T, X, SEG>(x + pbase, m, xv);
       } else {
 #pragma unroll
         for (int e = 0; e < SEG; ++e) xv[e] = T(0);
@@ -575,7 +609,7 @@ __global__ void __launch_bounds__(kThreads, 4) bt_cg_b(BatchProb<T, BS>* P, cons
         rv[e] = (e < m) ? rnd<S, T>(fma(-alpha, w, rv[e])) : T(0);
         xv[e] = fma(alpha, pv[e], xv[e]);
       }
-      bj_apply_tri_m<T, BS, SEG>(tri, rv, zv, m);
+      bj_apply_tri_m<T, BS, SEG>(stri, rv, zv, m);
 #pragma unroll
       for (int e = 0; e < SEG; ++e) {
         zv[e] = rnd<S, T>(zv[e]);
@@ -584,13 +618,13 @@ __global__ void __launch_bounds__(kThreads, 4) bt_cg_b(BatchProb<T, BS>* P, cons
           acc[1] = fma(rv[e], rv[e], acc[1]);
         }
       }
-      store_seg<X, T, SEG>(x + base, m, xv);
-      store_seg<S, T, SEG>(r + base, m, rv);
-      store_seg<S, T, SEG>(z + base, m, zv);
+      store_seg<X, T, SEG>(x + pbase, m, xv);
+      store_seg<S, T, SEG>(r + pbase, m, rv);
+      store_seg<S, T, SEG>(z + pbase, m, zv);
     }
     RK_BATCH_CHUNKS_END
     double tot[2];
-    if (prob_reduce<T, 2>(acc, pb.part, pb.ticket, item_.idx, pb.nitems, tot)) {
+    if (prob_reduce<T, 2>(acc, pb.part, pb.ticket, item_.idx, pb.fine ? pb.ntiles : pb.nitems, tot)) {
       const double rz_new = tot[0];
       sc->beta = rz_new / sc->rz;
       sc->rz = rz_new;
@@ -612,14 +646,28 @@ __global__ void __launch_bounds__(kThreads, 4) bt_cg_b(BatchProb<T, BS>* P, cons
 
 // Work list of the problems still iterating: the items of unfinished problems
 // of `in` are appended to `out` (order arbitrary: every problem's reduction
-// adds its partials by tile index, so results do not depend on it).
+// adds its partials by item index, so results do not depend on it).  When
+// `in` has at most expand_below items, the multi-tile items are split into
+// single-tile items (slot = tile index) and their problems switch to the
+// per-tile reduction count: the few problems of a solve's tail then spread
+// over more CTAs.  All items of a problem are in `in`, so a problem switches
+// whole.
 template <typename T, int BS>
-__global__ void __launch_bounds__(kThreads) bt_compact(const BatchProb<T, BS>* P, const BatchItem* in,
-                                                       const int* in_count, BatchItem* out, int* out_count) {
+__global__ void __launch_bounds__(kThreads) bt_compact(BatchProb<T, BS>* P, const BatchItem* in, const int* in_count,
+                                                       BatchItem* out, int* out_count, int expand_below) {
   const int n = *in_count;
+  const bool expand = n <= expand_below;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const BatchItem it = in[i];
-    if (!P[it.prob].sc->done) out[atomicAdd(out_count, 1)] = it;
+    BatchProb<T, BS>& pb = P[it.prob];
+    if (pb.sc->done) continue;
+    if (expand) {  // also items of one tile: their slot becomes the tile index
+      const int slot = atomicAdd(out_count, it.nch);
+      for (int t = 0; t < it.nch; ++t) out[slot + t] = BatchItem{it.prob, it.chunk + t, 1, it.chunk + t};
+      pb.fine = 1;
+    } else {
+      out[atomicAdd(out_count, 1)] = it;
+    }
   }
 }
 
@@ -669,7 +717,7 @@ static rk_status batch_group_bs(rk_problem** ps, int count, double dt, int nstep
   // host descriptors and the work list
   std::vector<Prob> hp(count);
   std::vector<BatchItem> items;
-  long long part_total = 0;
+  long long part_total = 0, ntiles_total = 0;
   for (int i = 0; i < count; ++i) {
     const rk_problem* p = ps[i];
     Prob& b = hp[i];
@@ -689,13 +737,20 @@ static rk_status batch_group_bs(rk_problem** ps, int count, double dt, int nstep
     b.wp[1] = p->wp[1];
     b.sc = p->sc;
     b.rs = p->rs;
+    // FP64 storage without correction keeps k^eps in k (unpadded); otherwise
+    // the Krylov vectors and k^eps use lines padded to batch_pitch(n)
+    b.ld = (!mixed && std::is_same<S, double>::value) ? p->n : batch_pitch(p->n);
+    b.plane = p->n * b.ld;
     const long long nsegs = b.g.n2 * b.g.nseg;
     const int ntiles = (int)((nsegs + kThreads - 1) / kThreads);
     b.nitems = (ntiles + kBatchTilesPerItem - 1) / kBatchTilesPerItem;
+    b.ntiles = ntiles;
+    b.fine = 0;
+    ntiles_total += ntiles;
     for (int c = 0; c < b.nitems; ++c)
       items.push_back(BatchItem{i, c * kBatchTilesPerItem, std::min(kBatchTilesPerItem, ntiles - c * kBatchTilesPerItem), c});
     b.part = reinterpret_cast<double*>(part_total);  // offset of the problem's partials (fixed up below)
-    part_total += 2LL * b.nitems;
+    part_total += 2LL * ntiles;
     b.max_iter = p->sol.max_iter;
     b.tol_rel = p->sol.tol_rel;
     b.tol_abs = p->sol.tol_abs;
@@ -734,8 +789,8 @@ static rk_status batch_group_bs(rk_problem** ps, int count, double dt, int nstep
       cudaMallocAsync((void**)&dpart, sizeof(double) * part_total, st) != cudaSuccess ||
       cudaMallocAsync((void**)&dtick, sizeof(unsigned) * count, st) != cudaSuccess ||
       cudaMallocAsync((void**)&dactive, sizeof(int), st) != cudaSuccess ||
-      cudaMallocAsync((void**)&dlist[0], sizeof(BatchItem) * items.size(), st) != cudaSuccess ||
-      cudaMallocAsync((void**)&dlist[1], sizeof(BatchItem) * items.size(), st) != cudaSuccess ||
+      cudaMallocAsync((void**)&dlist[0], sizeof(BatchItem) * ntiles_total, st) != cudaSuccess ||
+      cudaMallocAsync((void**)&dlist[1], sizeof(BatchItem) * ntiles_total, st) != cudaSuccess ||
       cudaMallocAsync((void**)&dcount, sizeof(int) * 3, st) != cudaSuccess ||
       cudaMallocHost((void**)&hactive, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
@@ -756,11 +811,11 @@ static rk_status batch_group_bs(rk_problem** ps, int count, double dt, int nstep
     cudaMemcpyAsync(dcount, counts, sizeof(counts), cudaMemcpyHostToDevice, st);
     cudaStreamSynchronize(st);  // counts lives on this stack frame
   }
-  auto grid_of = [&](const void* kern) {
+  auto grid_of = [&](const void* kern, int nlist) {
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, 0) != cudaSuccess || occ < 1) occ = 1;
     if (grid_cap > 0 && occ > grid_cap) occ = grid_cap;
-    return std::max(1, std::min(nit, device_sms() * occ));
+    return std::max(1, std::min(nlist, device_sms() * occ));
   };
   auto kcomb = bt_combine<T, BS, SEG, X>;
   auto kapp = bt_apply<T, BS, SEG>;
@@ -770,10 +825,11 @@ static rk_status batch_group_bs(rk_problem** ps, int count, double dt, int nstep
   auto kcor = bt_correct<T, BS, SEG, X>;
   auto kupd = bt_update<T, BS, SEG>;
   auto kcmp = bt_compact<T, BS>;
-  const int gcmp = std::max(1, std::min((nit + kThreads - 1) / kThreads, device_sms() * 4));
-  const int gcomb = grid_of((const void*)kcomb), gapp = grid_of((const void*)kapp),
-            gini = grid_of((const void*)kini), ga = grid_of((const void*)ka), gb = grid_of((const void*)kb),
-            gcor = grid_of((const void*)kcor), gupd = grid_of((const void*)kupd);
+  const int gcmp = std::max(1, std::min((int)((ntiles_total + kThreads - 1) / kThreads), device_sms() * 4));
+  const int gcomb = grid_of((const void*)kcomb, nit), gapp = grid_of((const void*)kapp, nit),
+            gini = grid_of((const void*)kini, nit), ga = grid_of((const void*)ka, (int)ntiles_total),
+            gb = grid_of((const void*)kb, (int)ntiles_total), gcor = grid_of((const void*)kcor, nit),
+            gupd = grid_of((const void*)kupd, nit);
   // stage coefficients of the shared tableau
   bool implicit[kBatchStages];
   for (int i = 0; i < q; ++i) implicit[i] = p0->Al[i * q + i] != 0.0;
@@ -808,6 +864,9 @@ static rk_status batch_group_bs(rk_problem** ps, int count, double dt, int nstep
       up.cb[up.nb++] = dt * p0->b[jj];
     }
   const bool aliased = p0->ke_alias[0] || (!mixed && std::is_same<S, double>::value);
+  // a solve's work list turns into single-tile items once it holds no more
+  // items than two rounds of the sweeps' CTAs
+  const int expand_below = 2 * std::min(ga, gb);
   std::vector<int> predicted(q, 8);
   long long launches = 0;
   for (int step = 0; step < nsteps && status == RK_OK; ++step) {
@@ -826,7 +885,7 @@ static rk_status batch_group_bs(rk_problem** ps, int count, double dt, int nstep
       // the work list of the problems whose solve did not end at the start
       int cur = 0;
       cudaMemsetAsync(dcount + cur, 0, sizeof(int), st);
-      kcmp<<<gcmp, kThreads, 0, st>>>(dp, ditems, dcount + 2, dlist[cur], dcount + cur);
+      kcmp<<<gcmp, kThreads, 0, st>>>(dp, ditems, dcount + 2, dlist[cur], dcount + cur, -1);
       launches += 2;
       int launched = 0, chunk = std::max(2, predicted[i]);
       while (true) {
@@ -835,7 +894,8 @@ static rk_status batch_group_bs(rk_problem** ps, int count, double dt, int nstep
           kb<<<gb, kThreads, 0, st>>>(dp, dlist[cur], dcount + cur, sg, dactive);
           // drop the items of the problems that finished in this iteration
           cudaMemsetAsync(dcount + (cur ^ 1), 0, sizeof(int), st);
-          kcmp<<<gcmp, kThreads, 0, st>>>(dp, dlist[cur], dcount + cur, dlist[cur ^ 1], dcount + (cur ^ 1));
+          kcmp<<<gcmp, kThreads, 0, st>>>(dp, dlist[cur], dcount + cur, dlist[cur ^ 1], dcount + (cur ^ 1),
+                                          expand_below);
           cur ^= 1;
         }
         launches += 3 * chunk;

@@ -13,9 +13,10 @@
 //   [z][y][x] -> [kx][z][y] -> [ky][kx][z] -> [kz][ky][kx]   (forward, P_D^-1 in
 //   the third pass's epilogue) -> [x][kz][ky] -> [y][x][kz] -> [z][y][x]  (inverse).
 // A CTA takes a tile of kCfTile lines (fixed slow index a, consecutive middle
-// indices b) into shared memory; each output element is an n-term complex sum
-// with the twiddles e^{-+2 pi i m / n} read from a table indexed by j k mod n,
-// kCfK outputs of a line per thread (the line element is read once for all).
+// indices b) into shared memory and transforms each line: for n = n1 n2 in two
+// steps of n1 and n2 terms (in place, see cfdm_pass), for a prime n as direct
+// n-term sums; the twiddles e^{-+2 pi i m / n} come from a table indexed by
+// the exponent mod n.
 // Arithmetic in T (FP32 for FP32 storage, FP64 for the FP64 path).
 #pragma once
 #include "rk_csr.cuh"
@@ -28,22 +29,22 @@ constexpr int kCfK = 4;      // outputs per thread per round
 
 template <typename T> struct Cplx { T re, im; };
 
-// Dynamic shared memory of a pass: the line tile, a second tile for the
-// factored transform's intermediate (n1 > 1), and the twiddles.
+constexpr int kCfMaxN1 = 20;  // largest first factor (n <= 400)
+
+// Dynamic shared memory of a pass: the line tile (the factored transform works
+// in place) and the twiddles.
 template <typename T>
-__host__ __device__ constexpr size_t cfdm_smem(int n, int n1) {
-  return (size_t)(n1 > 1 ? 2 : 1) * kCfTile * (n + 1) * sizeof(Cplx<T>) + (size_t)n * sizeof(Cplx<T>);
+__host__ __device__ constexpr size_t cfdm_smem(int n) {
+  return (size_t)kCfTile * (n + 1) * sizeof(Cplx<T>) + (size_t)n * sizeof(Cplx<T>);
 }
 
 // Factor n = n1 n2 for the two-step transform: n1 the largest divisor of n
-// not above sqrt(n) (1 for a prime n: the direct n-term sums), provided the
-// two tiles fit in smem_limit bytes.
-inline int cfdm_factor(int n, size_t elem_bytes, size_t smem_limit) {
+// not above sqrt(n) (1 for a prime n: the direct n-term sums).
+inline int cfdm_factor(int n) {
   int n1 = 1;
-  for (int d = 2; d * d <= n; ++d)
+  for (int d = 2; d * d <= n && d <= kCfMaxN1; ++d)
     if (n % d == 0) n1 = d;
-  const size_t need = 2 * (size_t)kCfTile * (n + 1) * elem_bytes + (size_t)n * elem_bytes;
-  return (n1 > 1 && need <= smem_limit) ? n1 : 1;
+  return n1;
 }
 
 // Parameters of the diagonal scaling P_D^-1 (third pass).
@@ -79,8 +80,7 @@ __global__ void __launch_bounds__(kCfThreads) cfdm_pass(const void* __restrict__
   extern __shared__ __align__(128) unsigned char smem[];
   using C = Cplx<T>;
   C* tile = reinterpret_cast<C*>(smem);                       // [kCfTile][n + 1]
-  C* tileA = n1 > 1 ? tile + (size_t)kCfTile * (n + 1) : tile;  // [kCfTile][n + 1], A[k1][j2] at k1 n2 + j2
-  C* tws = tile + (size_t)(n1 > 1 ? 2 : 1) * kCfTile * (n + 1);  // [n]
+  C* tws = tile + (size_t)kCfTile * (n + 1);                  // [n]
   const int nbt = (n + kCfTile - 1) / kCfTile;
   const int a = blockIdx.x / nbt;
   const int b0 = (blockIdx.x % nbt) * kCfTile;
@@ -166,52 +166,44 @@ __global__ void __launch_bounds__(kCfThreads) cfdm_pass(const void* __restrict__
     return;
   }
   const int n2 = n / n1;
-  // step 1: tasks (j2, group of kCfK consecutive k1), one per warp at a time
+  // step 1, in place: task j2 (one per warp at a time) reads the n1 elements
+  // n2 j1 + j2 of its line into registers and writes A[k1][j2] to the same
+  // slots n2 k1 + j2; the tasks' slot sets are disjoint
   {
-    const int kg = (n1 + kCfK - 1) / kCfK;
-    C* rowA = tileA + (size_t)bb * (n + 1);
-    for (int task = warp; task < n2 * kg; task += kWarps) {
-      const int j2 = task / kg;
-      const int k1b = (task - j2 * kg) * kCfK;
-      T re[kCfK], im[kCfK];
-      int idx[kCfK], inc[kCfK];  // n2 j1 k1 mod n and its step n2 k1 mod n
+    C* rowA = tile + (size_t)bb * (n + 1);
+    for (int j2 = warp; j2 < n2; j2 += kWarps) {
+      if (bb >= tb) continue;
+      C xr[kCfMaxN1];
 #pragma unroll
-      for (int q = 0; q < kCfK; ++q) {
-        const int k1 = k1b + q < n1 ? k1b + q : 0;
-        inc[q] = n2 * k1;  // < n
-        idx[q] = 0;
-        re[q] = im[q] = T(0);
-      }
-      if (bb < tb) {
-        for (int j1 = 0; j1 < n1; ++j1) {
-          const C x = row[n2 * j1 + j2];
+      for (int j1 = 0; j1 < kCfMaxN1; ++j1)
+        if (j1 < n1) xr[j1] = rowA[n2 * j1 + j2];
+      for (int k1 = 0; k1 < n1; ++k1) {
+        const int inc = n2 * k1;  // n2 j1 k1 mod n advances by n2 k1 < n
+        int idx = 0;
+        T re = T(0), im = T(0);
 #pragma unroll
-          for (int q = 0; q < kCfK; ++q) {
-            const C w = tws[idx[q]];
-            re[q] = fma(x.re, w.re, fma(-x.im, w.im, re[q]));
-            im[q] = fma(x.re, w.im, fma(x.im, w.re, im[q]));
-            idx[q] += inc[q];
-            if (idx[q] >= n) idx[q] -= n;
+        for (int j1 = 0; j1 < kCfMaxN1; ++j1)
+          if (j1 < n1) {
+            const C w = tws[idx];
+            re = fma(xr[j1].re, w.re, fma(-xr[j1].im, w.im, re));
+            im = fma(xr[j1].re, w.im, fma(xr[j1].im, w.re, im));
+            idx += inc;
+            if (idx >= n) idx -= n;
           }
-        }
-#pragma unroll
-        for (int q = 0; q < kCfK; ++q)
-          if (k1b + q < n1) {
-            C v;
-            v.re = re[q];
-            v.im = im[q];
-            rowA[(k1b + q) * n2 + j2] = v;
-          }
+        C v;
+        v.re = re;
+        v.im = im;
+        rowA[n2 * k1 + j2] = v;
       }
     }
   }
   __syncthreads();
   if (bb >= tb) return;
   // step 2: tasks (k1, group of kCfK consecutive k2): outputs k = k1 + n1 k2
-  // share the reads of A[k1][.]
+  // share the reads of A[k1][.], stored at n2 k1 + j2
   {
     const int kg = (n2 + kCfK - 1) / kCfK;
-    const C* rowA = tileA + (size_t)bb * (n + 1);
+    const C* rowA = tile + (size_t)bb * (n + 1);
     for (int task = warp; task < n1 * kg; task += kWarps) {
       const int k1 = task / kg;
       const int k2b = (task - k1 * kg) * kCfK;
@@ -224,7 +216,7 @@ __global__ void __launch_bounds__(kCfThreads) cfdm_pass(const void* __restrict__
         idx[q] = 0;
         re[q] = im[q] = T(0);
       }
-      const C* a1 = rowA + k1 * n2;
+      const C* a1 = rowA + (size_t)k1 * n2;
       for (int j2 = 0; j2 < n2; ++j2) {
         const C x = a1[j2];
 #pragma unroll

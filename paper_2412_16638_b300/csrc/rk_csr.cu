@@ -353,8 +353,13 @@ static rk_status cfdm_apply(rk_problem* p, double shift, const SI* in, long long
     }
     smem_optin = v;
   }
-  const int n1 = cfdm_factor(n, sizeof(C), (size_t)smem_optin);
-  const size_t smem = cfdm_smem<T>(n, n1);
+  const int n1 = cfdm_factor(n);
+  const size_t smem = cfdm_smem<T>(n);
+  if (smem > (size_t)smem_optin) {
+    set_error("periodic fast diagonalization: n = %d needs %zu bytes of shared memory (limit %d)", n, smem,
+              smem_optin);
+    return RK_ERR_ARG;
+  }
   const C* tw = static_cast<const C*>(w->cf_tw);
   CfScale sp{};
   sp.s = shift;

@@ -51,6 +51,15 @@ inline int basis_dtype(const rk_solver_desc& s) {
 // bytes per element of the Krylov solution k^eps (FP32 when work vectors are 16-bit)
 inline size_t xsize(int dt) { return dt == RK_F64 ? 8 : 4; }
 
+// Line pitch of the heat problems' Krylov vectors and k^eps in the batched
+// path: lines padded to a multiple of 8 elements, so every full segment of a
+// line starts on a 16-byte boundary (the single-problem path uses the
+// unpadded n^3 prefix of the same buffers).
+inline int batch_pitch(int n) { return (n + 7) / 8 * 8; }
+inline size_t krylov_elems(int op, int n) {
+  return op == RK_OP_HEAT7 ? (size_t)n * n * batch_pitch(n) : (size_t)n * n * n;
+}
+
 // storage x arithmetic dispatch: (f64,f64), (f32,f32), (f16,f32), (bf16,f32)
 template <typename F>
 inline void dispatch_st(int storage, F&& f) {

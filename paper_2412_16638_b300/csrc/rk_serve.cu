@@ -149,6 +149,10 @@ extern "C" rk_status rk_integrate_batch(rk_problem** ps, int count, double dt, i
     if (status != RK_OK) break;
     for (auto* p : g) p->launches += tot.launches - launches_before;
   }
+  // the batched kernels keep k^eps in padded lines: it is no initial guess for
+  // a later single-problem solve
+  for (int i = 0; i < count; ++i)
+    for (auto& v : ps[i]->warm_valid) v = false;
   rk_stats acc{};
   acc.iters_total = tot.iters_total;
   acc.iters_max = tot.iters_max;
