@@ -863,7 +863,8 @@ rk_status rk_create_problem(const rk_problem_desc* desc, const rk_solver_desc* s
   A((void**)&p->u, N * 8);
   A((void**)&p->r, N * 8);
   A((void**)&p->g64, N * 8);
-  const size_t NK = krylov_elems(desc->op, desc->n);  // padded lines for the batched path (heat)
+  // padded lines for the batched path (heat)
+  const size_t NK = krylov_elems(desc->op, desc->n, solver->storage, solver->bj_block);
   A(&p->wr, NK * s);
   A(&p->wz, NK * s);
   A(&p->wp[0], NK * s);
@@ -988,7 +989,8 @@ rk_status rk_set_tableau(rk_problem* p, int q, const double* A_hi, const double*
         p->ke[i] = p->k[i];
         p->ke_alias[i] = true;
       } else {
-        RK_TRY(alloc_dev(p, &p->ke[i], krylov_elems(p->desc.op, p->n) * (p->ke_hi ? 8 : xsize(p->sol.storage))));
+        RK_TRY(alloc_dev(p, &p->ke[i], krylov_elems(p->desc.op, p->n, p->sol.storage, p->sol.bj_block) *
+                                             (p->ke_hi ? 8 : xsize(p->sol.storage))));
       }
     }
   }

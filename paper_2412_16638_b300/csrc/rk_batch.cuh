@@ -43,6 +43,8 @@ struct BatchProb {
   int ntiles;              // its tiles: the single-tile items of the CG tail
   int fine;                // 1: the current CG work list holds its single-tile items
   int ld;                  // line pitch of the Krylov vectors and k^eps (elements; >= n)
+  int full;                // 1: ld is a multiple of the segment, so Krylov segments are
+                           // read and written whole (the padding holds zeros)
   int plane;               // n * ld (n <= 1024, so padded indices fit in int)
   int max_iter;            // CG settings of the problem
   double tol_rel, tol_abs;
@@ -170,7 +172,8 @@ __device__ __forceinline__ bool prob_reduce(A (&v)[NV], double* part, unsigned* 
     const int j = (int)(line % g.n);                                               \
     const int k = (int)(line / g.n);                                               \
     const long long base = line * g.n + i0;                                       \
-    const int pbase = k * (P).plane + j * (P).ld + i0;
+    const int pbase = k * (P).plane + j * (P).ld + i0;                            \
+    const int mk = (P).full ? (SEG) : m;
 
 // Sum of the six neighbours of a segment in the padded layout of the Krylov
 // vectors and k^eps (line pitch ld, plane pitch `plane`): nb_sum with pitched
@@ -228,7 +231,7 @@ __global__ void __launch_bounds__(kThreads) bt_combine(BatchProb<T, BS>* P, cons
     }
     for (int h = 0; h < st.ne; ++h) {
       const double c = st.ce[h] / pb.rs[st.ej[h]].sigma;
-      load_seg<double, X, SEG>(static_cast<const X*>(pb.ke[st.ej[h]]) + pbase, m, t);
+      load_seg<double, X, SEG>(static_cast<const X*>(pb.ke[st.ej[h]]) + pbase, mk, t);
 #pragma unroll
       for (int e = 0; e < SEG; ++e) v[e] = fma(c, t[e], v[e]);
     }
@@ -251,6 +254,7 @@ __global__ void __launch_bounds__(kThreads) bt_apply(BatchProb<T, BS>* P, const 
     double acc[2] = {0.0, 0.0};
     RK_BATCH_CHUNKS(pb, SEG)
     (void)pbase;
+    (void)mk;
     if (live_) {
       double xv[SEG], nb[SEG], yv[SEG];
       load_seg<double, double, SEG>(x + base, m, xv);
@@ -311,7 +315,7 @@ __global__ void __launch_bounds__(kThreads) bt_correct(BatchProb<T, BS>* P, cons
     RK_BATCH_CHUNKS(pb, SEG)
     if (live_ && !st.correct) {
       double v[SEG];
-      load_seg<double, X, SEG>(ke + pbase, m, v);
+      load_seg<double, X, SEG>(ke + pbase, mk, v);
 #pragma unroll
       for (int e = 0; e < SEG; ++e) v[e] *= inv_sigma;
       store_seg<double, double, SEG>(kout + base, m, v);
@@ -321,12 +325,12 @@ __global__ void __launch_bounds__(kThreads) bt_correct(BatchProb<T, BS>* P, cons
       load_seg<double, double, SEG>(pb.g64 + base, m, gs);
       if constexpr (sizeof(X) == 4) {
         float v[SEG], ym[SEG], yp[SEG], zm[SEG], zp[SEG];
-        load_seg<float, X, SEG>(ke + pbase, m, v);
+        load_seg<float, X, SEG>(ke + pbase, mk, v);
         const float left = (i0 > 0) ? wid<float>(ke[pbase - 1]) : 0.f;
         const float right = (i0 + SEG < g.n) ? wid<float>(ke[pbase + SEG]) : 0.f;
         auto seg_or_zero = [&](bool in, long long off, float (&w)[SEG]) {
           if (in) {
-            load_seg<float, X, SEG>(ke + off, m, w);
+            load_seg<float, X, SEG>(ke + off, mk, w);
           } else {
 #pragma unroll
             for (int e = 0; e < SEG; ++e) w[e] = 0.f;
@@ -346,9 +350,9 @@ __global__ void __launch_bounds__(kThreads) bt_correct(BatchProb<T, BS>* P, cons
         }
       } else {
         double v[SEG], nb[SEG];
-        load_seg<double, X, SEG>(ke + pbase, m, v);
+        load_seg<double, X, SEG>(ke + pbase, mk, v);
         bt_nb_sum<double, SEG>(
-            g.n, pb.ld, pb.plane, i0, m, j, k, pbase, v,
+            g.n, pb.ld, pb.plane, i0, mk, j, k, pbase, v,
             [&](long long off, int mm, double (&w)[SEG]) { load_seg<double, X, SEG>(ke + off, mm, w); },
             [&](long long idx) { return wid<double>(ke[idx]); }, nb);
 #pragma unroll
@@ -385,6 +389,7 @@ __global__ void __launch_bounds__(kThreads) bt_update(BatchProb<T, BS>* P, const
     const BatchProb<T, BS>& pb = P[item_.prob];
     RK_BATCH_CHUNKS(pb, SEG)
     (void)pbase;
+    (void)mk;
     if (!live_) continue;
     double v[SEG], t[SEG];
     load_seg<double, double, SEG>(pb.u + base, m, v);
@@ -460,9 +465,10 @@ __global__ void __launch_bounds__(kThreads) bt_cg_init(BatchProb<T, BS>* P, cons
         acc[0] = fma(rv[e], zv[e], acc[0]);
         acc[1] = fma(rv[e], rv[e], acc[1]);
       }
-      store_seg<S, T, SEG>(static_cast<S*>(pb.wr) + pbase, m, rv);
-      store_seg<S, T, SEG>(static_cast<S*>(pb.wz) + pbase, m, zv);
-      store_seg<X, T, SEG>(static_cast<X*>(pb.ke[st.stage]) + pbase, m, zero);
+      // whole segments: the line padding is set to zero here and stays zero
+      store_seg<S, T, SEG>(static_cast<S*>(pb.wr) + pbase, mk, rv);
+      store_seg<S, T, SEG>(static_cast<S*>(pb.wz) + pbase, mk, zv);
+      store_seg<X, T, SEG>(static_cast<X*>(pb.ke[st.stage]) + pbase, mk, zero);
     }
     RK_BATCH_CHUNKS_END
     double tot[2];
@@ -531,14 +537,14 @@ __global__ void __launch_bounds__(kThreads, 4) bt_cg_a(BatchProb<T, BS>* P, cons
         return v;
       };
       T pv[SEG], nb[SEG];
-      pseg(pbase, m, pv);
-      bt_nb_sum<T, SEG>(g.n, pb.ld, pb.plane, i0, m, j, k, pbase, pv, pseg, ppt, nb);
+      pseg(pbase, mk, pv);
+      bt_nb_sum<T, SEG>(g.n, pb.ld, pb.plane, i0, mk, j, k, pbase, pv, pseg, ppt, nb);
 #pragma unroll
       for (int e = 0; e < SEG; ++e) {
         const T w = fma(d, pv[e], o * nb[e]);
         if (e < m) acc[0] = fma(pv[e], w, acc[0]);
       }
-      store_seg<S, T, SEG>(pnew + pbase, m, pv);
+      store_seg<S, T, SEG>(pnew + pbase, mk, pv);
     }
     RK_BATCH_CHUNKS_END
     double tot[1];
@@ -591,14 +597,14 @@ __global__ void __launch_bounds__(kThreads, 4) bt_cg_b(BatchProb<T, BS>* P, cons
     (void)base;
     if (live_) {
       T pv[SEG], nb[SEG], rv[SEG], xv[SEG], zv[SEG];
-      load_seg<T, S, SEG>(p + pbase, m, pv);
+      load_seg<T, S, SEG>(p + pbase, mk, pv);
       bt_nb_sum<T, SEG>(
-          g.n, pb.ld, pb.plane, i0, m, j, k, pbase, pv,
+          g.n, pb.ld, pb.plane, i0, mk, j, k, pbase, pv,
           [&](long long off, int mm, T (&v)[SEG]) { load_seg<T, S, SEG>(p + off, mm, v); },
           [&](long long idx) { return wid<T>(p[idx]); }, nb);
-      load_seg<T, S, SEG>(r + pbase, m, rv);
+      load_seg<T, S, SEG>(r + pbase, mk, rv);
       if (!xzero) {
-        load_seg<T, X, SEG>(x + pbase, m, xv);
+        load_seg<T, X, SEG>(x + pbase, mk, xv);
       } else {
 #pragma unroll
         for (int e = 0; e < SEG; ++e) xv[e] = T(0);
@@ -618,9 +624,9 @@ __global__ void __launch_bounds__(kThreads, 4) bt_cg_b(BatchProb<T, BS>* P, cons
           acc[1] = fma(rv[e], rv[e], acc[1]);
         }
       }
-      store_seg<X, T, SEG>(x + pbase, m, xv);
-      store_seg<S, T, SEG>(r + pbase, m, rv);
-      store_seg<S, T, SEG>(z + pbase, m, zv);
+      store_seg<X, T, SEG>(x + pbase, mk, xv);
+      store_seg<S, T, SEG>(r + pbase, mk, rv);
+      store_seg<S, T, SEG>(z + pbase, mk, zv);
     }
     RK_BATCH_CHUNKS_END
     double tot[2];
@@ -739,7 +745,8 @@ static rk_status batch_group_bs(rk_problem** ps, int count, double dt, int nstep
     b.rs = p->rs;
     // FP64 storage without correction keeps k^eps in k (unpadded); otherwise
     // the Krylov vectors and k^eps use lines padded to batch_pitch(n)
-    b.ld = (!mixed && std::is_same<S, double>::value) ? p->n : batch_pitch(p->n);
+    b.ld = (!mixed && std::is_same<S, double>::value) ? p->n : batch_pitch(p->n, p->sol.storage, BS);
+    b.full = (b.ld % SEG == 0) ? 1 : 0;
     b.plane = p->n * b.ld;
     const long long nsegs = b.g.n2 * b.g.nseg;
     const int ntiles = (int)((nsegs + kThreads - 1) / kThreads);

@@ -52,12 +52,20 @@ inline int basis_dtype(const rk_solver_desc& s) {
 inline size_t xsize(int dt) { return dt == RK_F64 ? 8 : 4; }
 
 // Line pitch of the heat problems' Krylov vectors and k^eps in the batched
-// path: lines padded to a multiple of 8 elements, so every full segment of a
-// line starts on a 16-byte boundary (the single-problem path uses the
-// unpadded n^3 prefix of the same buffers).
-inline int batch_pitch(int n) { return (n + 7) / 8 * 8; }
-inline size_t krylov_elems(int op, int n) {
-  return op == RK_OP_HEAT7 ? (size_t)n * n * batch_pitch(n) : (size_t)n * n * n;
+// path: lines padded to a whole number of the thread segments of the problem's
+// storage type and block size (seg_of), so every segment of a line is a full,
+// 16-byte aligned vector (the single-problem path uses the unpadded n^3 prefix
+// of the same buffers).
+inline int batch_seg(int storage, int bs) {
+  const int v = (storage == RK_F16 || storage == RK_BF16) ? 8 : 4;
+  return bs > v ? bs : v;
+}
+inline int batch_pitch(int n, int storage, int bs) {
+  const int s = batch_seg(storage, bs);
+  return (n + s - 1) / s * s;
+}
+inline size_t krylov_elems(int op, int n, int storage, int bs) {
+  return op == RK_OP_HEAT7 ? (size_t)n * n * batch_pitch(n, storage, bs) : (size_t)n * n * n;
 }
 
 // storage x arithmetic dispatch: (f64,f64), (f32,f32), (f16,f32), (bf16,f32)

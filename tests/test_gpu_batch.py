@@ -100,3 +100,19 @@ def test_batch_rejects_bad_input(rk):
     with pytest.raises(rk.RKError):
         rk.rk_integrate_batch([p.h, p.h], 1e-3, 1)
     p.close()
+
+
+def test_single_then_batched_steps_of_one_problem(rk):
+    """A problem stepped by the single-problem path (which uses the buffers
+    unpadded) and then in a batch (lines padded to whole segments) matches the
+    oracle: the batched path rewrites its padding before it reads it."""
+    dt = 1e-3
+    for n, st in ((17, "f32"), (23, "f16"), (20, "f32")):
+        u0 = synth.heat_modes(seed=n, n_random=5).evaluate(n)
+        with make(rk, n, 1.3, st, "dirk3", u0) as p:
+            rk.rk_integrate(p.h, dt, 2)
+            rk.rk_integrate_batch([p.h], dt, 2)
+            got = p.state()
+        ref = dirk.integrate(u0, dt, 4, tableau.get("dirk3"), operators.HeatOperator(n, 1.3),
+                             dirk.Solver("cg", bs=8, tol_rel=1e-13))
+        assert rel_l2(got, ref) < BOUND[st], (n, st)
