@@ -501,8 +501,8 @@ __global__ void __launch_bounds__(kThreads) bt_cg_init(BatchProb<T, BS>* P, cons
 }
 
 // Sweep A of every unfinished problem: p = z + beta p_old (rounded to S),
-// p.Ap; its last CTA forms alpha (ping-pong p buffers chosen by the
-// problem's iteration parity).
+// p.Ap from the grid edges; its last CTA forms alpha (ping-pong p buffers
+// chosen by the problem's iteration parity).
 template <typename S, typename T, int BS, int SEG>
 __global__ void __launch_bounds__(kThreads, 4) bt_cg_a(BatchProb<T, BS>* P, const BatchItem* items, const int* nitems_dev,
                                                        BatchStage st, int* active) {
@@ -536,14 +536,29 @@ __global__ void __launch_bounds__(kThreads, 4) bt_cg_a(BatchProb<T, BS>* P, cons
         if (!first) v = rnd<S, T>(fma(beta, wid<T>(pold[idx]), v));
         return v;
       };
-      T pv[SEG], nb[SEG];
+      // p.Ap from the grid edges: A = d I + o (sum of the six neighbours) is
+      // symmetric, so p.Ap = sum_e p_e (d p_e + 2 o (p_{e+x} + p_{e+y} + p_{e+z}))
+      // with every edge taken once from its lower element (neighbours outside
+      // the grid zero): only the upper neighbours are formed
+      T pv[SEG], up[SEG], tmp[SEG];
       pseg(pbase, mk, pv);
-      bt_nb_sum<T, SEG>(g.n, pb.ld, pb.plane, i0, mk, j, k, pbase, pv, pseg, ppt, nb);
+      const T right = (i0 + SEG < g.n) ? ppt(pbase + SEG) : T(0);
 #pragma unroll
-      for (int e = 0; e < SEG; ++e) {
-        const T w = fma(d, pv[e], o * nb[e]);
-        if (e < m) acc[0] = fma(pv[e], w, acc[0]);
+      for (int e = 0; e < SEG; ++e) up[e] = (e + 1 < SEG) ? pv[e + 1] : right;
+      if (j < g.n - 1) {
+        pseg(pbase + pb.ld, mk, tmp);
+#pragma unroll
+        for (int e = 0; e < SEG; ++e) up[e] += tmp[e];
       }
+      if (k < g.n - 1) {
+        pseg(pbase + pb.plane, mk, tmp);
+#pragma unroll
+        for (int e = 0; e < SEG; ++e) up[e] += tmp[e];
+      }
+      const T o2 = o + o;
+#pragma unroll
+      for (int e = 0; e < SEG; ++e)
+        if (e < m) acc[0] = fma(pv[e], fma(d, pv[e], o2 * up[e]), acc[0]);
       store_seg<S, T, SEG>(pnew + pbase, mk, pv);
     }
     RK_BATCH_CHUNKS_END
