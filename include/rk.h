@@ -179,14 +179,18 @@ rk_status rk_destroy_problem(rk_problem* p);
 rk_status rk_set_wait_limit(rk_problem* p, unsigned long long spins);
 
 /* Introspection of a problem: device bytes the library allocated for it, kernel
- * launches issued so far, and the block-Jacobi blocks of the last
- * preconditioner set-up on the CSR path with how many of them adaptive
- * precision stored in FP16 (0 / 0 before a set-up and on the heat path). */
+ * launches issued so far, the block-Jacobi blocks of the last preconditioner
+ * set-up on the CSR path with how many of them adaptive precision stored in
+ * FP16 (0 / 0 before a set-up and on the heat path), and this problem's own
+ * outcome in its last rk_integrate_batch call (RK_OK, RK_ERR_NOT_CONVERGED or
+ * RK_ERR_NONFINITE; RK_OK before any): the call returns the worst outcome of
+ * its problems, while the other problems' states are advanced correctly. */
 typedef struct {
   size_t device_bytes;
   long long launches;
   long long bj_blocks;
   long long bj_half_blocks;
+  int batch_status;
 } rk_problem_info;
 
 rk_status rk_get_problem_info(const rk_problem* p, rk_problem_info* info);

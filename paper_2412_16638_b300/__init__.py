@@ -67,7 +67,7 @@ class rk_job_info(ctypes.Structure):
 
 class rk_problem_info(ctypes.Structure):
     _fields_ = [("device_bytes", ctypes.c_size_t), ("launches", ctypes.c_longlong), ("bj_blocks", ctypes.c_longlong),
-                ("bj_half_blocks", ctypes.c_longlong)]
+                ("bj_half_blocks", ctypes.c_longlong), ("batch_status", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

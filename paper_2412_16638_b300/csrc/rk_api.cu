@@ -917,6 +917,7 @@ rk_status rk_get_problem_info(const rk_problem* p, rk_problem_info* info) {
   info->launches = p->launches;
   info->bj_blocks = p->bj_blocks;
   info->bj_half_blocks = p->bj_half_blocks;
+  info->batch_status = p->batch_status;
   return RK_OK;
 }
 

@@ -981,6 +981,10 @@ static rk_status batch_group_bs(rk_problem** ps, int count, double dt, int nstep
       const double first_less = sb + xb;                     // no p_old, x read at a solve's first iteration
       for (const Prob& b : hp)
         out->bytes += (double)b.g.N * (fixed * nsteps + per_iter * b.iters_total - first_less * b.solves);
+      for (int i = 0; i < count; ++i) {
+        const Prob& b = hp[i];
+        ps[i]->batch_status = b.status == 5 ? RK_ERR_NONFINITE : (b.not_converged ? RK_ERR_NOT_CONVERGED : RK_OK);
+      }
       for (const Prob& b : hp) {
         out->iters_total += b.iters_total;
         out->iters_max = std::max(out->iters_max, b.iters_max);

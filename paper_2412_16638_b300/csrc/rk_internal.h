@@ -265,6 +265,7 @@ struct rk_problem {
   int last_iters[10]{};
   unsigned wait_spins = 0;  // bound of the sweeps' main-loop TMA waits (0 = default)
   bool warm_valid[10]{};  // slot holds a solution usable as the next initial guess
+  rk_status batch_status = RK_OK;  // this problem's outcome in its last batched call
   bool has_state = false;
   // CSR path
   rk::Csr csr;

@@ -80,6 +80,7 @@ extern "C" rk_status rk_integrate_batch(rk_problem** ps, int count, double dt, i
         return RK_ERR_ARG;
       }
   }
+  for (int i = 0; i < count; ++i) ps[i]->batch_status = RK_OK;
   auto t0 = std::chrono::steady_clock::now();
   cudaStream_t user = ps[0]->st;
   for (int i = 1; i < count; ++i)
@@ -435,11 +436,15 @@ static void worker_loop(rk_server* s) {
         rk_stats bst{};
         rk_status st = rk_integrate_batch(ps.data(), (int)ps.size(), dt, 1, &bst);
         const std::string err = st == RK_OK ? "" : rk_last_error();
+        // each job gets its own outcome: a job that went non-finite fails
+        // alone, the others of the group were stepped correctly
+        const bool per_problem = st == RK_OK || st == RK_ERR_NOT_CONVERGED || st == RK_ERR_NONFINITE;
         for (auto& j : group) {
           for (size_t i = 0; i < act.size(); ++i)
             if (act[i] == j) {
-              results[i] = st;
-              errors[i] = err;
+              results[i] = per_problem ? j->p->batch_status : st;
+              errors[i] = results[i] == RK_ERR_NONFINITE ? "non-finite value or CG breakdown in the batched step"
+                                                         : (per_problem ? "" : err);
             }
         }
         // per-job iteration statistics are not separated in a batched step;

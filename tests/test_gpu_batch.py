@@ -116,3 +116,28 @@ def test_single_then_batched_steps_of_one_problem(rk):
         ref = dirk.integrate(u0, dt, 4, tableau.get("dirk3"), operators.HeatOperator(n, 1.3),
                              dirk.Solver("cg", bs=8, tol_rel=1e-13))
         assert rel_l2(got, ref) < BOUND[st], (n, st)
+
+
+def test_nonfinite_problem_fails_alone(rk):
+    """One problem of a batch with an infinite value in its state: the call
+    reports RK_ERR_NONFINITE, that problem's own outcome says so, and the
+    other problems are advanced exactly as without it."""
+    dt, steps = 1e-3, 2
+    good = [(20, 1.0), (33, 0.5)]
+    u0s = [synth.heat_modes(seed=40 + i, n_random=4).evaluate(n) for i, (n, _k) in enumerate(good)]
+    bad_u0 = synth.sine_mode(24)
+    bad_u0[77] = np.inf
+    ref_batch = [make(rk, n, kap, "f32", "sdirk2", u0) for (n, kap), u0 in zip(good, u0s)]
+    rk.rk_integrate_batch([p.h for p in ref_batch], dt, steps)
+    want = [p.state() for p in ref_batch]
+    ps = [make(rk, n, kap, "f32", "sdirk2", u0) for (n, kap), u0 in zip(good, u0s)]
+    bad = make(rk, 24, 1.0, "f32", "sdirk2", bad_u0)
+    with pytest.raises(rk.RKError) as e:
+        rk.rk_integrate_batch([ps[0].h, bad.h, ps[1].h], dt, steps)
+    assert e.value.status == rk.RK_ERR_NONFINITE
+    assert rk.rk_get_problem_info(bad.h).batch_status == rk.RK_ERR_NONFINITE
+    for p, w in zip(ps, want):
+        assert rk.rk_get_problem_info(p.h).batch_status == rk.RK_OK
+        assert np.array_equal(p.state(), w)
+    for p in ps + ref_batch + [bad]:
+        p.close()

@@ -191,3 +191,30 @@ def test_new_problem_kinds_same_alone_and_in_mix(rk):
         assert rel_l2(out, ref) < 1e-6, (d.op, d.n)
         # FP32 solves (BF16 basis for the compressed GMRES job) against the oracle
         assert rel_l2(out, orc()) < 1e-6, (d.op, d.n)
+
+
+def test_nonfinite_job_fails_alone(rk):
+    """A job whose state turns non-finite fails with RK_ERR_NONFINITE; jobs
+    submitted with it (batched with it when they share a tick) complete and
+    match the oracle."""
+    dt, steps = 1e-3, 4
+    srv = rk.rk_server_create(8 << 30, 16)
+    try:
+        good = [(24, 1.0, "sdirk2", "f32"), (40, 0.5, "dirk3", "f32"), (32, 2.0, "sdirk2", "f32")]
+        d, s, t, _u = job_args(rk, 28, 1.0, "sdirk2", "f32", 0)
+        bad_u0 = synth.sine_mode(28)
+        bad_u0[5] = np.nan
+        ids = [rk.rk_submit_job(srv, d, s, *t, bad_u0, dt, steps)]
+        for i, (n, kap, tab, st) in enumerate(good):
+            dd, ss, tt, u0 = job_args(rk, n, kap, tab, st, 60 + i)
+            ids.append(rk.rk_submit_job(srv, dd, ss, *tt, u0, dt, steps))
+        with pytest.raises(rk.RKError) as e:
+            rk.rk_wait_job(srv, ids[0], None)
+        assert e.value.status == rk.RK_ERR_NONFINITE
+        for jid, (i, (n, kap, tab, st)) in zip(ids[1:], enumerate(good)):
+            out = np.empty(n ** 3)
+            rk.rk_wait_job(srv, jid, out, allow_not_converged=True)
+            ref = oracle_run(n, kap, tab, 60 + i, dt, steps)
+            assert rel_l2(out, ref) < BOUND[st], (n, tab)
+    finally:
+        rk.rk_server_destroy(srv)
