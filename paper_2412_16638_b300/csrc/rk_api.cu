@@ -880,6 +880,8 @@ rk_status rk_create_problem(const rk_problem_desc* desc, const rk_solver_desc* s
       r = RhsScalars{};
       r.sigma = 1.0;
       r.want_scale = (solver->storage == RK_F16);
+      // (not with warm starts: the previous solution is kept at scale 1)
+      r.want_range = (solver->storage == RK_F32 || solver->storage == RK_BF16) && !solver->warm_start;
     }
     if (cudaMemcpy(p->rs, z.data(), sizeof(RhsScalars) * 10, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(p->sc, 0, sizeof(CgScalars)) != cudaSuccess || cudaMemset(p->u, 0, N * 8) != cudaSuccess) {

@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(kThreads) bt_apply(BatchProb<T, BS>* P, const 
       RhsScalars* rs = pb.rs + st.stage;
       rs->gg = tot[0];
       rs->gmax = tot[1];
-      rs->sigma = (rs->want_scale && tot[1] > 0.0 && isfinite(tot[1])) ? 1.0 / tot[1] : 1.0;
+      rs->sigma = rhs_scale(rs, tot[0], tot[1], pb.g.N);
     }
   }
 }

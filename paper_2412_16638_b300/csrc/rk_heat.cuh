@@ -45,8 +45,25 @@ struct RhsScalars {
   double sigma;  // storage scale (1/||g||_inf for FP16, else 1)
   double res2;   // ||true residual||^2 from the FP64 correction
   unsigned ticket;
-  int want_scale;
+  int want_scale;   // FP16 storage: sigma = 1 / ||g||_inf
+  int want_range;   // FP32/BF16 storage: a power-of-two sigma when ||g|| leaves [2^-40, 2^40]
 };
+
+// Storage scale sigma of a stage right-hand side g (the solve runs on sigma g).
+// FP16 storage: 1 / ||g||_inf, for its narrow range (Sec. 2.3).  FP32 and BF16
+// storage: 1 while the RMS of g lies in [2^-40, 2^40], else the power of two
+// that brings it near 1.  Scaling by a power of two is exact, so results in
+// the normal range are unchanged; it keeps the low-precision products of a
+// decayed solution (|g| ~ 1e-20 after many steps of a stiff problem) clear of
+// underflow, where r.z and p.Ap would otherwise round to zero and break CG.
+// FP64 storage: 1.
+__host__ __device__ inline double rhs_scale(const RhsScalars* rs, double gg, double gmax, long long N) {
+  if (rs->want_scale) return (gmax > 0.0 && isfinite(gmax)) ? 1.0 / gmax : 1.0;
+  if (!rs->want_range || !(gg > 0.0) || !isfinite(gg) || N < 1) return 1.0;
+  const double rms = sqrt(gg / (double)N);
+  if (rms >= 0x1p-40 && rms <= 0x1p40) return 1.0;
+  return ldexp(1.0, -ilogb(rms));
+}
 
 // Sum of the six neighbours of every element of a segment (zero outside the
 // grid).  own[] holds the field on the segment (zeros past m); seg(off, m, v)
@@ -141,7 +158,7 @@ __global__ void __launch_bounds__(kThreads) heat_apply_f64(HeatGeo g, const doub
   if (grid_reduce<2, 2u>(acc, partials, &rs->ticket, tot)) {
     rs->gg = tot[0];
     rs->gmax = tot[1];
-    rs->sigma = (rs->want_scale && tot[1] > 0.0 && isfinite(tot[1])) ? 1.0 / tot[1] : 1.0;
+    rs->sigma = rhs_scale(rs, tot[0], tot[1], g.N);
   }
 }
 

@@ -65,7 +65,7 @@ static __global__ void __launch_bounds__(kThreads) vec_norms_f64(const double* _
   if (grid_reduce<2, 2u>(acc, partials, &rs->ticket, tot)) {
     rs->gg = tot[0];
     rs->gmax = tot[1];
-    rs->sigma = (rs->want_scale && tot[1] > 0.0 && isfinite(tot[1])) ? 1.0 / tot[1] : 1.0;
+    rs->sigma = rhs_scale(rs, tot[0], tot[1], N);
   }
 }
 

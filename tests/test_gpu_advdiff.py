@@ -236,3 +236,20 @@ def test_gmres_and_step_with_adaptive_block_jacobi(rk):
     ref_u = dirk.integrate(u0, dt, steps, tableau.dirk3(), operators.CSROperator(n, oracle_L(n)),
                            dirk.Solver("gmres", bs=8, tol_rel=1e-13, restart=30))
     assert rel_l2(u, ref_u) < 1e-6
+
+
+def test_tiny_state_fp32_storage_scale_gmres(rk):
+    """GMRES path with a state 1e-25 times the bump: the power-of-two storage
+    scale keeps the FP32 solve clear of underflow, so the step equals 1e-25
+    times the unit-data step."""
+    n, dt, steps = 18, 5e-4, 2
+    u0 = synth.gaussian_bump(n)
+    outs = []
+    for scale in (1.0, 1e-25):
+        with make(rk, n, storage="f32", bs=8, tol=1e-7, correct=1, tab="dirk3", u0=scale * u0, max_iter=800) as p:
+            rk.rk_integrate(p.h, dt, steps, allow_not_converged=True)
+            outs.append(p.state() / scale)
+    ref = dirk.integrate(u0, dt, steps, tableau.dirk3(), operators.CSROperator(n, oracle_L(n)),
+                         dirk.Solver("gmres", bs=8, tol_rel=1e-13, restart=30))
+    assert rel_l2(outs[0], ref) < 1e-6
+    assert rel_l2(outs[1], ref) < 1e-6

@@ -351,3 +351,28 @@ def test_large_grid_512_segment_sweeps_closed_form(rk):
     # sampled point may deviate a few times more (measured 1.9e-6 of max |u0|)
     idx = np.random.default_rng(0).integers(0, n ** 3, 4096)
     np.testing.assert_allclose(u[idx], R * u0[idx], rtol=0, atol=1e-5 * np.abs(u0).max())
+
+
+@pytest.mark.parametrize("path", ["single", "batch"])
+def test_tiny_state_fp32_storage_scale(rk, path):
+    """A state 1e-25 times the unit data (what many steps of a stiff problem
+    leave): FP32 products of its right-hand side (~1e-21) would underflow and
+    break CG; the power-of-two storage scale keeps the step exact up to the
+    scale, so the result is 1e-25 times the unit-data result."""
+    n, kappa, dt, steps = 24, 2.0, 1e-3, 3
+    u1 = synth.heat_modes(seed=7, n_random=6).evaluate(n)
+    tab = rk.tableaux.get("sdirk2")
+    outs = []
+    for scale in (1.0, 1e-25):
+        with rk.Problem(rk.problem_desc(n=n, kappa=kappa),
+                        rk.solver_desc(bj_block=8, tol_rel=1e-7, storage="f32", correct=1, max_iter=2000),
+                        tableau=tab, u0=scale * u1) as p:
+            if path == "single":
+                rk.rk_integrate(p.h, dt, steps)
+            else:
+                rk.rk_integrate_batch([p.h], dt, steps)
+            outs.append(p.state() / scale)
+    ref = dirk.integrate(u1, dt, steps, tableau.get("sdirk2"), operators.HeatOperator(n, kappa),
+                         dirk.Solver("cg", bs=8, tol_rel=1e-13))
+    assert rel_l2(outs[0], ref) < 1e-6
+    assert rel_l2(outs[1], ref) < 1e-6
