@@ -35,6 +35,7 @@ constexpr int kGmStages = 6;     // ring stages
 constexpr int kGmDots = 2 * kGmMax + 2;
 constexpr int kGmThreads = 256;
 constexpr int kGmRows = kGmTile / kGmThreads;  // rows per thread in a tile
+constexpr int kGmSpmvRows = 2;                   // rows whose slots a thread loads together
 
 // Sliced ELL, slices of 32 rows: entry k of row r sits at
 // ((r / 32) * kSellW + k) * 32 + r % 32, so the 32 rows of a warp read each
@@ -303,7 +304,7 @@ __host__ __device__ constexpr size_t gm_dc_smem() {
 // gm_dc_finish in the last CTA.  With j = m (the cycle's last column) only
 // the dots of u_m are formed (no product).  Persistent grid over tiles.
 template <typename S, typename B, typename T>
-__global__ void __launch_bounds__(kGmThreads, 2) gm_dc_arnoldi(const int* __restrict__ scol,
+__global__ void __launch_bounds__(kGmThreads, sizeof(T) == 4 ? 3 : 2) gm_dc_arnoldi(const int* __restrict__ scol,
                                                                const S* __restrict__ sval, T cs,
                                                                const S* __restrict__ z, B* __restrict__ V,
                                                                long long ldv, B* __restrict__ wbuf, long long N,
@@ -346,11 +347,11 @@ __global__ void __launch_bounds__(kGmThreads, 2) gm_dc_arnoldi(const int* __rest
     if (spmv) {
       // the product for the tile's rows (coalesced slot loads, L2-resident gathers)
 #pragma unroll
-      for (int h = 0; h < kGmRows; h += 4) {
-        int c[4][kSellW];
-        T a[4][kSellW];
+      for (int h = 0; h < kGmRows; h += kGmSpmvRows) {
+        int c[kGmSpmvRows][kSellW];
+        T a[kGmSpmvRows][kSellW];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
+        for (int e = 0; e < kGmSpmvRows; ++e) {
           const long long r = r0 + (long long)(h + e) * kGmThreads + tid;
 #pragma unroll
           for (int k = 0; k < kSellW; ++k) {
@@ -359,7 +360,7 @@ __global__ void __launch_bounds__(kGmThreads, 2) gm_dc_arnoldi(const int* __rest
           }
         }
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
+        for (int e = 0; e < kGmSpmvRows; ++e) {
           const long long r = r0 + (long long)(h + e) * kGmThreads + tid;
           T acc_r = T(0);
 #pragma unroll
