@@ -195,6 +195,23 @@ typedef struct {
 
 rk_status rk_get_problem_info(const rk_problem* p, rk_problem_info* info);
 
+/* Guard-band check (a stand-in for a device memory checker).  When the
+ * environment variable RK_GUARD_BYTES = G > 0 is set while a problem
+ * allocates, each of its device blocks gets G bytes (rounded up to 256) of a
+ * fixed pattern on both sides.  This call waits for the problem's stream,
+ * reads every guard band back and returns in *corrupted_bytes how many pattern
+ * bytes were overwritten (0 when no kernel wrote outside its buffers), and in
+ * *guarded_blocks (may be NULL) how many blocks carry guards (0 when the
+ * problem was created without them).  Errors: RK_ERR_ARG, RK_ERR_CUDA. */
+rk_status rk_check_guards(rk_problem* p, long long* corrupted_bytes, int* guarded_blocks);
+
+/* Test hook of the guard check: overwrite byte `offset` (0 <= offset < the
+ * guard size) of the leading guard band of the problem's guarded block number
+ * `block` (allocation order) with the pattern's complement, from the host.
+ * It writes inside the allocation, never into a buffer.  Errors: RK_ERR_ARG
+ * (no such block or offset), RK_ERR_CUDA. */
+rk_status rk_guard_poke(rk_problem* p, int block, long long offset);
+
 /* ---- single operations of the step (for testing the kernels) ------------- */
 
 /* y = L x in FP64 (the explicit evaluation k = f(y) of Sec. 4.2, without the

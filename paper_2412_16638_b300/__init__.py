@@ -92,6 +92,8 @@ _SIGS = {
     "rk_destroy_problem": [_P],
     "rk_set_wait_limit": [_P, ctypes.c_ulonglong],
     "rk_get_problem_info": [_P, ctypes.POINTER(rk_problem_info)],
+    "rk_check_guards": [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_I)],
+    "rk_guard_poke": [_P, _I, ctypes.c_longlong],
     "rk_apply_op": [_P, _P, _P, _I],
     "rk_solve": [_P, _D, _P, _P, _I, ctypes.POINTER(rk_stats)],
     "rk_apply_precond": [_P, _D, _P, _P, _I],
@@ -234,6 +236,20 @@ def rk_get_problem_info(p):
     info = rk_problem_info()
     _check(_lib.rk_get_problem_info(p, ctypes.byref(info)))
     return info
+
+
+def rk_check_guards(p):
+    """(corrupted guard bytes, guarded blocks) of a problem created with
+    RK_GUARD_BYTES > 0 in the environment."""
+    bad = ctypes.c_longlong()
+    n = _I()
+    _check(_lib.rk_check_guards(p, ctypes.byref(bad), ctypes.byref(n)))
+    return bad.value, n.value
+
+
+def rk_guard_poke(p, block, offset):
+    """Test hook: change one byte of a guard band (see rk_check_guards)."""
+    return _check(_lib.rk_guard_poke(p, int(block), int(offset)))
 
 
 def rk_set_wait_limit(p, spins):

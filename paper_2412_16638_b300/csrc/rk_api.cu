@@ -57,18 +57,60 @@ int grid_for(const void* kernel, long long work_items, int threads) {
   return (int)(g < 1 ? 1 : g);
 }
 
+// Guard bands: with the environment variable RK_GUARD_BYTES = G > 0 when a
+// block is allocated, the block gets G bytes (rounded up to 256, so alignment
+// is kept) of the pattern kGuardByte on each side; rk_check_guards counts the
+// pattern bytes that changed, which catches out-of-bounds writes of the
+// kernels near their buffers (the substitute for a memory checker).
+static const unsigned char kGuardByte = 0xA5;
+
+static size_t guard_bytes() {
+  const char* env = std::getenv("RK_GUARD_BYTES");
+  if (!env) return 0;
+  char* end = nullptr;
+  const long long v = std::strtoll(env, &end, 10);
+  if (end == env || v <= 0) return 0;
+  const long long capped = v < (1LL << 24) ? v : (1LL << 24);
+  return ((size_t)capped + 255) / 256 * 256;
+}
+
 rk_status alloc_dev(rk_problem* p, void** ptr, size_t bytes) {
   *ptr = nullptr;
   if (bytes == 0) return RK_OK;
-  cudaError_t e = cudaMalloc(ptr, bytes);
+  const size_t g = guard_bytes();
+  void* base = nullptr;
+  cudaError_t e = cudaMalloc(&base, bytes + 2 * g);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    *ptr = nullptr;
-    set_error("cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    set_error("cudaMalloc(%zu) failed: %s", bytes + 2 * g, cudaGetErrorString(e));
     return RK_ERR_OOM;
+  }
+  if (g > 0) {
+    unsigned char* b = static_cast<unsigned char*>(base);
+    if (cudaMemset(b, kGuardByte, g) != cudaSuccess || cudaMemset(b + g + bytes, kGuardByte, g) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(base);
+      set_error("guard band initialisation failed");
+      return RK_ERR_CUDA;
+    }
+    *ptr = b + g;
+    p->guards.push_back(rk_problem::Guard{base, *ptr, bytes, g});
+  } else {
+    *ptr = base;
   }
   p->bytes += bytes;
   return RK_OK;
+}
+
+void free_dev(rk_problem* p, void* ptr) {
+  if (!ptr) return;
+  for (size_t i = 0; i < p->guards.size(); ++i)
+    if (p->guards[i].user == ptr) {
+      cudaFree(p->guards[i].base);
+      p->guards.erase(p->guards.begin() + (long)i);
+      return;
+    }
+  cudaFree(ptr);
 }
 
 // Dense inverse of a tridiagonal m x m block (diag dd, off-diagonals off) by
@@ -477,6 +519,7 @@ static rk_status launch_ke(rk_problem* p, F&& f) {
 // float64 oracle, with the implicit solves in the storage/arithmetic
 // precision and every explicit evaluation and linear combination in FP64.
 rk_status step_impl(rk_problem* p, double dt, rk_stats* acc) {
+  NvtxRange range_step("rk_step");
   const int q = p->q;
   const bool mixed = p->sol.correct != 0;
   bool implicit[kMaxStages];
@@ -520,7 +563,10 @@ rk_status step_impl(rk_problem* p, double dt, rk_stats* acc) {
     int iters = 0, status = 0;
     // with an FP64 k^eps the solver writes its own solution type into wx
     void* xsol = p->ke_hi ? p->wx : p->ke[i];
-    RK_TRY(krylov_solve(p, shift, p->g64, rs, xsol, i, &iters, &status));
+    {
+      NvtxRange range_solve("stage solve");
+      RK_TRY(krylov_solve(p, shift, p->g64, rs, xsol, i, &iters, &status));
+    }
     if (acc) {
       acc->iters_total += iters;
       acc->iters_max = std::max(acc->iters_max, iters);
@@ -585,6 +631,7 @@ rk_status step_impl(rk_problem* p, double dt, rk_stats* acc) {
           RK_CUDA(cudaGetLastError());
         }
         int it2 = 0, st2 = 0;
+        NvtxRange range_refine("refinement solve");
         RK_TRY(krylov_solve(p, shift, p->res64, rsd, p->wdelta, 8, &it2, &st2));
         if (st2 == 5 || st2 == 6) {
           set_error("stage %d refinement solve failed (status %d)", i, st2);
@@ -756,9 +803,7 @@ static rk_status check_solver(const rk_solver_desc* s, const rk_problem_desc* d)
 
 static void free_problem(rk_problem* p) {
   if (!p) return;
-  auto f = [](void* ptr) {
-    if (ptr) cudaFree(ptr);
-  };
+  auto f = [p](void* ptr) { free_dev(p, ptr); };
   f(p->u);
   f(p->r);
   f(p->g64);
@@ -920,6 +965,38 @@ rk_status rk_get_problem_info(const rk_problem* p, rk_problem_info* info) {
   info->bj_blocks = p->bj_blocks;
   info->bj_half_blocks = p->bj_half_blocks;
   info->batch_status = p->batch_status;
+  return RK_OK;
+}
+
+rk_status rk_check_guards(rk_problem* p, long long* corrupted_bytes, int* guarded_blocks) {
+  if (!p || !corrupted_bytes) {
+    set_error("rk_check_guards: NULL argument");
+    return RK_ERR_ARG;
+  }
+  RK_CUDA(cudaStreamSynchronize(p->st));
+  long long bad = 0;
+  std::vector<unsigned char> h;
+  for (const auto& gd : p->guards) {
+    h.resize(gd.guard);
+    const unsigned char* b = static_cast<const unsigned char*>(gd.base);
+    for (const unsigned char* src : {b, b + gd.guard + gd.bytes}) {
+      RK_CUDA(cudaMemcpy(h.data(), src, gd.guard, cudaMemcpyDeviceToHost));
+      for (unsigned char c : h) bad += (c != kGuardByte);
+    }
+  }
+  *corrupted_bytes = bad;
+  if (guarded_blocks) *guarded_blocks = (int)p->guards.size();
+  return RK_OK;
+}
+
+rk_status rk_guard_poke(rk_problem* p, int block, long long offset) {
+  if (!p || block < 0 || block >= (int)p->guards.size() || offset < 0 ||
+      offset >= (long long)p->guards[block].guard) {
+    set_error("rk_guard_poke: no guarded block %d with a byte %lld", block, offset);
+    return RK_ERR_ARG;
+  }
+  RK_CUDA(cudaStreamSynchronize(p->st));
+  RK_CUDA(cudaMemset(static_cast<unsigned char*>(p->guards[block].base) + offset, (unsigned char)~kGuardByte, 1));
   return RK_OK;
 }
 

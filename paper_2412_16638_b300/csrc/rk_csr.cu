@@ -272,28 +272,28 @@ rk_status csr_setup(rk_problem* p) {
 
 rk_status csr_free(rk_problem* p) {
   Csr& c = p->csr;
-  if (c.rowptr) cudaFree(c.rowptr);
-  if (c.cols) cudaFree(c.cols);
-  if (c.v64) cudaFree(c.v64);
-  if (c.vS) cudaFree(c.vS);
+  if (c.rowptr) free_dev(p, c.rowptr);
+  if (c.cols) free_dev(p, c.cols);
+  if (c.v64) free_dev(p, c.v64);
+  if (c.vS) free_dev(p, c.vS);
   c = Csr{};
   if (p->gw) {
     GmresWork* w = p->gw;
-    if (w->V) cudaFree(w->V);
-    if (w->wbuf) cudaFree(w->wbuf);
-    if (w->z) cudaFree(w->z);
-    if (w->scol) cudaFree(w->scol);
-    if (w->sval) cudaFree(w->sval);
-    if (w->cf_tw) cudaFree(w->cf_tw);
-    if (w->cf_c[0]) cudaFree(w->cf_c[0]);
-    if (w->cf_c[1]) cudaFree(w->cf_c[1]);
-    if (w->cf_tmp) cudaFree(w->cf_tmp);
-    if (w->partials) cudaFree(w->partials);
-    if (w->sc) cudaFree(w->sc);
+    if (w->V) free_dev(p, w->V);
+    if (w->wbuf) free_dev(p, w->wbuf);
+    if (w->z) free_dev(p, w->z);
+    if (w->scol) free_dev(p, w->scol);
+    if (w->sval) free_dev(p, w->sval);
+    if (w->cf_tw) free_dev(p, w->cf_tw);
+    if (w->cf_c[0]) free_dev(p, w->cf_c[0]);
+    if (w->cf_c[1]) free_dev(p, w->cf_c[1]);
+    if (w->cf_tmp) free_dev(p, w->cf_tmp);
+    if (w->partials) free_dev(p, w->partials);
+    if (w->sc) free_dev(p, w->sc);
     if (w->h_sc) cudaFreeHost(w->h_sc);
     for (auto& e : w->minv) {
-      if (e.dev) cudaFree(e.dev);
-      if (e.flags) cudaFree(e.flags);
+      if (e.dev) free_dev(p, e.dev);
+      if (e.flags) free_dev(p, e.flags);
     }
     delete w;
     p->gw = nullptr;

@@ -246,9 +246,9 @@ rk_status fdm_precond_f64(rk_problem* p, double shift, const double* r, double* 
 
 void fdm_free(rk_problem* p) {
   if (!p->fdm) return;
-  if (p->fdm->q) cudaFree(p->fdm->q);
-  if (p->fdm->mu) cudaFree(p->fdm->mu);
-  if (p->fdm->t) cudaFree(p->fdm->t);
+  if (p->fdm->q) free_dev(p, p->fdm->q);
+  if (p->fdm->mu) free_dev(p, p->fdm->mu);
+  if (p->fdm->t) free_dev(p, p->fdm->t);
   delete p->fdm;
   p->fdm = nullptr;
 }

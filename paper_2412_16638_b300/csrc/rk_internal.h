@@ -11,6 +11,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/rk.h"
 #include "rk_device.cuh"
 #include "rk_heat.cuh"
@@ -266,6 +268,14 @@ struct rk_problem {
   unsigned wait_spins = 0;  // bound of the sweeps' main-loop TMA waits (0 = default)
   bool warm_valid[10]{};  // slot holds a solution usable as the next initial guess
   rk_status batch_status = RK_OK;  // this problem's outcome in its last batched call
+  // guard bands (RK_GUARD_BYTES > 0 at allocation): per block the cudaMalloc
+  // base, the pointer handed out, its size and the guard size on each side
+  struct Guard {
+    void* base;
+    void* user;
+    size_t bytes, guard;
+  };
+  std::vector<Guard> guards;
   bool has_state = false;
   // CSR path
   rk::Csr csr;
@@ -281,6 +291,17 @@ struct rk_problem {
 
 namespace rk {
 rk_status alloc_dev(rk_problem* p, void** ptr, size_t bytes);
+// Free a block from alloc_dev (its guard bands too, when it has them).
+void free_dev(rk_problem* p, void* ptr);
+
+// NVTX range for the lifetime of the object (steps, stage solves, batched
+// calls, server ticks): visible to profilers, a few nanoseconds without one.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 rk_status get_minv(rk_problem* p, double shift, const void** out);
 // Heat path: the cache entry (host and device copies) for this shift.
 rk_status get_minv_entry(rk_problem* p, double shift, const MinvEntry** out);

@@ -45,6 +45,7 @@ struct GroupKey {
 using namespace rk;
 
 extern "C" rk_status rk_integrate_batch(rk_problem** ps, int count, double dt, int nsteps, rk_stats* stats) {
+  NvtxRange range_batch("rk_integrate_batch");
   if (!ps || count < 1) {
     set_error("rk_integrate_batch: need at least one problem");
     return RK_ERR_ARG;
@@ -397,6 +398,7 @@ static void worker_loop(rk_server* s) {
     if (act.empty()) continue;
     // one step for every resident job: this tick's index and start time
     const long long tick = s->tick++;
+    NvtxRange range_tick("serve tick");
     {
       const auto now = std::chrono::steady_clock::now();
       std::lock_guard<std::mutex> lk(s->mu);
