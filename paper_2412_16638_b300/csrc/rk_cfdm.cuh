@@ -29,22 +29,28 @@ constexpr int kCfK = 4;      // outputs per thread per round
 
 template <typename T> struct Cplx { T re, im; };
 
-constexpr int kCfMaxN1 = 20;  // largest first factor (n <= 400)
-
-// Dynamic shared memory of a pass: the line tile (the factored transform works
-// in place) and the twiddles.
-template <typename T>
-__host__ __device__ constexpr size_t cfdm_smem(int n) {
-  return (size_t)kCfTile * (n + 1) * sizeof(Cplx<T>) + (size_t)n * sizeof(Cplx<T>);
-}
+constexpr int kCfMaxN1 = 20;    // largest first factor (n <= 400)
+constexpr int kCfMaxTab = 1024;  // entries of the two small-DFT tables, n1^2 + n2^2
 
 // Factor n = n1 n2 for the two-step transform: n1 the largest divisor of n
-// not above sqrt(n) (1 for a prime n: the direct n-term sums).
-inline int cfdm_factor(int n) {
+// not above sqrt(n), provided the tables of the two small transforms (n1^2 +
+// n2^2 entries) stay small; else 1 (the direct n-term sums, e.g. for a prime n).
+__host__ __device__ inline int cfdm_factor(int n) {
   int n1 = 1;
   for (int d = 2; d * d <= n && d <= kCfMaxN1; ++d)
     if (n % d == 0) n1 = d;
-  return n1;
+  const int n2 = n / n1;
+  return (n1 > 1 && n1 * n1 + n2 * n2 <= kCfMaxTab) ? n1 : 1;
+}
+
+// Dynamic shared memory of a pass: the line tile (the factored transform works
+// in place), the n twiddles, and for n = n1 n2 the tables of the two small
+// transforms.
+template <typename T>
+__host__ __device__ inline size_t cfdm_smem(int n) {
+  const int n1 = cfdm_factor(n), n2 = n / n1;
+  const size_t tab = n1 > 1 ? (size_t)n1 * n1 + (size_t)n2 * n2 : 0;
+  return (size_t)kCfTile * (n + 1) * sizeof(Cplx<T>) + ((size_t)n + tab) * sizeof(Cplx<T>);
 }
 
 // Parameters of the diagonal scaling P_D^-1 (third pass).
@@ -64,12 +70,13 @@ struct CfScale {
 // in + sc->j * in_jstride elements.
 //
 // With n = n1 n2 (n1 > 1) each line is transformed in two steps (Cooley-Tukey,
-// decimation in time: j = n2 j1 + j2, k = k1 + n1 k2):
-//   A[k1][j2] = sum_{j1} x[n2 j1 + j2] w^{n2 j1 k1}       (n1 terms)
-//   X[k]      = sum_{j2} A[k mod n1][j2] w^{j2 k}           (n2 terms)
-// (w = e^{-+2 pi i / n}; the second step's twiddle w^{j2 k} is the inner
-// transform's w^{n1 j2 k2} times the usual w^{j2 k1}), n1 + n2 products per
-// output instead of n.
+// decimation in time: j = n2 j1 + j2, k = k1 + n1 k2, w = e^{-+2 pi i / n}):
+//   A[k1][j2]      = w^{j2 k1} sum_{j1} x[n2 j1 + j2] w^{n2 j1 k1}   (n1 terms)
+//   X[k1 + n1 k2]  = sum_{j2} A[k1][j2] w^{n1 j2 k2}                  (n2 terms)
+// since w^{jk} = w^{n2 j1 k1} w^{j2 k1} w^{n1 j2 k2} (the w^{n j1 k2} factor is
+// 1): n1 + n2 + 1 products per output instead of n.  The two small transforms
+// read their twiddles from n1 x n1 and n2 x n2 tables, so the inner loops do
+// no index arithmetic mod n.
 template <typename SI, typename SO, typename T, bool IN_REAL, bool OUT_REAL>
 __global__ void __launch_bounds__(kCfThreads) cfdm_pass(const void* __restrict__ in, void* __restrict__ out, int n,
                                                         int n1, const Cplx<T>* __restrict__ tw, int inverse,
@@ -81,14 +88,28 @@ __global__ void __launch_bounds__(kCfThreads) cfdm_pass(const void* __restrict__
   using C = Cplx<T>;
   C* tile = reinterpret_cast<C*>(smem);                       // [kCfTile][n + 1]
   C* tws = tile + (size_t)kCfTile * (n + 1);                  // [n]
+  const int n2 = n / n1;
+  C* W1 = tws + n;             // [n1][n1]: w^{n2 (j1 k1 mod n1)} at k1 n1 + j1
+  C* W2 = W1 + n1 * n1;        // [n2][n2]: w^{n1 (j2 k2 mod n2)} at k2 n2 + j2
   const int nbt = (n + kCfTile - 1) / kCfTile;
   const int a = blockIdx.x / nbt;
   const int b0 = (blockIdx.x % nbt) * kCfTile;
   const int tb = min(kCfTile, n - b0);
-  for (int m = threadIdx.x; m < n; m += blockDim.x) {
+  auto twid = [&](int m) {
     C w = tw[m];
     if (inverse) w.im = -w.im;
-    tws[m] = w;
+    return w;
+  };
+  for (int m = threadIdx.x; m < n; m += blockDim.x) tws[m] = twid(m);
+  if (n1 > 1) {
+    for (int e = threadIdx.x; e < n1 * n1; e += blockDim.x) {
+      const int k1 = e / n1, j1 = e - k1 * n1;
+      W1[e] = twid(n2 * ((j1 * k1) % n1));
+    }
+    for (int e = threadIdx.x; e < n2 * n2; e += blockDim.x) {
+      const int k2 = e / n2, j2 = e - k2 * n2;
+      W2[e] = twid(n1 * ((j2 * k2) % n2));
+    }
   }
   // load the lines (a, b0 + bb, 0..n-1), coalesced along the line
   for (int e = threadIdx.x; e < tb * n; e += blockDim.x) {
@@ -165,10 +186,11 @@ __global__ void __launch_bounds__(kCfThreads) cfdm_pass(const void* __restrict__
     }
     return;
   }
-  const int n2 = n / n1;
   // step 1, in place: task j2 (one per warp at a time) reads the n1 elements
-  // n2 j1 + j2 of its line into registers and writes A[k1][j2] to the same
-  // slots n2 k1 + j2; the tasks' slot sets are disjoint
+  // n2 j1 + j2 of its line into registers and writes
+  // A[k1][j2] = w^{j2 k1} sum_{j1} x[n2 j1 + j2] w^{n2 j1 k1} to the same slots
+  // n2 k1 + j2 (the tasks' slot sets are disjoint); j2 k1 < n, so the twiddle
+  // needs no reduction mod n
   {
     C* rowA = tile + (size_t)bb * (n + 1);
     for (int j2 = warp; j2 < n2; j2 += kWarps) {
@@ -178,29 +200,27 @@ __global__ void __launch_bounds__(kCfThreads) cfdm_pass(const void* __restrict__
       for (int j1 = 0; j1 < kCfMaxN1; ++j1)
         if (j1 < n1) xr[j1] = rowA[n2 * j1 + j2];
       for (int k1 = 0; k1 < n1; ++k1) {
-        const int inc = n2 * k1;  // n2 j1 k1 mod n advances by n2 k1 < n
-        int idx = 0;
+        const C* w1 = W1 + k1 * n1;
         T re = T(0), im = T(0);
 #pragma unroll
         for (int j1 = 0; j1 < kCfMaxN1; ++j1)
           if (j1 < n1) {
-            const C w = tws[idx];
+            const C w = w1[j1];
             re = fma(xr[j1].re, w.re, fma(-xr[j1].im, w.im, re));
             im = fma(xr[j1].re, w.im, fma(xr[j1].im, w.re, im));
-            idx += inc;
-            if (idx >= n) idx -= n;
           }
+        const C t = tws[j2 * k1];
         C v;
-        v.re = re;
-        v.im = im;
+        v.re = fma(re, t.re, -im * t.im);
+        v.im = fma(re, t.im, im * t.re);
         rowA[n2 * k1 + j2] = v;
       }
     }
   }
   __syncthreads();
   if (bb >= tb) return;
-  // step 2: tasks (k1, group of kCfK consecutive k2): outputs k = k1 + n1 k2
-  // share the reads of A[k1][.], stored at n2 k1 + j2
+  // step 2: X[k1 + n1 k2] = sum_{j2} A[k1][j2] w^{n1 (j2 k2 mod n2)}; tasks
+  // (k1, group of kCfK consecutive k2) share the reads of A[k1][.]
   {
     const int kg = (n2 + kCfK - 1) / kCfK;
     const C* rowA = tile + (size_t)bb * (n + 1);
@@ -208,12 +228,10 @@ __global__ void __launch_bounds__(kCfThreads) cfdm_pass(const void* __restrict__
       const int k1 = task / kg;
       const int k2b = (task - k1 * kg) * kCfK;
       T re[kCfK], im[kCfK];
-      int idx[kCfK], kk[kCfK];  // j2 k mod n, and k (0 for outputs past the end)
+      const C* w2[kCfK];
 #pragma unroll
       for (int q = 0; q < kCfK; ++q) {
-        const int k = k1 + n1 * (k2b + q);
-        kk[q] = k2b + q < n2 ? k : 0;
-        idx[q] = 0;
+        w2[q] = W2 + (size_t)(k2b + q < n2 ? k2b + q : 0) * n2;
         re[q] = im[q] = T(0);
       }
       const C* a1 = rowA + (size_t)k1 * n2;
@@ -221,11 +239,9 @@ __global__ void __launch_bounds__(kCfThreads) cfdm_pass(const void* __restrict__
         const C x = a1[j2];
 #pragma unroll
         for (int q = 0; q < kCfK; ++q) {
-          const C w = tws[idx[q]];
+          const C w = w2[q][j2];
           re[q] = fma(x.re, w.re, fma(-x.im, w.im, re[q]));
           im[q] = fma(x.re, w.im, fma(x.im, w.re, im[q]));
-          idx[q] += kk[q];
-          if (idx[q] >= n) idx[q] -= n;
         }
       }
 #pragma unroll
