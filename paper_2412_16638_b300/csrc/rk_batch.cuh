@@ -37,11 +37,9 @@ struct BatchProb {
   void* wp[2];
   CgScalars* sc;           // the problem's CG scalars
   RhsScalars* rs;          // the problem's per-stage right-hand-side scalars [0..7]
-  double* part;            // per-item partials, ntiles x 2
+  double* part;            // per-item partials, nitems x 2
   unsigned* ticket;        // per-problem reduction ticket
   int nitems;              // items (kBatchTilesPerItem tiles) of this problem
-  int ntiles;              // its tiles: the single-tile items of the CG tail
-  int fine;                // 1: the current CG work list holds its single-tile items
   int ld;                  // line pitch of the Krylov vectors and k^eps (elements; >= n)
   int full;                // 1: ld is a multiple of the segment, so Krylov segments are
                            // read and written whole (the padding holds zeros)
@@ -477,7 +475,6 @@ __global__ void __launch_bounds__(kThreads) bt_cg_init(BatchProb<T, BS>* P, cons
       sc->tol_rel = pb.tol_rel;
       sc->tol_abs = pb.tol_abs;
       sc->max_iter = pb.max_iter;
-      pb.fine = 0;
       sc->rz = tot[0];
       sc->rr = tot[1];
       sc->gg = tot[1];
@@ -563,7 +560,7 @@ __global__ void __launch_bounds__(kThreads, 4) bt_cg_a(BatchProb<T, BS>* P, cons
     }
     RK_BATCH_CHUNKS_END
     double tot[1];
-    if (prob_reduce<T, 1>(acc, pb.part, pb.ticket, item_.idx, pb.fine ? pb.ntiles : pb.nitems, tot)) {
+    if (prob_reduce<T, 1>(acc, pb.part, pb.ticket, item_.idx, pb.nitems, tot)) {
       sc->pAp = tot[0];
       const double alpha = sc->rz / tot[0];
       sc->alpha = alpha;
@@ -645,7 +642,7 @@ __global__ void __launch_bounds__(kThreads, 4) bt_cg_b(BatchProb<T, BS>* P, cons
     }
     RK_BATCH_CHUNKS_END
     double tot[2];
-    if (prob_reduce<T, 2>(acc, pb.part, pb.ticket, item_.idx, pb.fine ? pb.ntiles : pb.nitems, tot)) {
+    if (prob_reduce<T, 2>(acc, pb.part, pb.ticket, item_.idx, pb.nitems, tot)) {
       const double rz_new = tot[0];
       sc->beta = rz_new / sc->rz;
       sc->rz = rz_new;
@@ -666,29 +663,17 @@ __global__ void __launch_bounds__(kThreads, 4) bt_cg_b(BatchProb<T, BS>* P, cons
 }
 
 // Work list of the problems still iterating: the items of unfinished problems
-// of `in` are appended to `out` (order arbitrary: every problem's reduction
-// adds its partials by item index, so results do not depend on it).  When
-// `in` has at most expand_below items, the multi-tile items are split into
-// single-tile items (slot = tile index) and their problems switch to the
-// per-tile reduction count: the few problems of a solve's tail then spread
-// over more CTAs.  All items of a problem are in `in`, so a problem switches
-// whole.
+// of `in` are appended to `out`.  Their order is arbitrary: every problem's
+// reduction adds its partials by item index, so results depend neither on it
+// nor on the launch shape.
 template <typename T, int BS>
 __global__ void __launch_bounds__(kThreads) bt_compact(BatchProb<T, BS>* P, const BatchItem* in, const int* in_count,
-                                                       BatchItem* out, int* out_count, int expand_below) {
+                                                       BatchItem* out, int* out_count) {
   const int n = *in_count;
-  const bool expand = n <= expand_below;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const BatchItem it = in[i];
-    BatchProb<T, BS>& pb = P[it.prob];
-    if (pb.sc->done) continue;
-    if (expand) {  // also items of one tile: their slot becomes the tile index
-      const int slot = atomicAdd(out_count, it.nch);
-      for (int t = 0; t < it.nch; ++t) out[slot + t] = BatchItem{it.prob, it.chunk + t, 1, it.chunk + t};
-      pb.fine = 1;
-    } else {
-      out[atomicAdd(out_count, 1)] = it;
-    }
+    if (P[it.prob].sc->done) continue;
+    out[atomicAdd(out_count, 1)] = it;
   }
 }
 
@@ -738,7 +723,7 @@ static rk_status batch_group_bs(rk_problem** ps, int count, double dt, int nstep
   // host descriptors and the work list
   std::vector<Prob> hp(count);
   std::vector<BatchItem> items;
-  long long part_total = 0, ntiles_total = 0;
+  long long part_total = 0;
   for (int i = 0; i < count; ++i) {
     const rk_problem* p = ps[i];
     Prob& b = hp[i];
@@ -766,13 +751,10 @@ static rk_status batch_group_bs(rk_problem** ps, int count, double dt, int nstep
     const long long nsegs = b.g.n2 * b.g.nseg;
     const int ntiles = (int)((nsegs + kThreads - 1) / kThreads);
     b.nitems = (ntiles + kBatchTilesPerItem - 1) / kBatchTilesPerItem;
-    b.ntiles = ntiles;
-    b.fine = 0;
-    ntiles_total += ntiles;
     for (int c = 0; c < b.nitems; ++c)
       items.push_back(BatchItem{i, c * kBatchTilesPerItem, std::min(kBatchTilesPerItem, ntiles - c * kBatchTilesPerItem), c});
     b.part = reinterpret_cast<double*>(part_total);  // offset of the problem's partials (fixed up below)
-    part_total += 2LL * ntiles;
+    part_total += 2LL * b.nitems;
     b.max_iter = p->sol.max_iter;
     b.tol_rel = p->sol.tol_rel;
     b.tol_abs = p->sol.tol_abs;
@@ -811,8 +793,8 @@ static rk_status batch_group_bs(rk_problem** ps, int count, double dt, int nstep
       cudaMallocAsync((void**)&dpart, sizeof(double) * part_total, st) != cudaSuccess ||
       cudaMallocAsync((void**)&dtick, sizeof(unsigned) * count, st) != cudaSuccess ||
       cudaMallocAsync((void**)&dactive, sizeof(int), st) != cudaSuccess ||
-      cudaMallocAsync((void**)&dlist[0], sizeof(BatchItem) * ntiles_total, st) != cudaSuccess ||
-      cudaMallocAsync((void**)&dlist[1], sizeof(BatchItem) * ntiles_total, st) != cudaSuccess ||
+      cudaMallocAsync((void**)&dlist[0], sizeof(BatchItem) * items.size(), st) != cudaSuccess ||
+      cudaMallocAsync((void**)&dlist[1], sizeof(BatchItem) * items.size(), st) != cudaSuccess ||
       cudaMallocAsync((void**)&dcount, sizeof(int) * 3, st) != cudaSuccess ||
       cudaMallocHost((void**)&hactive, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
@@ -847,10 +829,10 @@ static rk_status batch_group_bs(rk_problem** ps, int count, double dt, int nstep
   auto kcor = bt_correct<T, BS, SEG, X>;
   auto kupd = bt_update<T, BS, SEG>;
   auto kcmp = bt_compact<T, BS>;
-  const int gcmp = std::max(1, std::min((int)((ntiles_total + kThreads - 1) / kThreads), device_sms() * 4));
+  const int gcmp = std::max(1, std::min((nit + kThreads - 1) / kThreads, device_sms() * 4));
   const int gcomb = grid_of((const void*)kcomb, nit), gapp = grid_of((const void*)kapp, nit),
-            gini = grid_of((const void*)kini, nit), ga = grid_of((const void*)ka, (int)ntiles_total),
-            gb = grid_of((const void*)kb, (int)ntiles_total), gcor = grid_of((const void*)kcor, nit),
+            gini = grid_of((const void*)kini, nit), ga = grid_of((const void*)ka, nit),
+            gb = grid_of((const void*)kb, nit), gcor = grid_of((const void*)kcor, nit),
             gupd = grid_of((const void*)kupd, nit);
   // stage coefficients of the shared tableau
   bool implicit[kBatchStages];
@@ -886,9 +868,6 @@ static rk_status batch_group_bs(rk_problem** ps, int count, double dt, int nstep
       up.cb[up.nb++] = dt * p0->b[jj];
     }
   const bool aliased = p0->ke_alias[0] || (!mixed && std::is_same<S, double>::value);
-  // a solve's work list turns into single-tile items once it holds no more
-  // items than two rounds of the sweeps' CTAs
-  const int expand_below = 2 * std::min(ga, gb);
   std::vector<int> predicted(q, 8);
   long long launches = 0;
   for (int step = 0; step < nsteps && status == RK_OK; ++step) {
@@ -907,7 +886,7 @@ static rk_status batch_group_bs(rk_problem** ps, int count, double dt, int nstep
       // the work list of the problems whose solve did not end at the start
       int cur = 0;
       cudaMemsetAsync(dcount + cur, 0, sizeof(int), st);
-      kcmp<<<gcmp, kThreads, 0, st>>>(dp, ditems, dcount + 2, dlist[cur], dcount + cur, -1);
+      kcmp<<<gcmp, kThreads, 0, st>>>(dp, ditems, dcount + 2, dlist[cur], dcount + cur);
       launches += 2;
       int launched = 0, chunk = std::max(2, predicted[i]);
       while (true) {
@@ -916,8 +895,7 @@ static rk_status batch_group_bs(rk_problem** ps, int count, double dt, int nstep
           kb<<<gb, kThreads, 0, st>>>(dp, dlist[cur], dcount + cur, sg, dactive);
           // drop the items of the problems that finished in this iteration
           cudaMemsetAsync(dcount + (cur ^ 1), 0, sizeof(int), st);
-          kcmp<<<gcmp, kThreads, 0, st>>>(dp, dlist[cur], dcount + cur, dlist[cur ^ 1], dcount + (cur ^ 1),
-                                          expand_below);
+          kcmp<<<gcmp, kThreads, 0, st>>>(dp, dlist[cur], dcount + cur, dlist[cur ^ 1], dcount + (cur ^ 1));
           cur ^= 1;
         }
         launches += 3 * chunk;

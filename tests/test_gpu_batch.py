@@ -141,3 +141,30 @@ def test_nonfinite_problem_fails_alone(rk):
         assert np.array_equal(p.state(), w)
     for p in ps + ref_batch + [bad]:
         p.close()
+
+
+def test_launch_shape_does_not_change_results(rk):
+    """The same batch under fixed launch shapes (RK_BATCH_GRID_CAP: 1, 2 and
+    the occupancy limit) gives bit-identical states: every reduction adds its
+    partials in item order, whichever CTA computed them."""
+    import os
+    dt, steps = 1e-3, 2
+    specs = [(17, 0.4), (32, 2.0), (45, 1.0), (9, 5.0)]
+    outs = []
+    old = os.environ.get("RK_BATCH_GRID_CAP")
+    try:
+        for cap in ("1", "2", "0"):
+            os.environ["RK_BATCH_GRID_CAP"] = cap
+            ps = [make(rk, n, kap, "f32", "dirk3", synth.heat_modes(seed=n, n_random=3).evaluate(n)) for n, kap in specs]
+            rk.rk_integrate_batch([p.h for p in ps], dt, steps)
+            outs.append([p.state() for p in ps])
+            for p in ps:
+                p.close()
+    finally:
+        if old is None:
+            os.environ.pop("RK_BATCH_GRID_CAP", None)
+        else:
+            os.environ["RK_BATCH_GRID_CAP"] = old
+    for other in outs[1:]:
+        for a, b in zip(outs[0], other):
+            assert np.array_equal(a, b)
