@@ -37,22 +37,17 @@ S host_round(double v) {
     return __double2bfloat16(v);
 }
 
-// Largest dynamic shared memory a block of fdm_pass<S> may use on this
-// device: the opt-in limit minus the kernel's static shared memory.
-template <typename S>
-int smem_dynamic_max() {
-  static int v = 0;
-  if (v == 0) {
-    int dev = 0, optin = 0;
-    cudaFuncAttributes fa{};
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || optin <= 0)
-      optin = 227 * 1024;
-    if (cudaFuncGetAttributes(&fa, (const void*)fdm_pass<S>) != cudaSuccess) fa.sharedSizeBytes = 4096;
-    cudaGetLastError();
-    v = optin - (int)fa.sharedSizeBytes;
-  }
-  return v;
+// Largest dynamic shared memory a block of `kern` may use on this device:
+// the opt-in limit minus the kernel's static shared memory.
+int smem_dynamic_max(const void* kern) {
+  int dev = 0, optin = 0;
+  cudaFuncAttributes fa{};
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || optin <= 0)
+    optin = 227 * 1024;
+  if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) fa.sharedSizeBytes = 4096;
+  cudaGetLastError();
+  return optin - (int)fa.sharedSizeBytes;
 }
 
 template <typename S>
@@ -68,22 +63,27 @@ rk_status setup_typed(rk_problem* p) {
     set_error("cuTensorMapEncodeTiled is not available");
     return RK_ERR_CUDA;
   }
+  // n <= 128: one CTA per 128-row tile with all N columns; n > 128: CTA
+  // pairs on 256-row tiles, each CTA holding one N half of Q
   FdmGeo g{};
   g.n = n;
   g.rows = n * n;
-  g.ntiles = n <= 128 ? 1 : 2;
-  g.nt = ((n + g.ntiles - 1) / g.ntiles + 15) / 16 * 16;
+  g.pair = n > 128 ? 1 : 0;
+  g.ntiles = 1;
+  g.nt = (n + 15) / 16 * 16;
   g.kblocks = (int)((n * sizeof(S) + 127) / 128);
-  g.mtiles = (g.rows + kFdmRows - 1) / kFdmRows;
-  const size_t budget = (size_t)smem_dynamic_max<S>();
-  const size_t fixed = fdm_smem_bytes(g.nt, g.kblocks, 0);
+  g.mtiles = g.pair ? (g.rows + kFdmPairRows - 1) / kFdmPairRows : (g.rows + kFdmRows - 1) / kFdmRows;
+  const void* kern = g.pair ? (const void*)fdm_pass_pair<S> : (const void*)fdm_pass<S>;
+  const int qrows = g.pair ? g.nt / 2 : g.nt;  // Q rows held by one CTA
+  const size_t budget = (size_t)smem_dynamic_max(kern);
+  const size_t fixed = fdm_smem_bytes(qrows, g.kblocks, 0);
   g.stages = budget > fixed ? (int)std::min<size_t>(kFdmMaxStages, (budget - fixed) / kFdmStageBytes) : 0;
   if (g.stages < 2) {
     set_error("fast diagonalization: shared memory too small for n = %d", n);
     return RK_ERR_ARG;
   }
   f.geo = g;
-  f.smem = fdm_smem_bytes(g.nt, g.kblocks, g.stages);
+  f.smem = fdm_smem_bytes(qrows, g.kblocks, g.stages);
 
   // Q_jk = sqrt(2/(n+1)) sin((j+1)(k+1) pi/(n+1)); mu_k = 4 sin^2((k+1) pi/(2(n+1)))
   std::vector<S> qh((size_t)n * n);
@@ -123,7 +123,7 @@ rk_status setup_typed(rk_problem* p) {
   {
     const cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)n};
     const cuuint64_t strides[1] = {(cuuint64_t)n * sizeof(S)};
-    const cuuint32_t box[2] = {kb_elems, (cuuint32_t)g.nt};
+    const cuuint32_t box[2] = {kb_elems, (cuuint32_t)qrows};
     if (enc(&f.qmap, tma_dtype<S>(), 2, f.q, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
@@ -132,13 +132,16 @@ rk_status setup_typed(rk_problem* p) {
     }
   }
   // Set once per kernel to the largest size any problem uses.  At least
-  // 120 KB is requested so one CTA is resident per SM: its 256 TMEM columns
-  // are then always free at allocation.
+  // 120 KB is requested so one CTA is resident per SM: its tensor memory
+  // columns (256, or all 512 for a pair) are then always free at allocation.
   static std::once_flag once;
   static cudaError_t attr = cudaSuccess;
   std::call_once(once, [] {
-    attr = cudaFuncSetAttribute((const void*)fdm_pass<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                smem_dynamic_max<S>());
+    const void* k1 = (const void*)fdm_pass<S>;
+    const void* k2 = (const void*)fdm_pass_pair<S>;
+    attr = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_dynamic_max(k1));
+    if (attr == cudaSuccess)
+      attr = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_dynamic_max(k2));
     cudaGetLastError();
   });
   if (attr != cudaSuccess) {
@@ -146,9 +149,22 @@ rk_status setup_typed(rk_problem* p) {
     return RK_ERR_CUDA;
   }
   f.smem = std::max<size_t>(f.smem, 120 * 1024);
-  const int total = g.mtiles * g.ntiles;
-  const int slots = device_sms() / g.ntiles * g.ntiles;
-  f.grid = std::max(g.ntiles, std::min(total, slots));
+  if (g.pair) {
+    // persistent pairs: as many as can be resident at once (a cluster's two
+    // CTAs must share a GPC, so this can be below half the SM count)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * std::max(1, device_sms() / 2));
+    cfg.blockDim = dim3(kFdmPairThreads);
+    cfg.dynamicSmemBytes = f.smem;
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, (const void*)fdm_pass_pair<S>, &cfg) != cudaSuccess || clusters < 1) {
+      cudaGetLastError();
+      clusters = std::max(1, device_sms() / 2);
+    }
+    f.grid = 2 * std::min(g.mtiles, clusters);
+  } else {
+    f.grid = std::max(1, std::min(g.mtiles, device_sms()));
+  }
   f.ok = true;
   return RK_OK;
 }
@@ -172,8 +188,12 @@ rk_status apply_typed(rk_problem* p, double shift, bool cg, int solve, int idx) 
   for (const Pass& ps : passes) {
     const int kid = ps.mode == kFdmDot ? K_FDM_DOT : (ps.mode == kFdmScale ? K_FDM_SCALE : K_FDM);
     prof_begin(p, kid, (ps.mode == kFdmDot ? 3.0 : 2.0) * Ns, cg ? solve : -1, cg ? idx : -1);
-    fdm_pass<S><<<f.grid, kFdmThreads, f.smem, p->st>>>(*ps.in, f.qmap, g, ps.mode, c, f.mu, ps.out, r, cg ? 1 : 0,
-                                                         p->sc, p->partials);
+    if (g.pair)
+      fdm_pass_pair<S><<<f.grid, kFdmPairThreads, f.smem, p->st>>>(*ps.in, f.qmap, g, ps.mode, c, f.mu, ps.out, r,
+                                                                cg ? 1 : 0, p->sc, p->partials);
+    else
+      fdm_pass<S><<<f.grid, kFdmThreads, f.smem, p->st>>>(*ps.in, f.qmap, g, ps.mode, c, f.mu, ps.out, r, cg ? 1 : 0,
+                                                           p->sc, p->partials);
     prof_end(p);
   }
   if (cudaGetLastError() != cudaSuccess) {

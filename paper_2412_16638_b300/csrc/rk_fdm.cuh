@@ -18,19 +18,20 @@
 // Unlike the paper's three strided kernels (one per T), every pass reads and
 // writes with unit stride and contracts on the tensor cores.
 //
-// Per CTA (one per SM, persistent over 128-row tiles): warp 0 issues TMA
-// loads (the CTA's N tile of Q once, then 128 x 128-byte K blocks of X into a
-// ring of stages); warp 1 owns the tensor memory and issues tcgen05.mma with
-// the accumulator in TMEM (two accumulators, so the epilogue of one tile
-// overlaps the MMAs of the next); warps 2-9 read the accumulator with
-// tcgen05.ld and store (two warps per TMEM lane quadrant, alternating
-// 16-column chunks, so the stores of one hide the latency of the other).
-// The ring holds as many 16 KB X stages as shared memory allows beside the
-// Q tile, up to 6 (measured: 4 and 6 stages give the same time at n = 256;
-// the two CTAs that share an X tile for the two N halves read it from L2
-// twice, and that L2 traffic, not the ring depth, bounds the pass).  Every mbarrier wait is bounded; a wait that runs out
-// sets a shared flag that stops the other roles, the CTA lets its copies and
-// MMAs land, frees its tensor memory and reports status 6.
+// n <= 128: one CTA per SM, persistent over 128-row tiles (fdm_pass).  Warp 0
+// issues TMA loads (Q once, then 128 x 128-byte K blocks of X into a ring of
+// stages); warp 1 owns the tensor memory and issues tcgen05.mma with the
+// accumulator in TMEM (two accumulators, so the epilogue of one tile overlaps
+// the MMAs of the next); warps 2-9 read the accumulator with tcgen05.ld and
+// store (two warps per TMEM lane quadrant, alternating 16-column chunks, so
+// the stores of one hide the latency of the other).  The ring holds as many
+// 16 KB X stages as shared memory allows beside Q, up to 6.
+// 128 < n <= 256: Q (up to 256 KB) no longer fits one CTA's shared memory,
+// and the pass runs on CTA pairs with tcgen05.mma.cta_group::2 (fdm_pass_pair
+// below), each CTA holding one N half of Q.
+// Every mbarrier wait is bounded; a wait that runs out sets a shared flag that
+// stops the other roles, the CTA lets its copies and MMAs land, frees its
+// tensor memory and reports status 6.
 //
 // Storage float runs kind::tf32, __half and __nv_bfloat16 run kind::f16 with
 // the same type for both operands; accumulation is FP32 in TMEM.
@@ -309,6 +310,351 @@ __global__ void __launch_bounds__(kFdmThreads, 1)
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(kFdmTmemCols) : "memory");
+  }
+  const bool failed = *fail != 0;
+  if (failed && threadIdx.x == 0) {
+    sc->status = 6;
+    sc->done = 1;
+  }
+  if (mode != kFdmDot) return;
+  double a[1] = {(double)dot};
+  double tot[1];
+  if (grid_reduce<1, 0u>(a, partials, &sc->ticket, tot)) {
+    if (sc->status == 6) return;
+    const double rz = tot[0];
+    if (sc->iter > 0) sc->beta = sc->beta * (rz / sc->rz);
+    sc->rz = rz;
+    if (!isfinite(rz)) {
+      sc->done = 1;
+      sc->status = 5;
+    } else if (!(rz > 0.0)) {
+      sc->done = 1;
+      sc->status = 4;
+    }
+  }
+}
+
+// ------------------------------------------------------------- the CTA pair
+// For 128 < n <= 256 the pass runs on CTA pairs (clusters of two) with
+// tcgen05.mma.cta_group::2.  A pair owns 256-row tiles of X: CTA rank r holds
+// rows 128 r .. 128 r + 127 of each tile (its half of the A operand) and the
+// N half r of Q (its half of the B operand, loaded once), and its tensor
+// memory receives its 128 rows x all N columns.  Every X tile then crosses
+// from L2 to shared memory once; with one CTA per N half (all that shared
+// memory holds of Q) it crossed twice.  Each CTA's epilogue has 256 columns
+// per tile, so it runs 16 warps, four per TMEM lane quadrant.
+//
+// Rank 0 issues the MMAs.  Each CTA loads its own operands with TMA, and
+// every copy of the pair completes on rank 0's barriers (rank 0 expects the
+// bytes of both; rank 1's copies name rank 0's barrier, the .cta_group::2
+// form).  The MMA completions arrive on both CTAs' barriers (multicast
+// commit); both CTAs' epilogue warps release an accumulator on rank 0's
+// barrier.  These hand-offs order tensor-memory accesses only (tcgen05 fences
+// around a CTA-scope arrive and wait), so the epilogue's global stores never
+// wait for a cluster-scope release.  A wait that runs out sets the failure
+// flag of both CTAs, so the peer stops too.  At the end rank 0 learns how many
+// copies rank 1 issued and waits for every copy of the pair to land, and both
+// CTAs meet at a cluster barrier before freeing the tensor memory.
+constexpr int kFdmPairRows = 2 * kFdmRows;  // rows of X per pair tile
+constexpr int kFdmPairEpiWarps = 16;        // epilogue warps: four per TMEM lane quadrant
+constexpr int kFdmPairThreads = 32 * (2 + kFdmPairEpiWarps);
+constexpr int kFdmPairTmemCols = 512;       // two FP32 accumulators of up to 256 columns
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Shared::cluster address of the same shared variable in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t cluster_addr(const void* p, uint32_t rank) {
+  uint32_t a;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(a) : "r"(smem_addr(p)), "r"(rank));
+  return a;
+}
+
+// Arrive on a barrier of either CTA of the cluster (CTA-scope release).
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_bar) {
+  asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(cluster_bar) : "memory");
+}
+
+// Completes `bytes` of the current phase's transaction count without a copy
+// (accounts for a copy that was expected but never issued).
+__device__ __forceinline__ void mbar_complete_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.complete_tx.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void st_cluster_u32(uint32_t cluster_addr_, uint32_t v) {
+  asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(cluster_addr_), "r"(v) : "memory");
+}
+
+// Bounded wait of the pair kernel: gives up once either CTA has failed, and
+// a wait that runs out marks both CTAs failed.
+__device__ __forceinline__ bool pair_wait(uint64_t* bar, uint32_t parity, volatile int* fail, uint32_t peer_fail) {
+  for (unsigned i = 0; i < kWaitSpins; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 63u) == 63u && *fail) return false;
+  }
+  *fail = 1;
+  st_cluster_u32(peer_fail, 1u);
+  return false;
+}
+
+// Full bound, for draining copies in flight (no early exit on failure).
+__device__ __forceinline__ bool pair_drain(uint64_t* bar, uint32_t parity) {
+  for (unsigned i = 0; i < kWaitSpins; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// 2-D tile load by either CTA of a pair onto a barrier of rank 0 (its
+// shared::cluster address): the copy's bytes complete there.
+__device__ __forceinline__ void tma_load2_pair(void* dst, const CUtensorMap* map, uint32_t cluster_bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], "
+      "[%2];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(cluster_bar), "r"(x), "r"(y)
+      : "memory");
+}
+
+template <typename S>
+__device__ __forceinline__ void fdm_mma2(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  if constexpr (std::is_same<S, float>::value) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+  }
+}
+
+// Arrives once on the barrier at this offset in both CTAs of the pair when
+// the MMAs issued so far have completed.
+__device__ __forceinline__ void fdm_commit2_both(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_addr(bar)),
+      "h"((unsigned short)3)
+      : "memory");
+}
+
+__device__ __forceinline__ void fdm_commit2_own(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
+               : "memory");
+}
+
+// Instruction descriptor of the pair MMA: M = 256 rows (128 per CTA), N = nt.
+template <typename S>
+__host__ __device__ constexpr uint32_t fdm_idesc2(int nt) {
+  constexpr uint32_t fmt = std::is_same<S, float>::value ? 2u : (std::is_same<S, __half>::value ? 0u : 1u);
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(nt >> 3) << 17) | ((uint32_t)(kFdmPairRows >> 4) << 24);
+}
+
+// The pass of fdm_pass on CTA pairs.  fg.nt is the full N (a multiple of 16,
+// <= 256; each CTA holds nt/2 rows of Q), fg.mtiles counts 256-row tiles.
+template <typename S>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFdmPairThreads, 1)
+    fdm_pass_pair(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CUtensorMap tm_q, FdmGeo fg,
+                  int mode, float c, const float* __restrict__ mu, S* __restrict__ out, const S* __restrict__ rdot,
+                  int cg, CgScalars* sc, double* partials) {
+  extern __shared__ unsigned char fdm_smem_raw[];
+  unsigned char* sm = fdm_smem_raw + ((1024u - (smem_addr(fdm_smem_raw) & 1023u)) & 1023u);
+  const int nh = fg.nt / 2;  // Q rows (N columns) held by each CTA
+  const uint32_t qbytes = (uint32_t)fg.kblocks * nh * 128;
+  unsigned char* sQ = sm;
+  unsigned char* sX = sm + qbytes;
+  const int NS = fg.stages;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sX + (size_t)NS * kFdmStageBytes);
+  uint64_t* landed = bars;                       // [NS] rank 0: the stage of both CTAs landed
+  uint64_t* empty = bars + kFdmMaxStages;        // [NS] stage consumed by the pair's MMAs (both CTAs)
+  uint64_t* qlanded = bars + 2 * kFdmMaxStages;  // rank 0: both Q halves landed
+  uint64_t* accfull = qlanded + 1;               // [2] accumulator ready (both CTAs)
+  uint64_t* accempty = qlanded + 3;              // [2] rank 0: accumulator drained by both CTAs
+  uint64_t* mmadone = qlanded + 5;               // rank 0: every MMA finished
+  uint32_t* tholder = reinterpret_cast<uint32_t*>(qlanded + 6);
+  volatile int* fail = reinterpret_cast<volatile int*>(tholder + 1);
+  volatile int* skip = reinterpret_cast<volatile int*>(tholder + 2);
+  volatile uint32_t* peer_issued = reinterpret_cast<volatile uint32_t*>(tholder + 3);  // rank 0: rank 1's copies
+
+  const uint32_t rank = cluster_rank();
+  const uint32_t peer = rank ^ 1u;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int pair_id = (int)(blockIdx.x >> 1), npairs = (int)(gridDim.x >> 1);
+  const int total = fg.mtiles;
+  constexpr int KB = 128 / (int)sizeof(S);
+  const uint32_t peer_fail = cluster_addr((const void*)fail, peer);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(&landed[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(qlanded, 1);
+    mbar_init(&accfull[0], 1);
+    mbar_init(&accfull[1], 1);
+    mbar_init(&accempty[0], 2 * kFdmPairEpiWarps);
+    mbar_init(&accempty[1], 2 * kFdmPairEpiWarps);
+    mbar_init(mmadone, 1);
+    *fail = 0;
+    mbar_fence_init();
+  }
+  cluster_sync();  // both CTAs running, barriers initialised: remote access is safe from here
+  if (threadIdx.x == 0 && rank == 0) {  // one decision for the pair: both CTAs return, or neither
+    const uint32_t v = (cg && sc->done) ? 1u : 0u;
+    *skip = (int)v;
+    st_cluster_u32(cluster_addr((const void*)skip, 1u), v);
+  }
+  cluster_sync();
+  if (*skip) return;
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tholder)),
+                 "r"(kFdmPairTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    tc_fence_before();
+  }
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = *tholder;
+
+  float dot = 0.f;
+  uint32_t issued = 0;  // X copies issued by this CTA's producer
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---- TMA producer (both CTAs): own Q half once, own 128 rows of each
+      // tile; the bytes of both CTAs complete on rank 0's barriers
+      const uint32_t qbar = cluster_addr(qlanded, 0u);
+      if (rank == 0) mbar_expect_tx(qlanded, 2u * qbytes);
+      for (int kb = 0; kb < fg.kblocks; ++kb)
+        tma_load2_pair(sQ + (size_t)kb * nh * 128, &tm_q, qbar, kb * KB, (int)rank * nh);
+      bool ok = true;
+      for (int t = pair_id; t < total && ok; t += npairs) {
+        for (int kb = 0; kb < fg.kblocks; ++kb, ++issued) {
+          const int s = (int)(issued % NS);
+          if (!pair_wait(&empty[s], ((issued / NS) & 1u) ^ 1u, fail, peer_fail) || *fail) {
+            ok = false;
+            break;
+          }
+          if (rank == 0) mbar_expect_tx(&landed[s], 2u * kFdmStageBytes);
+          tma_load2_pair(sX + (size_t)s * kFdmStageBytes, &tm_in, cluster_addr(&landed[s], 0u), kb * KB,
+                         t * kFdmPairRows + (int)rank * kFdmRows);
+        }
+      }
+      if (rank == 1) st_cluster_u32(cluster_addr((const void*)peer_issued, 0u), issued);
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && rank == 0) {
+      // ---- MMA issuer (rank 0): both CTAs' stages, pair MMAs, multicast commits
+      const uint32_t idesc = fdm_idesc2<S>(fg.nt);
+      bool ok = pair_wait(qlanded, 0, fail, peer_fail);
+      tc_fence_after();
+      const uint32_t q0 = smem_addr(sQ), x0 = smem_addr(sX);
+      uint32_t it = 0, lt = 0;
+      for (int t = pair_id; t < total && ok; t += npairs, ++lt) {
+        const uint32_t acc = lt & 1u;
+        if (!pair_wait(&accempty[acc], ((lt >> 1) & 1u) ^ 1u, fail, peer_fail)) break;
+        tc_fence_after();
+        const uint32_t d = tbase + acc * 256u;
+        for (int kb = 0; kb < fg.kblocks; ++kb, ++it) {
+          const int s = (int)(it % NS);
+          if (!pair_wait(&landed[s], (it / NS) & 1u, fail, peer_fail)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint64_t ad = fdm_desc(x0 + (uint32_t)s * kFdmStageBytes);
+          const uint64_t bd = fdm_desc(q0 + (uint32_t)kb * nh * 128u);
+#pragma unroll
+          for (int k = 0; k < 4; ++k)  // 32 bytes of K per instruction
+            fdm_mma2<S>(d, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), idesc, (kb | k) != 0);
+          fdm_commit2_both(&empty[s]);
+        }
+        if (ok) fdm_commit2_both(&accfull[acc]);
+      }
+      // all MMAs issued by this thread complete before the commit below arrives
+      fdm_commit2_own(mmadone);
+      (void)pair_drain(mmadone, 0);
+    }
+  } else {
+    // ---- epilogue (both CTAs): warp w owns TMEM lane quadrant w % 4 and every
+    // second 16-column chunk, starting at (w - 2) / 4
+    const int quad = warp & 3;
+    const int part = (warp - 2) >> 2;  // 0..3
+    const int row = quad * 32 + lane;
+    const uint32_t release0 = cluster_addr(&accempty[0], 0u), release1 = cluster_addr(&accempty[1], 0u);
+    float dacc[4] = {0.f, 0.f, 0.f, 0.f};
+    uint32_t lt = 0;
+    for (int t = pair_id; t < total; t += npairs, ++lt) {
+      const uint32_t acc = lt & 1u;
+      if (!__all_sync(0xffffffffu, pair_wait(&accfull[acc], (lt >> 1) & 1u, fail, peer_fail))) break;
+      tc_fence_after();
+      const int m = t * kFdmPairRows + (int)rank * kFdmRows + row;
+      const bool mrow = m < fg.rows;
+      float cab = 0.f;
+      if (mode == kFdmScale && mrow) cab = fmaf(c, mu[m / fg.n] + mu[m % fg.n], 1.0f);
+      for (int c0 = 16 * part; c0 < fg.nt; c0 += 64) {
+        float rv[16];
+        if (mode == kFdmDot) {
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj) {
+            const int j = c0 + jj;
+            rv[jj] = (mrow && j < fg.n) ? wid<float>(rdot[(size_t)j * fg.rows + m]) : 0.f;
+          }
+        }
+        float v[16];
+        tmem_ld16(tbase + ((uint32_t)(quad * 32) << 16) + acc * 256u + (uint32_t)c0, v);
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) {
+          const int j = c0 + jj;
+          if (mrow && j < fg.n) {
+            float y = v[jj];
+            if (mode == kFdmScale) y = __fdividef(y, fmaf(c, mu[j], cab));
+            const S ys = nar<S>(y);
+            out[(size_t)j * fg.rows + m] = ys;
+            if (mode == kFdmDot) dacc[jj & 3] = fmaf(rv[jj], wid<float>(ys), dacc[jj & 3]);
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive_remote(acc ? release1 : release0);
+    }
+    dot = (dacc[0] + dacc[1]) + (dacc[2] + dacc[3]);
+  }
+  __syncthreads();
+  cluster_sync();  // both producers done; rank 1's copy count visible to rank 0
+  if (rank == 0 && warp == 0 && lane == 0) {
+    // every copy of the pair lands before either CTA exits.  Stage s's last
+    // phases: rank 0 expected both CTAs' bytes for its own copies; a copy one
+    // CTA issued and the other did not (after a failure) is balanced here.
+    (void)pair_drain(qlanded, 0);
+    const uint32_t i0 = issued, i1 = *peer_issued;
+    const uint32_t hi = i0 > i1 ? i0 : i1;
+    for (uint32_t jj = hi > (uint32_t)NS ? hi - NS : 0u; jj < hi; ++jj) {
+      uint64_t* bar = &landed[jj % NS];
+      const bool e0 = jj < i0, e1 = jj < i1;
+      if (e0 && !e1) mbar_complete_tx(bar, kFdmStageBytes);  // rank 1's share never comes
+      if (!e0 && e1) mbar_expect_tx(bar, kFdmStageBytes);    // only rank 1's share comes
+      (void)pair_drain(bar, (jj / NS) & 1u);
+    }
+  }
+  __syncthreads();
+  // no copy, remote arrive, multicast commit or flag store targets either CTA after this
+  cluster_sync();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(kFdmPairTmemCols)
+                 : "memory");
   }
   const bool failed = *fail != 0;
   if (failed && threadIdx.x == 0) {

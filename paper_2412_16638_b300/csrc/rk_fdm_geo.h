@@ -7,10 +7,11 @@ namespace rk {
 struct FdmGeo {
   int n;        // nodes per direction
   int rows;     // n*n
-  int nt;       // columns per N tile: multiple of 16, <= 128
-  int ntiles;   // N tiles (1 or 2); the grid is a multiple of ntiles
+  int nt;       // columns per N tile: multiple of 16, <= 128 (pair: the full N, <= 256)
+  int ntiles;   // N tiles (1 or 2); the grid is a multiple of ntiles (pair: 1)
   int kblocks;  // 128-byte K blocks: ceil(n * sizeof(S) / 128)
-  int mtiles;   // ceil(rows / 128)
+  int mtiles;   // ceil(rows / 128) (pair: ceil(rows / 256))
+  int pair;     // 1: fdm_pass_pair on CTA pairs (n > 128)
   int stages;   // X stages in the TMA ring (as many as shared memory holds, <= 6)
 };
 
