@@ -2,7 +2,9 @@
 // block-Jacobi with per-block inverses, and the GMRES(m) driver.
 #include <algorithm>
 #include <cmath>
+#include <map>
 #include <utility>
+#include <vector>
 
 #include "rk_cfdm.cuh"
 #include "rk_csr.cuh"
@@ -49,6 +51,9 @@ struct GmresWork {
   void* z = nullptr;          // preconditioned vector
   int* scol = nullptr;        // sliced-ELL copy of L: columns (ldv * kSellW) ...
   void* sval = nullptr;       // ... and values lscale * L in the storage type
+  unsigned* smask = nullptr;  // per 32-row slice: slots whose columns follow `pat`
+  SellPattern pat{};          // the operator's column offsets by slot
+  double scol_bytes = 0.0;    // column bytes the product still loads (irregular slots + masks)
   long long ldv = 0;          // leading dimension: N rounded up to a whole tile
   // complex fast diagonalization (periodic advection): twiddles, two complex
   // work arrays, one real work vector in the storage type
@@ -228,14 +233,40 @@ rk_status csr_setup(rk_problem* p) {
     RK_TRY(alloc_dev(p, &w->z, (size_t)p->N * s));
     RK_TRY(alloc_dev(p, (void**)&w->scol, (size_t)w->ldv * kSellW * sizeof(int)));
     RK_TRY(alloc_dev(p, &w->sval, (size_t)w->ldv * kSellW * s));
+    const long long nslices = w->ldv / 32;
+    RK_TRY(alloc_dev(p, (void**)&w->smask, (size_t)nslices * sizeof(unsigned)));
+    {
+      // the kSellW most common column offsets, ascending
+      std::map<long long, long long> hist;
+      for (size_t r = 0; r + 1 < rowptr.size(); ++r)
+        for (int e = rowptr[r]; e < rowptr[r + 1]; ++e) ++hist[(long long)cols[e] - (long long)r];
+      std::vector<std::pair<long long, long long>> byc(hist.begin(), hist.end());
+      std::stable_sort(byc.begin(), byc.end(), [](const auto& a, const auto& b) { return a.second > b.second; });
+      std::vector<long long> ds;
+      for (size_t i = 0; i < byc.size() && (int)ds.size() < kSellW; ++i) ds.push_back(byc[i].first);
+      while ((int)ds.size() < kSellW) ds.push_back(0);
+      std::sort(ds.begin(), ds.end());
+      for (int k = 0; k < kSellW; ++k) w->pat.d[k] = (int)ds[k];
+    }
     dispatch_st(p->sol.storage, [&](auto ts, auto) {
       using S = typename decltype(ts)::type;
       auto kern = sell_from_csr<S>;
       kern<<<grid_for((const void*)kern, w->ldv), kThreads, 0, p->st>>>(
-          CsrView{c.rowptr, c.cols}, c.v64, c.lscale, p->N, w->ldv, w->scol, static_cast<S*>(w->sval));
+          CsrView{c.rowptr, c.cols}, c.v64, c.lscale, p->N, w->ldv, w->pat, w->scol, static_cast<S*>(w->sval));
       if (cudaGetLastError() != cudaSuccess) st = RK_ERR_CUDA;
     });
     RK_TRY(st);
+    {
+      auto km = sell_mask;
+      km<<<grid_for((const void*)km, nslices), kThreads, 0, p->st>>>(w->scol, nslices, w->pat, w->smask);
+      RK_CUDA(cudaGetLastError());
+      std::vector<unsigned> hm((size_t)nslices);
+      RK_CUDA(cudaMemcpyAsync(hm.data(), w->smask, hm.size() * sizeof(unsigned), cudaMemcpyDeviceToHost, p->st));
+      RK_CUDA(cudaStreamSynchronize(p->st));
+      long long loaded = 0;  // (slice, slot) pairs whose columns are still loaded
+      for (unsigned m : hm) loaded += kSellW - __builtin_popcount(m & ((1u << kSellW) - 1u));
+      w->scol_bytes = (double)loaded * 32.0 * sizeof(int) + (double)nslices * sizeof(unsigned);
+    }
     const int seg = gm_seg(p->sol.storage, p->sol.bj_block);
     const long long nsegs = (long long)p->n * p->n * ((p->n + seg - 1) / seg);
     const long long ctas = (nsegs + kThreads - 1) / kThreads;
@@ -283,6 +314,7 @@ rk_status csr_free(rk_problem* p) {
     if (w->wbuf) free_dev(p, w->wbuf);
     if (w->z) free_dev(p, w->z);
     if (w->scol) free_dev(p, w->scol);
+    if (w->smask) free_dev(p, w->smask);
     if (w->sval) free_dev(p, w->sval);
     if (w->cf_tw) free_dev(p, w->cf_tw);
     if (w->cf_c[0]) free_dev(p, w->cf_c[0]);
@@ -574,7 +606,8 @@ rk_status gmres_solve(rk_problem* p, double shift, const double* g64, RhsScalars
       const double Ns = (double)p->N * sizeof(S), Nx = (double)p->N * sizeof(X);
       const double Nb = (double)p->N * sizeof(B);
       const double mat = (double)p->csr.nnz * (4.0 + sizeof(S)) + 4.0 * (p->N + 1);
-      const double sell = (double)p->N * kSellW * (4.0 + sizeof(S));
+      // the slot values, plus the columns of the slots off the pattern
+      const double sell = (double)p->N * kSellW * sizeof(S) + w->scol_bytes;
       // block inverses read per apply: BS entries per row, FP16 for the
       // adaptively stored blocks, plus one flag byte per block
       const double fhalf = p->bj_blocks > 0 ? (double)p->bj_half_blocks / (double)p->bj_blocks : 0.0;
@@ -638,8 +671,8 @@ rk_status gmres_solve(rk_problem* p, double shift, const double* g64, RhsScalars
             prof_end(p);
           }
           prof_begin(p, K_GM_ARNOLDI, sell + Ns + Nb + (jb + 1.0) * Nb, solve, idx);
-          k_arn<<<ga, kGmThreads, smem, p->st>>>(w->scol, static_cast<const S*>(w->sval), cs, z, V, ldv, wb,
-                                                  p->N, w->sc, w->partials);
+          k_arn<<<ga, kGmThreads, smem, p->st>>>(w->scol, w->smask, w->pat, static_cast<const S*>(w->sval), cs, z, V,
+                                                 ldv, wb, p->N, w->sc, w->partials);
           prof_end(p);
           prof_begin(p, K_GM_ORTH, (jb + 2.0) * Nb + 2.0 * Nb, solve, idx);
           k_upd_basis<<<gu, kGmThreads, smem, p->st>>>(V, ldv, wb, p->N, w->sc);

@@ -45,22 +45,75 @@ __device__ __forceinline__ long long sell_index(long long r, int k) {
   return (((r >> 5) * kSellW + k) << 5) + (r & 31);
 }
 
+// The operator's column offsets (col - row) by slot: the kSellW most common
+// offsets of the matrix, ascending (a 7-point stencil: -n^2, -n, -1, 0, 1,
+// n, n^2).
+struct SellPattern {
+  int d[kSellW];
+};
+
 // Build the sliced-ELL copy (values * lscale rounded to S) from the CSR
-// operator; one thread per row.
+// operator; one thread per row.  An entry whose offset is pat.d[k] goes to
+// slot k; entries with other offsets (periodic wrap-around) fill the slots
+// left free, in order.  A slot still free holds the value 0 with column
+// r + pat.d[k] when that is a row of the matrix (else r), so that the slot
+// stays on the pattern: multiplying the zero by that entry of z adds nothing
+// for finite z.
 template <typename S>
 __global__ void __launch_bounds__(kThreads) sell_from_csr(CsrView A, const double* __restrict__ vals, double scale,
-                                                          long long N, long long Npad, int* __restrict__ scol,
-                                                          S* __restrict__ sval) {
+                                                          long long N, long long Npad, SellPattern pat,
+                                                          int* __restrict__ scol, S* __restrict__ sval) {
   for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < Npad;
        r += (long long)gridDim.x * blockDim.x) {
     const int e0 = r < N ? A.rowptr[r] : 0, e1 = r < N ? A.rowptr[r + 1] : 0;
+    int slot_e[kSellW];
+    unsigned used = 0u;  // entries placed (bit e - e0)
 #pragma unroll
     for (int k = 0; k < kSellW; ++k) {
-      const int e = e0 + k;
-      const bool has = e < e1;
-      scol[sell_index(r, k)] = has ? A.cols[e] : (int)(r < N ? r : 0);
-      sval[sell_index(r, k)] = nar<S>(has ? vals[e] * scale : 0.0);
+      slot_e[k] = -1;
+      for (int e = e0; e < e1; ++e)
+        if (!((used >> (e - e0)) & 1u) && (long long)A.cols[e] - r == pat.d[k]) {
+          slot_e[k] = e;
+          used |= 1u << (e - e0);
+          break;
+        }
     }
+    for (int e = e0; e < e1; ++e) {
+      if ((used >> (e - e0)) & 1u) continue;
+      for (int k = 0; k < kSellW; ++k)
+        if (slot_e[k] < 0) {
+          slot_e[k] = e;
+          used |= 1u << (e - e0);
+          break;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kSellW; ++k) {
+      const int e = slot_e[k];
+      const long long on = r + pat.d[k];
+      scol[sell_index(r, k)] = e >= 0 ? A.cols[e] : (int)((on >= 0 && on < N) ? on : (r < N ? r : 0));
+      sval[sell_index(r, k)] = nar<S>(e >= 0 ? vals[e] * scale : 0.0);
+    }
+  }
+}
+
+// Bit k of mask[slice] is set when every row r of the 32-row slice has its
+// slot-k column at r + pat.d[k]: the product then forms that column instead
+// of loading it.  One thread per slice.
+__global__ void __launch_bounds__(kThreads) sell_mask(const int* __restrict__ scol, long long nslices, SellPattern pat,
+                                                      unsigned* __restrict__ mask) {
+  for (long long sl = (long long)blockIdx.x * blockDim.x + threadIdx.x; sl < nslices;
+       sl += (long long)gridDim.x * blockDim.x) {
+    unsigned m = 0u;
+    for (int k = 0; k < kSellW; ++k) {
+      bool all = true;
+      for (int i = 0; i < 32 && all; ++i) {
+        const long long r = sl * 32 + i;
+        all = (long long)scol[sell_index(r, k)] == r + pat.d[k];
+      }
+      if (all) m |= 1u << k;
+    }
+    mask[sl] = m;
   }
 }
 
@@ -298,13 +351,15 @@ __host__ __device__ constexpr size_t gm_dc_smem() {
 }
 
 // Step j, part 2: w = (I - shift L) z on the sliced-ELL copy (values Lhat =
-// lscale L in S, cs = shift / lscale), stored to wbuf in the basis type; the
+// lscale L in S, cs = shift / lscale; a column is formed from the pattern
+// where the slice's mask bit is set, else loaded), stored to wbuf in the basis type; the
 // dots s_i, t_i (i < j), u_j.u_j, u_j.w with the basis tiles streamed through
 // the ring (u_j first, then v_0 .. v_{j-1}); one grid reduction, then
 // gm_dc_finish in the last CTA.  With j = m (the cycle's last column) only
 // the dots of u_m are formed (no product).  Persistent grid over tiles.
 template <typename S, typename B, typename T>
 __global__ void __launch_bounds__(kGmThreads, sizeof(T) == 4 ? 3 : 2) gm_dc_arnoldi(const int* __restrict__ scol,
+                                                               const unsigned* __restrict__ smask, SellPattern pat,
                                                                const S* __restrict__ sval, T cs,
                                                                const S* __restrict__ z, B* __restrict__ V,
                                                                long long ldv, B* __restrict__ wbuf, long long N,
@@ -353,9 +408,10 @@ __global__ void __launch_bounds__(kGmThreads, sizeof(T) == 4 ? 3 : 2) gm_dc_arno
 #pragma unroll
         for (int e = 0; e < kGmSpmvRows; ++e) {
           const long long r = r0 + (long long)(h + e) * kGmThreads + tid;
+          const unsigned msk = smask[r >> 5];  // one slice per warp: a broadcast load
 #pragma unroll
           for (int k = 0; k < kSellW; ++k) {
-            c[e][k] = scol[sell_index(r, k)];
+            c[e][k] = ((msk >> k) & 1u) ? (int)r + pat.d[k] : scol[sell_index(r, k)];
             a[e][k] = wid<T>(sval[sell_index(r, k)]);
           }
         }
