@@ -19,6 +19,8 @@
 // the exponent mod n.
 // Arithmetic in T (FP32 for FP32 storage, FP64 for the FP64 path).
 #pragma once
+#include <type_traits>
+
 #include "rk_csr.cuh"
 
 namespace rk {
@@ -250,6 +252,228 @@ __global__ void __launch_bounds__(kCfThreads) cfdm_pass(const void* __restrict__
     }
   }
 }
+
+// ------------------------------------------------ compile-time small DFTs
+// For the grid sizes below, n = N1 N2 is a template parameter and every small
+// transform is written out at compile time: mixed-radix Cooley-Tukey down to
+// sizes 2 and odd primes, the twiddles as constants (cos and sin of 2 pi m / N
+// by Taylor series at compile time), multiplications by +-1 and +-i turned
+// into adds, and the odd-prime sizes through the symmetric pairs x_j +- x_{N-j}
+// (outputs k and N - k share their products).  No twiddle table is read and
+// no index is formed at run time inside a small transform.
+
+// cos / sin of 2 pi m / N (0 <= m < N), for compile-time twiddles.
+constexpr double cf_series_sin(double x) {
+  double t = x, s = x;
+  for (int i = 1; i < 30; ++i) {
+    t *= -x * x / ((2.0 * i) * (2.0 * i + 1.0));
+    s += t;
+  }
+  return s;
+}
+constexpr double cf_series_cos(double x) {
+  double t = 1.0, s = 1.0;
+  for (int i = 1; i < 30; ++i) {
+    t *= -x * x / ((2.0 * i - 1.0) * (2.0 * i));
+    s += t;
+  }
+  return s;
+}
+constexpr double cf_angle(int m, int N) {  // 2 pi m / N reduced to [-pi, pi]
+  const double pi = 3.14159265358979323846;
+  return (2 * m > N ? 2.0 * pi * (m - N) : 2.0 * pi * m) / N;
+}
+constexpr double cf_cos(int m, int N) { return cf_series_cos(cf_angle(m, N)); }
+constexpr double cf_sin(int m, int N) { return cf_series_sin(cf_angle(m, N)); }
+
+constexpr int cf_small_factor(int N) {
+  for (int p = 2; p * p <= N; ++p)
+    if (N % p == 0) return p;
+  return N;
+}
+
+template <int I, int E, typename F>
+__device__ __forceinline__ void cf_for(F&& f) {
+  if constexpr (I < E) {
+    f(std::integral_constant<int, I>{});
+    cf_for<I + 1, E>(f);
+  }
+}
+
+// x * e^{-2 pi i M / N}
+template <typename T, int N, int M>
+__device__ __forceinline__ Cplx<T> cf_twiddle(Cplx<T> x) {
+  constexpr int m = M % N;
+  if constexpr (m == 0) {
+    return x;
+  } else if constexpr (2 * m == N) {
+    return Cplx<T>{-x.re, -x.im};
+  } else if constexpr (4 * m == N) {
+    return Cplx<T>{x.im, -x.re};
+  } else if constexpr (4 * m == 3 * N) {
+    return Cplx<T>{-x.im, x.re};
+  } else {
+    constexpr double c = cf_cos(m, N), sn = -cf_sin(m, N);  // w = c + i sn
+    return Cplx<T>{fma(x.re, (T)c, -x.im * (T)sn), fma(x.re, (T)sn, x.im * (T)c)};
+  }
+}
+
+// In place: x[k] <- sum_j x[j] e^{-2 pi i j k / N}.
+template <typename T, int N>
+__device__ __forceinline__ void cf_dft(Cplx<T> (&x)[N]) {
+  if constexpr (N == 1) {
+    return;
+  } else if constexpr (N == 2) {
+    const Cplx<T> a = x[0], b = x[1];
+    x[0] = Cplx<T>{a.re + b.re, a.im + b.im};
+    x[1] = Cplx<T>{a.re - b.re, a.im - b.im};
+  } else if constexpr (cf_small_factor(N) == N) {
+    // odd prime: s_j = x_j + x_{N-j}, d_j = x_j - x_{N-j} (j = 1 .. H);
+    // y_k = x_0 + sum_j s_j cos(2 pi j k / N) - i d_j sin(2 pi j k / N), and
+    // y_{N-k} the same with the sine terms negated
+    constexpr int H = (N - 1) / 2;
+    Cplx<T> sv[H], dv[H];
+    Cplx<T> y0 = x[0];
+    cf_for<1, H + 1>([&](auto jc) {
+      constexpr int J = decltype(jc)::value;
+      sv[J - 1] = Cplx<T>{x[J].re + x[N - J].re, x[J].im + x[N - J].im};
+      dv[J - 1] = Cplx<T>{x[J].re - x[N - J].re, x[J].im - x[N - J].im};
+      y0.re += sv[J - 1].re;
+      y0.im += sv[J - 1].im;
+    });
+    Cplx<T> out[N];
+    out[0] = y0;
+    cf_for<1, H + 1>([&](auto kc) {
+      constexpr int K = decltype(kc)::value;
+      T are = x[0].re, aim = x[0].im, bre = T(0), bim = T(0);
+      cf_for<1, H + 1>([&](auto jc) {
+        constexpr int J = decltype(jc)::value;
+        constexpr double c = cf_cos((J * K) % N, N), sn = cf_sin((J * K) % N, N);
+        are = fma(sv[J - 1].re, (T)c, are);
+        aim = fma(sv[J - 1].im, (T)c, aim);
+        bre = fma(dv[J - 1].im, (T)sn, bre);
+        bim = fma(dv[J - 1].re, (T)sn, bim);
+      });
+      out[K] = Cplx<T>{are + bre, aim - bim};
+      out[N - K] = Cplx<T>{are - bre, aim + bim};
+    });
+    cf_for<0, N>([&](auto kc) { x[decltype(kc)::value] = out[decltype(kc)::value]; });
+  } else {
+    // N = P Q: j = Q j1 + j2, k = k1 + P k2
+    constexpr int P = cf_small_factor(N), Q = N / P;
+    Cplx<T> a[Q][P];
+    cf_for<0, Q>([&](auto j2c) {
+      constexpr int J2 = decltype(j2c)::value;
+      Cplx<T> v[P];
+      cf_for<0, P>([&](auto j1c) { v[decltype(j1c)::value] = x[Q * decltype(j1c)::value + J2]; });
+      cf_dft<T, P>(v);
+      cf_for<0, P>([&](auto k1c) {
+        constexpr int K1 = decltype(k1c)::value;
+        a[J2][K1] = cf_twiddle<T, N, J2 * K1>(v[K1]);
+      });
+    });
+    cf_for<0, P>([&](auto k1c) {
+      constexpr int K1 = decltype(k1c)::value;
+      Cplx<T> v[Q];
+      cf_for<0, Q>([&](auto j2c) { v[decltype(j2c)::value] = a[decltype(j2c)::value][K1]; });
+      cf_dft<T, Q>(v);
+      cf_for<0, Q>([&](auto k2c) { x[K1 + P * decltype(k2c)::value] = v[decltype(k2c)::value]; });
+    });
+  }
+}
+
+// The pass of cfdm_pass for n = N1 N2 known at compile time, 32 N1 threads
+// (warp w, lane = line bb of the tile).  Step 1: task j2 (warps in turn)
+// transforms x[N2 j1 + j2] over j1 with cf_dft<N1>, multiplies by w^{j2 k1}
+// (table, j2 varies at run time) and writes back in place; step 2: warp k1
+// transforms A[k1][.] with cf_dft<N2> and emits X[k1 + N1 k2].  The inverse
+// transform is conj(F conj(x)).
+template <typename SI, typename SO, typename T, bool IN_REAL, bool OUT_REAL, int N1, int N2>
+__global__ void __launch_bounds__(32 * N1) cfdm_pass_ct(const void* __restrict__ in, void* __restrict__ out,
+                                                        const Cplx<T>* __restrict__ tw, int inverse, int scale,
+                                                        CfScale sp, const GmScalars* sc, long long in_jstride) {
+  constexpr int n = N1 * N2;
+  if (sc && (sc->done || sc->cycle_end || sc->j >= sc->m)) return;
+  if (sc && in_jstride > 0) in = static_cast<const SI*>(in) + (long long)sc->j * in_jstride;
+  extern __shared__ __align__(128) unsigned char smem[];
+  using C = Cplx<T>;
+  C* tile = reinterpret_cast<C*>(smem);       // [kCfTile][n + 1]
+  C* tws = tile + (size_t)kCfTile * (n + 1);  // [n], forward twiddles
+  constexpr int nbt = (n + kCfTile - 1) / kCfTile;
+  const int a = blockIdx.x / nbt;
+  const int b0 = (blockIdx.x % nbt) * kCfTile;
+  const int tb = min(kCfTile, n - b0);
+  const T cj = inverse ? T(-1) : T(1);  // conjugation of the inverse transform
+  for (int m = threadIdx.x; m < n; m += blockDim.x) tws[m] = tw[m];
+  for (int e = threadIdx.x; e < tb * n; e += blockDim.x) {
+    const int bb = e / n, j = e - bb * n;
+    const long long gi = ((long long)a * n + b0 + bb) * n + j;
+    C v;
+    if constexpr (IN_REAL) {
+      v.re = wid<T>(static_cast<const SI*>(in)[gi]);
+      v.im = T(0);
+    } else {
+      v = static_cast<const C*>(in)[gi];
+      v.im *= cj;
+    }
+    tile[(size_t)bb * (n + 1) + j] = v;
+  }
+  __syncthreads();
+  const int bb = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  C* row = tile + (size_t)bb * (n + 1);
+  if (bb < tb) {
+    for (int j2 = warp; j2 < N2; j2 += N1) {
+      C x[N1];
+      cf_for<0, N1>([&](auto j1c) { x[decltype(j1c)::value] = row[N2 * decltype(j1c)::value + j2]; });
+      cf_dft<T, N1>(x);
+      cf_for<0, N1>([&](auto k1c) {
+        constexpr int K1 = decltype(k1c)::value;
+        C v = x[K1];
+        if constexpr (K1 > 0) {
+          const C t = tws[j2 * K1];
+          v = C{fma(x[K1].re, t.re, -x[K1].im * t.im), fma(x[K1].re, t.im, x[K1].im * t.re)};
+        }
+        row[N2 * K1 + j2] = v;
+      });
+    }
+  }
+  __syncthreads();
+  if (bb >= tb) return;
+  const int k1 = warp;  // N1 warps: one task each
+  C y[N2];
+  cf_for<0, N2>([&](auto j2c) { y[decltype(j2c)::value] = row[N2 * k1 + decltype(j2c)::value]; });
+  cf_dft<T, N2>(y);
+  cf_for<0, N2>([&](auto k2c) {
+    constexpr int K2 = decltype(k2c)::value;
+    const int k = k1 + N1 * K2;
+    T r = y[K2].re, i = y[K2].im * cj;
+    if (scale) {
+      const int kx = b0 + bb;
+      const T th = ((T)sp.beta[0] * (-tws[kx].im) + (T)sp.beta[1] * (-tws[a].im) + (T)sp.beta[2] * (-tws[k].im)) *
+                   (T)sp.inv_h;
+      const T c = (T)sp.s * th;
+      const T den = (T)sp.norm / fma(c, c, T(1));
+      const T r2 = fma(i, c, r) * den, i2 = fma(-r, c, i) * den;
+      r = r2;
+      i = i2;
+    }
+    const long long go = ((long long)k * n + a) * n + b0 + bb;
+    if constexpr (OUT_REAL) {
+      static_cast<SO*>(out)[go] = nar<SO>(r);
+    } else {
+      C v;
+      v.re = r;
+      v.im = i;
+      static_cast<C*>(out)[go] = v;
+    }
+  });
+}
+
+// Grid sizes with a compile-time pass (FP32 and FP64 paths): n -> (N1, N2) =
+// 200 -> (10, 20), 64 -> (8, 8), 32 -> (4, 8), 20 -> (4, 5), the factors of
+// cfdm_factor.
+__host__ __device__ constexpr bool cfdm_has_ct(int n) { return n == 200 || n == 64 || n == 32 || n == 20; }
 
 // u = sum_{i < jused} y_i V_i (the cycle-end combination of the basis,
 // before the preconditioner is applied to it), stored in S.

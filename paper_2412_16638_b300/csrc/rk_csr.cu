@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cmath>
 #include <map>
+#include <mutex>
 #include <utility>
 #include <vector>
 
@@ -363,6 +364,58 @@ rk_status csr_correct_f64(rk_problem* p, double shift, const double* gv, const v
   return st;
 }
 
+// The six passes with the compile-time kernel for n = N1 N2 (rk_cfdm.cuh).
+template <typename SI, typename S, typename T, int N1, int N2>
+static rk_status cfdm_apply_ct(rk_problem* p, const SI* in, long long in_jstride, S* out, const GmScalars* sc,
+                               int solve, int idx, const Cplx<T>* tw, const CfScale& sp) {
+  constexpr int n = N1 * N2;
+  using C = Cplx<T>;
+  GmresWork* w = p->gw;
+  const int grid = n * ((n + kCfTile - 1) / kCfTile);
+  const size_t smem = (size_t)kCfTile * (n + 1) * sizeof(C) + (size_t)n * sizeof(C);
+  auto k_first = cfdm_pass_ct<SI, S, T, true, false, N1, N2>;
+  auto k_mid = cfdm_pass_ct<SI, S, T, false, false, N1, N2>;
+  auto k_last = cfdm_pass_ct<SI, S, T, false, true, N1, N2>;
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [&] {
+    for (const void* k : {(const void*)k_first, (const void*)k_mid, (const void*)k_last})
+      if (attr == cudaSuccess) attr = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaGetLastError();
+  });
+  if (attr != cudaSuccess) {
+    set_error("periodic fast diagonalization: shared-memory attribute refused");
+    return RK_ERR_CUDA;
+  }
+  constexpr int threads = 32 * N1;
+  const double Nc = (double)p->N * sizeof(C);
+  void* c0 = w->cf_c[0];
+  void* c1 = w->cf_c[1];
+  prof_begin(p, K_CFDM, (double)p->N * sizeof(SI) + Nc, solve, idx);
+  k_first<<<grid, threads, smem, p->st>>>(in, c0, tw, 0, 0, sp, sc, in_jstride);
+  prof_end(p);
+  prof_begin(p, K_CFDM, 2.0 * Nc, solve, idx);
+  k_mid<<<grid, threads, smem, p->st>>>(c0, c1, tw, 0, 0, sp, sc, 0);
+  prof_end(p);
+  prof_begin(p, K_CFDM, 2.0 * Nc, solve, idx);
+  k_mid<<<grid, threads, smem, p->st>>>(c1, c0, tw, 0, 1, sp, sc, 0);
+  prof_end(p);
+  prof_begin(p, K_CFDM, 2.0 * Nc, solve, idx);
+  k_mid<<<grid, threads, smem, p->st>>>(c0, c1, tw, 1, 0, sp, sc, 0);
+  prof_end(p);
+  prof_begin(p, K_CFDM, 2.0 * Nc, solve, idx);
+  k_mid<<<grid, threads, smem, p->st>>>(c1, c0, tw, 1, 0, sp, sc, 0);
+  prof_end(p);
+  prof_begin(p, K_CFDM, Nc + (double)p->N * sizeof(S), solve, idx);
+  k_last<<<grid, threads, smem, p->st>>>(c0, out, tw, 1, 0, sp, sc, 0);
+  prof_end(p);
+  if (cudaGetLastError() != cudaSuccess) {
+    set_error("periodic fast-diagonalization launch failed");
+    return RK_ERR_CUDA;
+  }
+  return RK_OK;
+}
+
 // z = P^-1 u for the periodic advection stage matrix by the six complex
 // passes (rk_cfdm.cuh).  u: basis slot sc->j when sc != null (a GMRES step,
 // skipped on the device when none is due), else the vector `in`.
@@ -400,6 +453,17 @@ static rk_status cfdm_apply(rk_problem* p, double shift, const SI* in, long long
   sp.beta[2] = p->desc.vel[2];
   sp.inv_h = (double)n;
   sp.norm = 1.0 / ((double)n * n * n);
+  // the grids with a compile-time pass (cfdm_has_ct), for FP32 and FP64
+  // throughout; 16-bit storage and compressed bases take the table pass
+  if constexpr (std::is_same<SI, S>::value && std::is_same<S, T>::value) {
+    switch (n) {
+      case 200: return cfdm_apply_ct<SI, S, T, 10, 20>(p, in, in_jstride, out, sc, solve, idx, tw, sp);
+      case 64: return cfdm_apply_ct<SI, S, T, 8, 8>(p, in, in_jstride, out, sc, solve, idx, tw, sp);
+      case 32: return cfdm_apply_ct<SI, S, T, 4, 8>(p, in, in_jstride, out, sc, solve, idx, tw, sp);
+      case 20: return cfdm_apply_ct<SI, S, T, 4, 5>(p, in, in_jstride, out, sc, solve, idx, tw, sp);
+      default: break;
+    }
+  }
   auto k_first = cfdm_pass<SI, S, T, true, false>;
   auto k_mid = cfdm_pass<SI, S, T, false, false>;
   auto k_last = cfdm_pass<SI, S, T, false, true>;

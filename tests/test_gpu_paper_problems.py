@@ -176,11 +176,15 @@ def periodic_fdm(rk, n, storage="f32", tol=1e-7, correct=None, tab=None, u0=None
 
 
 @pytest.mark.parametrize("n,beta,shift,storage,bound", [(20, BETA, 0.05, "f32", 2e-6), (33, (1.0, 0.5, 0.25), 0.3, "f32", 2e-6),
-                                                        (17, BETA, 0.1, "f64", 1e-12), (64, BETA, 0.1, "f32", 2e-6)])
+                                                        (17, BETA, 0.1, "f64", 1e-12), (64, BETA, 0.1, "f32", 2e-6),
+                                                        (20, (1.0, 0.5, 0.25), 0.3, "f64", 1e-12),
+                                                        (32, BETA, 0.1, "f64", 1e-12), (200, BETA, 0.1, "f32", 2e-6)])
 def test_periodic_fdm_apply_matches_oracle(rk, n, beta, shift, storage, bound):
     """The six complex Fourier passes apply P^-1 of the periodic advection
     stage matrix: against the oracle's fast diagonalization (LAPACK Schur
-    basis), for grids that fill the 32-line tiles and grids that do not."""
+    basis), for grids that fill the 32-line tiles and grids that do not.
+    n = 20, 32, 64 and 200 run the compile-time small transforms (FP32 and
+    FP64); n = 17 and 33 (a prime and 3 x 11) the table passes."""
     r = synth.gaussian_bump_periodic(n) + 0.1 * np.random.default_rng(n).standard_normal(n ** 3)
     with periodic_fdm(rk, n, storage=storage, beta=beta) as p:
         z = np.empty_like(r)
