@@ -130,16 +130,19 @@ __global__ void __launch_bounds__(kCfThreads) cfdm_pass(const void* __restrict__
   const int bb = threadIdx.x % kCfTile;
   const int warp = threadIdx.x / kCfTile;
   constexpr int kWarps = kCfThreads / kCfTile;
+  // P_D^-1 constants in T, converted once (an FP64 -> FP32 conversion per
+  // element would run on the slow conversion path); (kz, ky, kx) = (k, a, b),
+  // sin(2 pi m / n) = -Im e^{-2 pi i m / n}, theta summed in the order
+  // kx, ky, kz
+  const T sb2 = (T)sp.beta[2], sinvh = (T)sp.inv_h, ss = (T)sp.s, snorm = (T)sp.norm;
+  const T th_ab = scale ? (T)sp.beta[0] * (-tw[min(b0 + bb, n - 1)].im) + (T)sp.beta[1] * (-tw[a].im) : T(0);
   // output k of line bb: P_D^-1 in the third pass, then the store; lanes of a
   // warp take consecutive bb (coalesced stores)
   auto emit = [&](int k, T r, T i) {
     if (scale) {
-      // (kz, ky, kx) = (k, a, b); sin(2 pi m / n) = -Im e^{-2 pi i m / n}
-      const int kx = b0 + bb;
-      const T th = ((T)sp.beta[0] * (-tw[kx].im) + (T)sp.beta[1] * (-tw[a].im) + (T)sp.beta[2] * (-tw[k].im)) *
-                   (T)sp.inv_h;
-      const T c = (T)sp.s * th;
-      const T den = (T)sp.norm / fma(c, c, T(1));
+      const T th = (th_ab + sb2 * (-tw[k].im)) * sinvh;
+      const T c = ss * th;
+      const T den = snorm / fma(c, c, T(1));
       const T r2 = fma(i, c, r) * den, i2 = fma(-r, c, i) * den;
       r = r2;
       i = i2;
@@ -441,6 +444,9 @@ __global__ void __launch_bounds__(32 * N1) cfdm_pass_ct(const void* __restrict__
   __syncthreads();
   if (bb >= tb) return;
   const int k1 = warp;  // N1 warps: one task each
+  // P_D^-1 constants in T, converted once (see cfdm_pass)
+  const T sb2 = (T)sp.beta[2], sinvh = (T)sp.inv_h, ss = (T)sp.s, snorm = (T)sp.norm;
+  const T th_ab = scale ? (T)sp.beta[0] * (-tws[b0 + bb].im) + (T)sp.beta[1] * (-tws[a].im) : T(0);
   C y[N2];
   cf_for<0, N2>([&](auto j2c) { y[decltype(j2c)::value] = row[N2 * k1 + decltype(j2c)::value]; });
   cf_dft<T, N2>(y);
@@ -449,11 +455,9 @@ __global__ void __launch_bounds__(32 * N1) cfdm_pass_ct(const void* __restrict__
     const int k = k1 + N1 * K2;
     T r = y[K2].re, i = y[K2].im * cj;
     if (scale) {
-      const int kx = b0 + bb;
-      const T th = ((T)sp.beta[0] * (-tws[kx].im) + (T)sp.beta[1] * (-tws[a].im) + (T)sp.beta[2] * (-tws[k].im)) *
-                   (T)sp.inv_h;
-      const T c = (T)sp.s * th;
-      const T den = (T)sp.norm / fma(c, c, T(1));
+      const T th = (th_ab + sb2 * (-tws[k].im)) * sinvh;
+      const T c = ss * th;
+      const T den = snorm / fma(c, c, T(1));
       const T r2 = fma(i, c, r) * den, i2 = fma(-r, c, i) * den;
       r = r2;
       i = i2;
