@@ -69,7 +69,6 @@ rk_status setup_typed(rk_problem* p) {
   g.n = n;
   g.rows = n * n;
   g.pair = n > 128 ? 1 : 0;
-  g.ntiles = 1;
   g.nt = (n + 15) / 16 * 16;
   g.kblocks = (int)((n * sizeof(S) + 127) / 128);
   g.mtiles = g.pair ? (g.rows + kFdmPairRows - 1) / kFdmPairRows : (g.rows + kFdmRows - 1) / kFdmRows;

@@ -171,8 +171,7 @@ __global__ void __launch_bounds__(kFdmThreads, 1)
   volatile int* fail = reinterpret_cast<volatile int*>(qfull + 7);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ntile = blockIdx.x % fg.ntiles;
-  const int total = fg.mtiles * fg.ntiles;
+  const int total = fg.mtiles;
   constexpr int KB = 128 / (int)sizeof(S);  // elements per 128-byte K block
 
   if (threadIdx.x == 0) {
@@ -206,11 +205,11 @@ __global__ void __launch_bounds__(kFdmThreads, 1)
       // ---- TMA producer
       mbar_expect_tx(qfull, qbytes);
       for (int kb = 0; kb < fg.kblocks; ++kb)
-        tma_load2(sQ + (size_t)kb * fg.nt * 128, &tm_q, qfull, kb * KB, ntile * fg.nt);
+        tma_load2(sQ + (size_t)kb * fg.nt * 128, &tm_q, qfull, kb * KB, 0);
       uint32_t it = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
-        const int mt = t / fg.ntiles;
+        const int mt = t;
         for (int kb = 0; kb < fg.kblocks; ++kb, ++it) {
           const int s = (int)(it % NS);
           if (!fdm_wait(&empty[s], ((it / NS) & 1u) ^ 1u, fail)) {
@@ -272,17 +271,16 @@ __global__ void __launch_bounds__(kFdmThreads, 1)
       // warp-uniform: tcgen05.ld below is a warp-collective instruction
       if (!__all_sync(0xffffffffu, fdm_wait(&accfull[acc], (lt >> 1) & 1u, fail))) break;
       tc_fence_after();
-      const int m = (t / fg.ntiles) * kFdmRows + row;
+      const int m = t * kFdmRows + row;
       const bool mrow = m < fg.rows;
       float cab = 0.f;
       if (mode == kFdmScale && mrow) cab = fmaf(c, mu[m / fg.n] + mu[m % fg.n], 1.0f);
-      const int j0 = ntile * fg.nt;
       for (int c0 = 16 * half; c0 < fg.nt; c0 += 32) {
         float rv[16];
         if (mode == kFdmDot) {  // r loads in flight during the TMEM read
 #pragma unroll
           for (int jj = 0; jj < 16; ++jj) {
-            const int j = j0 + c0 + jj;
+            const int j = c0 + jj;
             rv[jj] = (mrow && j < fg.n) ? wid<float>(rdot[(size_t)j * fg.rows + m]) : 0.f;
           }
         }
@@ -290,7 +288,7 @@ __global__ void __launch_bounds__(kFdmThreads, 1)
         tmem_ld16(tbase + ((uint32_t)(quad * 32) << 16) + acc * 128u + (uint32_t)c0, v);
 #pragma unroll
         for (int jj = 0; jj < 16; ++jj) {
-          const int j = j0 + c0 + jj;
+          const int j = c0 + jj;
           if (mrow && j < fg.n) {
             float y = v[jj];
             // P_D >= 1: the fast division's 2-ulp error is far below TF32/FP16 rounding

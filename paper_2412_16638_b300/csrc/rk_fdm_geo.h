@@ -7,8 +7,7 @@ namespace rk {
 struct FdmGeo {
   int n;        // nodes per direction
   int rows;     // n*n
-  int nt;       // columns per N tile: multiple of 16, <= 128 (pair: the full N, <= 256)
-  int ntiles;   // N tiles (1 or 2); the grid is a multiple of ntiles (pair: 1)
+  int nt;       // N columns, a multiple of 16: all of Q (n <= 128), or both CTAs' halves together (pair, <= 256)
   int kblocks;  // 128-byte K blocks: ceil(n * sizeof(S) / 128)
   int mtiles;   // ceil(rows / 128) (pair: ceil(rows / 256))
   int pair;     // 1: fdm_pass_pair on CTA pairs (n > 128)
