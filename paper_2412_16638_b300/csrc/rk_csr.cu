@@ -527,8 +527,11 @@ static rk_status csr_minv(rk_problem* p, double shift, const void** out, const u
   const int bs = p->sol.bj_block;
   const long long nbl = (p->n + bs - 1) / bs;
   const long long nblocks = (long long)p->n * p->n * nbl;
-  if (!e.dev) RK_TRY(alloc_dev(p, &e.dev, (size_t)nblocks * bs * bs * dtype_size(p->sol.storage)));
   const double tau = p->sol.bj_adapt_tau;
+  // Thomas factors (3 values per row) without adaptive precision, else the
+  // dense inverses (see csr_bj_setup)
+  const long long slot = tau > 0.0 ? (long long)bs * bs : 3LL * bs;
+  if (!e.dev) RK_TRY(alloc_dev(p, &e.dev, (size_t)(nblocks * slot) * dtype_size(p->sol.storage)));
   if (tau > 0.0 && !e.flags) RK_TRY(alloc_dev(p, (void**)&e.flags, (size_t)nblocks));
   rk_status st = RK_OK;
   dispatch_st(p->sol.storage, [&](auto ts, auto) {
@@ -536,7 +539,7 @@ static rk_status csr_minv(rk_problem* p, double shift, const void** out, const u
     dispatch_bs(bs, [&](auto bsc) {
       constexpr int BS = decltype(bsc)::value;
       auto kern = csr_bj_setup<S, BS>;
-      launch(p, K_CSR_BJ_SETUP, (double)p->csr.nnz * 12.0 + (double)nblocks * BS * BS * sizeof(S), [&] {
+      launch(p, K_CSR_BJ_SETUP, (double)p->csr.nnz * 12.0 + (double)(nblocks * slot) * sizeof(S), [&] {
         kern<<<grid_for((const void*)kern, nblocks), kThreads, 0, p->st>>>(view(p), p->csr.v64, p->n, shift,
                                                                           static_cast<S*>(e.dev), tau, e.flags);
       });
@@ -600,7 +603,7 @@ rk_status csr_precond_f64(rk_problem* p, double shift, const double* r, double* 
       constexpr int SEG = seg_of<S, BS>();
       HeatGeo g{p->n, (p->n + SEG - 1) / SEG, (long long)p->n * p->n, p->N};
       auto kern = csr_bj_apply_f64io<S, T, BS, SEG>;
-      launch(p, K_BJ, (16.0 + BS * sizeof(S)) * p->N, [&] {
+      launch(p, K_BJ, (16.0 + (flags ? BS : 3) * sizeof(S)) * p->N, [&] {
         kern<<<grid_for((const void*)kern, g.n2 * g.nseg), kThreads, 0, p->st>>>(g, static_cast<const S*>(minv), flags,
                                                                                 r, z);
       });
@@ -675,8 +678,11 @@ rk_status gmres_solve(rk_problem* p, double shift, const double* g64, RhsScalars
       // block inverses read per apply: BS entries per row, FP16 for the
       // adaptively stored blocks, plus one flag byte per block
       const double fhalf = p->bj_blocks > 0 ? (double)p->bj_half_blocks / (double)p->bj_blocks : 0.0;
-      const double minv_bytes = (double)BS * p->N * (sizeof(S) * (1.0 - fhalf) + 2.0 * fhalf) +
-                                (mflags ? (double)p->bj_blocks : 0.0);
+      // the block-Jacobi data read per application: Thomas factors (3 per
+      // row), or dense inverse rows (BS per row, FP16 rows at 2 bytes) and flags
+      const double minv_bytes = mflags ? (double)BS * p->N * (sizeof(S) * (1.0 - fhalf) + 2.0 * fhalf) +
+                                             (double)p->bj_blocks
+                                       : 3.0 * p->N * sizeof(S);
       auto k_start = gm_start<S, B, T, SEG>;
       auto k_restart = gm_restart<S, B, T, SEG>;
       auto k_prec = gm_dc_prec<S, B, T, BS, SEG>;

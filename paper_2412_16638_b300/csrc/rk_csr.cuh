@@ -88,16 +88,20 @@ __global__ void __launch_bounds__(kThreads) csr_correct_f64_kernel(CsrView A, co
 }
 
 // ------------------------------------------------------------- block-Jacobi
-// Per-block inverses of the x-line-segment blocks of I - shift L.  One thread
-// per block: the block of a 7-point operator restricted to an x-line segment
-// is tridiagonal; its inverse is formed column by column with the Thomas
-// recurrences in FP64 (the blocks are diagonally dominant M-matrices, so no
-// pivoting is needed) and stored row-major, zero padded to BS x BS, in a slot
-// of BS*BS storage elements.  Adaptive precision (tau > 0; the
-// adaptive-precision block-Jacobi of Ginkgo, Sec. 1): a block whose 1-norm
-// condition number kappa_1 = ||D||_1 ||D^-1||_1 satisfies
-// kappa_1 * 2^-11 <= tau is stored in FP16 in the first half of its slot and
-// flagged (flags[b] = 1); flags may be null when tau <= 0.
+// The x-line-segment blocks of I - shift L.  One thread per block: the block
+// of a 7-point operator restricted to an x-line segment is tridiagonal, and
+// its Thomas factorisation is formed in FP64 (the blocks are diagonally
+// dominant, so no pivoting is needed).
+//   * flags == null (no adaptive precision): the slot of 3 BS storage
+//     elements holds the factors -- multipliers l_i, inverse pivots 1/d_i and
+//     ratios c_i -- and D^-1 r is applied by forward and back substitution
+//     (3 values per row instead of the BS of a dense inverse row).
+//   * flags != null (adaptive precision, tau > 0; the adaptive-precision
+//     block-Jacobi of Ginkgo, Sec. 1): the inverse is formed column by column
+//     and stored row-major, zero padded to BS x BS, in a slot of BS*BS storage
+//     elements.  A block whose 1-norm condition number
+//     kappa_1 = ||D||_1 ||D^-1||_1 satisfies kappa_1 * 2^-11 <= tau is stored
+//     in FP16 in the first half of its slot and flagged (flags[b] = 1).
 template <typename S, int BS>
 __global__ void __launch_bounds__(kThreads) csr_bj_setup(CsrView A, const double* __restrict__ vals, int n,
                                                          double shift, S* __restrict__ minv, double tau,
@@ -129,6 +133,15 @@ __global__ void __launch_bounds__(kThreads) csr_bj_setup(CsrView A, const double
     for (int i = 0; i < m; ++i) {
       den[i] = di[i] - (i > 0 ? lo[i] * cp[i - 1] : 0.0);
       cp[i] = (i + 1 < m) ? up[i] / den[i] : 0.0;
+    }
+    if (!flags) {  // the factors; rows past m stay zero (their z is 0)
+      S* f = minv + b * 3 * BS;
+      for (int i = 0; i < BS; ++i) {
+        f[i] = nar<S>(i < m && i > 0 ? lo[i] : 0.0);
+        f[BS + i] = nar<S>(i < m ? 1.0 / den[i] : 0.0);
+        f[2 * BS + i] = nar<S>(i < m ? cp[i] : 0.0);
+      }
+      continue;
     }
     double inv[BS][BS];
     double ninv = 0.0, nblk = 0.0;  // 1-norms of the inverse and of the block
@@ -167,8 +180,9 @@ __global__ void __launch_bounds__(kThreads) csr_bj_setup(CsrView A, const double
   }
 }
 
-// z = D^{-1} r for the blocks of one segment (per-block inverses in S, or in
-// FP16 where flags marks the block).
+// z = D^{-1} r for the blocks of one segment: by the Thomas factors when
+// flags is null, else by the per-block inverses (in S, or in FP16 where flags
+// marks the block); see csr_bj_setup.
 template <typename T, typename S, int BS, int SEG>
 __device__ __forceinline__ void bj_apply_blocks(const S* __restrict__ minv, const unsigned char* __restrict__ flags,
                                                 long long line, int nbl, int i0, const T (&r)[SEG], T (&z)[SEG]) {
@@ -181,6 +195,20 @@ __device__ __forceinline__ void bj_apply_blocks(const S* __restrict__ minv, cons
       continue;
     }
     const long long blk = line * nbl + bi;
+    if (flags == nullptr) {
+      const S* F = minv + blk * (long long)(3 * BS);
+      T lf[BS], iv[BS], cf[BS], dp[BS];
+      load_seg<T, S, BS>(F, BS, lf);
+      load_seg<T, S, BS>(F + BS, BS, iv);
+      load_seg<T, S, BS>(F + 2 * BS, BS, cf);
+      dp[0] = r[cb * BS] * iv[0];
+#pragma unroll
+      for (int i = 1; i < BS; ++i) dp[i] = fma(-lf[i], dp[i - 1], r[cb * BS + i]) * iv[i];
+      z[cb * BS + BS - 1] = dp[BS - 1];
+#pragma unroll
+      for (int i = BS - 2; i >= 0; --i) z[cb * BS + i] = fma(-cf[i], z[cb * BS + i + 1], dp[i]);
+      continue;
+    }
     const S* M = minv + blk * (long long)(BS * BS);
     const bool half_block = flags != nullptr && flags[blk] != 0;
 #pragma unroll
