@@ -22,9 +22,9 @@
 // issues TMA loads (Q once, then 128 x 128-byte K blocks of X into a ring of
 // stages); warp 1 owns the tensor memory and issues tcgen05.mma with the
 // accumulator in TMEM (two accumulators, so the epilogue of one tile overlaps
-// the MMAs of the next); warps 2-9 read the accumulator with tcgen05.ld and
-// store (two warps per TMEM lane quadrant, alternating 16-column chunks, so
-// the stores of one hide the latency of the other).  The ring holds as many
+// the MMAs of the next); warps 2-17 read the accumulator with tcgen05.ld and
+// store (four warps per TMEM lane quadrant, every fourth 16-column chunk each,
+// so the stores of one hide the latency of the others).  The ring holds as many
 // 16 KB X stages as shared memory allows beside Q, up to 6.
 // 128 < n <= 256: Q (up to 256 KB) no longer fits one CTA's shared memory,
 // and the pass runs on CTA pairs with tcgen05.mma.cta_group::2 (fdm_pass_pair
@@ -48,7 +48,7 @@
 namespace rk {
 
 constexpr int kFdmMaxStages = 6;  // K-block stages of X (ring depth set per problem)
-constexpr int kFdmEpiWarps = 8;    // epilogue warps: two per TMEM lane quadrant
+constexpr int kFdmEpiWarps = 16;   // epilogue warps: four per TMEM lane quadrant
 constexpr int kFdmThreads = 32 * (2 + kFdmEpiWarps);
 constexpr int kFdmRows = 128;      // rows per tile (TMEM lanes)
 constexpr int kFdmTmemCols = 256;  // two FP32 accumulators of up to 128 columns
@@ -260,9 +260,9 @@ __global__ void __launch_bounds__(kFdmThreads, 1)
     }
   } else {
     // ---- epilogue: warp w owns TMEM lane quadrant w % 4 (the hardware
-    // restriction) and every second 16-column chunk, starting at (w - 2) / 4
+    // restriction) and every fourth 16-column chunk, starting at (w - 2) / 4
     const int quad = warp & 3;
-    const int half = (warp - 2) >> 2;
+    const int part = (warp - 2) >> 2;  // 0..3
     const int row = quad * 32 + lane;
     float dacc[4] = {0.f, 0.f, 0.f, 0.f};
     uint32_t lt = 0;
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(kFdmThreads, 1)
       const bool mrow = m < fg.rows;
       float cab = 0.f;
       if (mode == kFdmScale && mrow) cab = fmaf(c, mu[m / fg.n] + mu[m % fg.n], 1.0f);
-      for (int c0 = 16 * half; c0 < fg.nt; c0 += 32) {
+      for (int c0 = 16 * part; c0 < fg.nt; c0 += 64) {
         float rv[16];
         if (mode == kFdmDot) {  // r loads in flight during the TMEM read
 #pragma unroll
@@ -585,7 +585,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFdmPairThreads, 1)
     }
   } else {
     // ---- epilogue (both CTAs): warp w owns TMEM lane quadrant w % 4 and every
-    // second 16-column chunk, starting at (w - 2) / 4
+    // fourth 16-column chunk, starting at (w - 2) / 4
     const int quad = warp & 3;
     const int part = (warp - 2) >> 2;  // 0..3
     const int row = quad * 32 + lane;
